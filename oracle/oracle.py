@@ -1,0 +1,173 @@
+"""ctypes wrapper around the plain C QRDM oracle (qrdm_oracle.c).
+
+Test infrastructure only: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may use it; the product path never does.
+
+The oracle is a slow, single-threaded FP64 restatement of QRDM2 (Algorithm 4)
+with Deviation Maximization (Algorithm 1) and the implementation choices of
+Sec. 4; the readings it takes where the paper is silent are listed in the C
+file's header.  Every function here is pinned by tests against values fixed
+by the paper or the mathematics (see tests/test_oracle_*.py).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qrdm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+EPS = 2.0 ** -52
+
+STEP_DTYPE = np.dtype(
+    [
+        ("ns", np.int64),
+        ("jstar", np.int64),
+        ("ncand_all", np.int64),
+        ("ncand", np.int64),
+        ("k", np.int64),
+        ("l", np.int64),
+        ("dm_on", np.int64),
+        ("nrecomp", np.int64),
+        ("mu", np.float64),
+        ("eps_s", np.float64),
+        ("s_argmax", np.float64),
+        ("s_cand", np.float64),
+        ("s_order", np.float64),
+        ("s_cos", np.float64),
+        ("s_break", np.float64),
+        ("s_stop", np.float64),
+        ("s_recomp", np.float64),
+        ("g_argmax", np.float64),
+        ("g_cand", np.float64),
+        ("g_cos", np.float64),
+        ("g_break", np.float64),
+        ("g_stop", np.float64),
+    ]
+)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (gcc, plain C)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, f64, p = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+            lib.oq_qrdm.restype = ctypes.c_int
+            lib.oq_qrdm.argtypes = [i64, i64, p, i64, f64, f64, i64, i64, i64, i64, i64, i64, i64, p, p, p, p, p, p,
+                                    p, i64, p, p]
+            lib.oq_house.restype = None
+            lib.oq_house.argtypes = [i64, p, p, p]
+            lib.oq_larft.restype = None
+            lib.oq_larft.argtypes = [i64, i64, p, i64, p, p, i64]
+            lib.oq_cosine.restype = None
+            lib.oq_cosine.argtypes = [i64, i64, p, i64, i64, p, p, p]
+            lib.oq_step_size.restype = i64
+            assert lib.oq_step_size() == STEP_DTYPE.itemsize, "oracle trace layout mismatch"
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def house(x):
+    """Householder reflector of x: returns (beta, htau, v) with v[0] = 1."""
+    lib = _load()
+    x = np.array(x, dtype=np.float64)
+    beta = np.zeros(1)
+    ht = np.zeros(1)
+    lib.oq_house(x.shape[0], _ptr(x), _ptr(beta), _ptr(ht))
+    v = x.copy()
+    v[0] = 1.0
+    return float(beta[0]), float(ht[0]), v
+
+
+def larft(V: np.ndarray, htau: np.ndarray) -> np.ndarray:
+    """T (l x l, upper) with H_1 ... H_l = I - V T V^T; V unit lower trapezoidal."""
+    lib = _load()
+    V = np.asfortranarray(V, dtype=np.float64)
+    mr, l = V.shape
+    ht = np.ascontiguousarray(htau, dtype=np.float64)
+    T = np.zeros((l, l), order="F")
+    lib.oq_larft(mr, l, _ptr(V), max(mr, 1), _ptr(ht), _ptr(T), max(l, 1))
+    return T
+
+
+def cosine(A: np.ndarray, cols, r0: int = 0):
+    """(G, Theta) for columns ``cols`` of A over rows r0..m-1."""
+    lib = _load()
+    A = np.asfortranarray(A, dtype=np.float64)
+    m = A.shape[0]
+    c = np.ascontiguousarray(cols, dtype=np.int64)
+    kc = c.shape[0]
+    G = np.zeros((kc, kc), order="F")
+    Th = np.zeros((kc, kc), order="F")
+    lib.oq_cosine(m, r0, _ptr(A), max(m, 1), kc, _ptr(c), _ptr(G), _ptr(Th))
+    return G, Th
+
+
+def qrdm(A: np.ndarray, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mode: int = 0,
+         stop_at_rank: bool = False, check_last: bool = False, no_break: bool = False, sdd: bool = False,
+         max_steps: int = 0, trace_cap: int | None = None) -> dict:
+    """Factor A Pi = Q R by QRDM2.  Returns a dict:
+
+    ``A`` (R above the diagonal, reflector tails below), ``htau``, ``perm``,
+    ``rank``, ``rank_colmax``, ``u``/``uref`` (partial norms at exit),
+    ``trace`` (one record per block step, STEP_DTYPE), ``J`` (per step, the
+    original indices of the selected columns, -1 padded), ``status``.
+    """
+    lib = _load()
+    A = np.array(A, dtype=np.float64, order="F", copy=True)
+    m, n = A.shape
+    kmin = min(m, n)
+    htau = np.zeros(max(kmin, 1))
+    perm = np.zeros(max(n, 1), dtype=np.int64)
+    rank = np.zeros(1, dtype=np.int64)
+    rank_cm = np.zeros(1, dtype=np.int64)
+    u = np.zeros(max(n, 1))
+    uref = np.zeros(max(n, 1))
+    cap = trace_cap if trace_cap is not None else max(kmin, 1)
+    trace = np.zeros(cap, dtype=STEP_DTYPE)
+    J = np.full((cap, k_max), -1, dtype=np.int64)
+    nsteps = np.zeros(1, dtype=np.int64)
+    st = lib.oq_qrdm(m, n, _ptr(A), max(m, 1), float(tau), float(delta), int(k_max), int(eps1_mode),
+                     int(stop_at_rank), int(check_last), int(no_break), int(sdd), int(max_steps), _ptr(htau),
+                     _ptr(perm), _ptr(rank), _ptr(rank_cm), _ptr(u), _ptr(uref), _ptr(trace), cap, _ptr(J),
+                     _ptr(nsteps))
+    ns = int(nsteps[0])
+    return {
+        "status": int(st),
+        "A": A,
+        "htau": htau[:kmin],
+        "perm": perm[:n],
+        "rank": int(rank[0]),
+        "rank_colmax": int(rank_cm[0]),
+        "u": u[:n],
+        "uref": uref[:n],
+        "trace": trace[:min(ns, cap)],
+        "J": J[:min(ns, cap)],
+        "nsteps": ns,
+    }
+
