@@ -1,0 +1,141 @@
+/*
+ * qrdm.h -- C ABI of the GB300 QRDM library (libqrdm.so).
+ *
+ * QRDM is Householder QR with Deviation Maximization column pivoting
+ * (Dessole & Marcuzzi, "Deviation Maximization for Rank-Revealing QR
+ * Factorizations", 2021): A Pi = Q R, where each block step picks up to
+ * k_max well-separated, large-norm columns at once (Algorithm 1), moves them
+ * to the front, factors them as a Householder panel that stops early when a
+ * column turns out dependent (Algorithm 4), and updates the trailing matrix
+ * with one compact-WY block reflector (Sec. 3.2).
+ *
+ * Every step runs on the GPU as hand-written sm_103a CUDA kernels.  The
+ * library allocates no device memory: the caller passes the matrix, the
+ * outputs and one workspace buffer sized by qrdm_workspace_size().  All
+ * pointers named d_* are device pointers; all others are host pointers.
+ * Calls are ordered on the given CUDA stream.  The factorization is driven
+ * from the host; qrdm_factor() returns after the stream has completed the
+ * work (it synchronizes on `stream` while stepping).
+ *
+ * Errors: 0 on success; -i when the i-th argument is invalid (LAPACK
+ * convention: nothing is read or written); a positive QRDM_ERR_* code
+ * otherwise.  On QRDM_ERR_NONFINITE the matrix has not been modified.
+ */
+#ifndef QRDM_H
+#define QRDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QRDM_OK 0
+#define QRDM_ERR_CUDA 1      /* a CUDA runtime call failed (qrdm_last_cuda_error() has it) */
+#define QRDM_ERR_NONFINITE 2 /* A holds a NaN or an infinity; A is left unmodified */
+#define QRDM_ERR_WORKSPACE 3 /* workspace too small or misaligned (256-byte alignment) */
+#define QRDM_ERR_UNSUPPORTED 4 /* the device or an option is not supported */
+#define QRDM_ERR_INTERNAL 5  /* an internal consistency check failed on the device */
+
+#define QRDM_KMAX_LIMIT 128 /* largest supported k_max */
+
+/* Options; a NULL pointer means all zero (the defaults). */
+typedef struct qrdm_opts {
+  /* eps1 in the stopping criterion sqrt(n - n_s) max||c_i|| <= eps1 max||a_i||
+     (Sec. 3.4, eq. practical stopping criterion): 0 -> eps*n (default, the
+     paper's preferred choice), 1 -> eps*sqrt(n); eps = 2^-52. */
+  int32_t eps1_mode;
+  /* 0 (default): factor all min(m,n) columns; once the criterion holds, DM is
+     switched off and single-column pivoting finishes (Sec. 4, DM safeguard).
+     1: stop at the numerical rank; rows >= rank of the trailing block are
+     left unreduced and htau[i] = 0 for i >= rank. */
+  int32_t stop_at_rank;
+  /* 1: the panel break test (Algorithm 4) also checks the last panel column;
+     0 (default): the literal test, applied while l+1 < k_s (1-based). */
+  int32_t check_last;
+  /* 1: no break test at all (Algorithm 3). */
+  int32_t no_break;
+  /* 1: use delta_s = min(delta, tau^2 / max(1,|I|)) per step (eq. delta_max),
+     which makes every DM block satisfy Lemma 1. */
+  int32_t sdd;
+  /* > 0: stop after this many block steps (partial factorization). */
+  int32_t max_steps;
+  int32_t reserved0;
+  int32_t reserved1;
+} qrdm_opts;
+
+/* Host-side results of one factorization. */
+typedef struct qrdm_info {
+  int64_t rank;        /* n_s at which the criterion of Sec. 3.4 first held (min(m,n) if never) */
+  int64_t rank_colmax; /* same test without the sqrt(n - n_s) factor */
+  int64_t nsteps;      /* block steps executed */
+  int32_t cuda_error;  /* cudaError_t of the failing call when QRDM_ERR_CUDA */
+  int32_t reserved;
+} qrdm_info;
+
+/* One record per block step, written on the device when a trace is requested. */
+typedef struct qrdm_step_record {
+  int64_t ns;        /* columns factored before the step */
+  int64_t jstar;     /* current position of the largest partial norm */
+  int64_t ncand_all; /* candidates u_i >= tau*mu before the k_max - 1 cap */
+  int64_t ncand;     /* |I| after the cap */
+  int64_t k;         /* |J|: columns picked by DM */
+  int64_t l;         /* reflectors accepted by the panel */
+  int64_t dm_on;     /* 1 while DM pivoting is on */
+  int64_t nrecomp;   /* partial norms recomputed in the norm update */
+  double mu;         /* largest partial norm at step start */
+  double eps_s;      /* panel break threshold tau*mu (eq. lenght_check) */
+} qrdm_step_record;
+
+/*
+ * Bytes of device workspace qrdm_factor() needs for an m x n matrix and this
+ * k_max (1 <= k_max <= QRDM_KMAX_LIMIT).  Returns 0 or -i.
+ */
+int qrdm_workspace_size(int64_t m, int64_t n, int32_t k_max, size_t* bytes);
+
+/*
+ * Factor A Pi = Q R in place (QRDM2, Algorithm 4 of the paper, with DM of
+ * Algorithm 1 and the Sec. 4 choices).
+ *
+ *   dA      device, m x n, column-major, leading dimension lda >= max(1,m);
+ *           on return R is in the upper triangle and the Householder vectors
+ *           v_i (v_i(i) = 1 implicit) below the diagonal, as in LAPACK dgeqp3.
+ *   tau     candidate threshold, 0 < tau <= 1 (eq. def_candidate_set).
+ *   delta   cosine bound, 0 <= delta <= 1 (strict test |theta| < delta).
+ *   k_max   block cap: |J| <= k_max, 1 <= k_max <= QRDM_KMAX_LIMIT; k_max = 1
+ *           is QR with column pivoting (Algorithm 2).
+ *   d_htau  device, min(m,n) doubles: Q = H_1 ... H_min(m,n),
+ *           H_i = I - htau_i v_i v_i^T.
+ *   d_perm  device, n int32: column i of A Pi is column d_perm[i] of A (0-based).
+ *   info    host, required: rank, rank_colmax, steps.
+ *   opts    host, may be NULL.
+ *   d_work  device workspace of at least qrdm_workspace_size() bytes,
+ *           256-byte aligned; its contents on entry are ignored.
+ *   stream  cudaStream_t (NULL: the legacy default stream).
+ *   d_trace, d_trace_J, trace_cap: optional (NULL/0) device step trace:
+ *           trace_cap records and trace_cap*k_max int32 original column
+ *           indices of J per step (-1 padded).
+ *
+ * Error behaviour: -1..-7 for invalid m, n, dA, lda, tau, delta, k_max; -8/-9
+ * for NULL d_htau/d_perm when needed, -10 for NULL info, -12 for a NULL
+ * workspace when one is needed.  m = 0 or n = 0 returns 0 with rank 0.
+ */
+int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, double delta, int32_t k_max,
+                double* d_htau, int32_t* d_perm, qrdm_info* info, const qrdm_opts* opts, void* d_work,
+                size_t work_bytes, void* stream, qrdm_step_record* d_trace, int32_t* d_trace_J, int64_t trace_cap);
+
+/* Static description of an error code. */
+const char* qrdm_strerror(int code);
+
+/* cudaError_t of the last failing CUDA call in this thread (0 if none). */
+int qrdm_last_cuda_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int qrdm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QRDM_H */

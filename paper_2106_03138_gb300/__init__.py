@@ -1,0 +1,129 @@
+"""GB300-native QRDM: rank-revealing Householder QR with Deviation Maximization
+pivoting (Dessole & Marcuzzi, 2021), as hand-written sm_103a CUDA kernels
+behind the C ABI of include/qrdm.h.
+
+``factor`` is a convenience wrapper: it allocates the outputs and the
+workspace with PyTorch (device memory and the current stream only) and calls
+``qrdm_factor`` through ctypes.  The factorization itself runs entirely in the
+library's kernels; there is no CPU path.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from ._binding import (  # noqa: F401
+    EXPORTS,
+    QRDM_ERR_CUDA,
+    QRDM_ERR_INTERNAL,
+    QRDM_ERR_NONFINITE,
+    QRDM_ERR_UNSUPPORTED,
+    QRDM_ERR_WORKSPACE,
+    QRDM_KMAX_LIMIT,
+    QRDM_OK,
+    load,
+    qrdm_factor,
+    qrdm_info,
+    qrdm_opts,
+    qrdm_step_record,
+    qrdm_strerror,
+    qrdm_workspace_size,
+)
+
+TRACE_DTYPE = np.dtype([("ns", np.int64), ("jstar", np.int64), ("ncand_all", np.int64), ("ncand", np.int64),
+                        ("k", np.int64), ("l", np.int64), ("dm_on", np.int64), ("nrecomp", np.int64),
+                        ("mu", np.float64), ("eps_s", np.float64)])
+
+
+class QRDMError(RuntimeError):
+    def __init__(self, code: int, where: str = "qrdm_factor"):
+        self.code = code
+        msg = f"{where} failed: {code} ({qrdm_strerror(code)})"
+        super().__init__(msg)
+
+
+@dataclass
+class Factorization:
+    A: object          # torch tensor (m x n, column-major): R above, reflector tails below the diagonal
+    htau: object       # torch float64 (min(m, n),)
+    perm: object       # torch int32 (n,)
+    rank: int
+    rank_colmax: int
+    nsteps: int
+    trace: np.ndarray | None = None   # TRACE_DTYPE records, one per block step
+    J: np.ndarray | None = None       # (nsteps, k_max) original indices of the picked columns
+
+
+def make_opts(eps1_mode=0, stop_at_rank=False, check_last=False, no_break=False, sdd=False, max_steps=0) -> qrdm_opts:
+    o = qrdm_opts()
+    o.eps1_mode = int(eps1_mode)
+    o.stop_at_rank = int(bool(stop_at_rank))
+    o.check_last = int(bool(check_last))
+    o.no_break = int(bool(no_break))
+    o.sdd = int(bool(sdd))
+    o.max_steps = int(max_steps)
+    return o
+
+
+def colmajor(A, device="cuda"):
+    """A column-major (Fortran-order) float64 CUDA tensor holding A."""
+    import torch
+
+    if isinstance(A, np.ndarray):
+        t = torch.from_numpy(np.asfortranarray(A, dtype=np.float64))
+    else:
+        t = A
+    t = t.to(device=device, dtype=torch.float64)
+    if t.dim() != 2:
+        raise ValueError("A must be 2-D")
+    m, n = t.shape
+    if (m > 1 and t.stride(0) != 1) or (n > 1 and t.stride(1) < max(1, m)):
+        t = t.t().contiguous().t()
+    return t
+
+
+def factor(A, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mode: int = 0,
+           stop_at_rank: bool = False, check_last: bool = False, no_break: bool = False, sdd: bool = False,
+           max_steps: int = 0, trace: bool = False, workspace=None, out_htau=None, out_perm=None,
+           stream=None) -> Factorization:
+    """Factor A Pi = Q R in place.  ``A`` is a CUDA float64 tensor with
+    stride(0) == 1 (column-major, lda = stride(1))."""
+    import torch
+
+    if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2):
+        raise ValueError("A must be a 2-D float64 CUDA tensor")
+    m, n = A.shape
+    if m > 1 and A.stride(0) != 1:
+        raise ValueError("A must be column-major (stride(0) == 1)")
+    lda = A.stride(1) if n > 1 else max(m, 1)
+    if m * n and lda < max(m, 1):
+        raise ValueError("A's column stride is smaller than its row count")
+    kmin = min(m, n)
+    dev = A.device
+    htau = out_htau if out_htau is not None else torch.empty(max(kmin, 1), dtype=torch.float64, device=dev)
+    perm = out_perm if out_perm is not None else torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    wbytes = qrdm_workspace_size(m, n, k_max)
+    if workspace is None:
+        workspace = torch.empty(wbytes, dtype=torch.uint8, device=dev)
+    tr = trJ = None
+    cap = 0
+    if trace:
+        cap = max(kmin, 1) + 1
+        tr = torch.zeros(cap * TRACE_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        trJ = torch.empty(cap * k_max, dtype=torch.int32, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    opts = make_opts(eps1_mode, stop_at_rank, check_last, no_break, sdd, max_steps)
+    rc, info = qrdm_factor(A.data_ptr() if m * n else 0, m, n, lda, float(tau), float(delta), int(k_max),
+                           htau.data_ptr(), perm.data_ptr(), opts, workspace.data_ptr(), workspace.numel(),
+                           s.cuda_stream, tr.data_ptr() if tr is not None else 0,
+                           trJ.data_ptr() if trJ is not None else 0, cap)
+    if rc != 0:
+        raise QRDMError(rc)
+    out = Factorization(A=A, htau=htau[:kmin], perm=perm[:n], rank=int(info.rank), rank_colmax=int(info.rank_colmax),
+                        nsteps=int(info.nsteps))
+    if trace:
+        ns = min(out.nsteps, cap)
+        out.trace = np.frombuffer(tr.cpu().numpy().tobytes(), dtype=TRACE_DTYPE)[:ns].copy()
+        out.J = trJ.cpu().numpy().reshape(cap, k_max)[:ns].copy()
+    return out

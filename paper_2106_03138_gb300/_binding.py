@@ -1,0 +1,98 @@
+"""ctypes binding of libqrdm.so: the C ABI of include/qrdm.h, same names.
+
+Argument marshalling only.  Every step of the factorization runs in the
+library's CUDA kernels; nothing here computes.  There is no fallback: if the
+library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+c_i32, c_i64, c_f64, c_p, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+
+QRDM_OK = 0
+QRDM_ERR_CUDA = 1
+QRDM_ERR_NONFINITE = 2
+QRDM_ERR_WORKSPACE = 3
+QRDM_ERR_UNSUPPORTED = 4
+QRDM_ERR_INTERNAL = 5
+QRDM_KMAX_LIMIT = 128
+
+
+class qrdm_opts(ctypes.Structure):
+    _fields_ = [("eps1_mode", c_i32), ("stop_at_rank", c_i32), ("check_last", c_i32), ("no_break", c_i32),
+                ("sdd", c_i32), ("max_steps", c_i32), ("reserved0", c_i32), ("reserved1", c_i32)]
+
+
+class qrdm_info(ctypes.Structure):
+    _fields_ = [("rank", c_i64), ("rank_colmax", c_i64), ("nsteps", c_i64), ("cuda_error", c_i32),
+                ("reserved", c_i32)]
+
+
+class qrdm_step_record(ctypes.Structure):
+    _fields_ = [("ns", c_i64), ("jstar", c_i64), ("ncand_all", c_i64), ("ncand", c_i64), ("k", c_i64), ("l", c_i64),
+                ("dm_on", c_i64), ("nrecomp", c_i64), ("mu", c_f64), ("eps_s", c_f64)]
+
+
+# every symbol declared in include/qrdm.h
+EXPORTS = ("qrdm_workspace_size", "qrdm_factor", "qrdm_strerror", "qrdm_last_cuda_error", "qrdm_version")
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libqrdm.so (building it first if needed).  Raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB) or not _build.up_to_date():
+            if not build_if_missing:
+                raise RuntimeError(f"libqrdm.so not built ({_build.LIB}); run __graft_entry__.build()")
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        lib.qrdm_workspace_size.restype = ctypes.c_int
+        lib.qrdm_workspace_size.argtypes = [c_i64, c_i64, c_i32, ctypes.POINTER(c_sz)]
+        lib.qrdm_factor.restype = ctypes.c_int
+        lib.qrdm_factor.argtypes = [c_p, c_i64, c_i64, c_i64, c_f64, c_f64, c_i32, c_p, c_p, ctypes.POINTER(qrdm_info),
+                                    ctypes.POINTER(qrdm_opts), c_p, c_sz, c_p, c_p, c_p, c_i64]
+        lib.qrdm_strerror.restype = ctypes.c_char_p
+        lib.qrdm_strerror.argtypes = [ctypes.c_int]
+        lib.qrdm_last_cuda_error.restype = ctypes.c_int
+        lib.qrdm_last_cuda_error.argtypes = []
+        lib.qrdm_version.restype = ctypes.c_int
+        lib.qrdm_version.argtypes = []
+        _lib = lib
+        return lib
+
+
+def qrdm_workspace_size(m: int, n: int, k_max: int) -> int:
+    out = c_sz(0)
+    rc = load().qrdm_workspace_size(m, n, k_max, ctypes.byref(out))
+    if rc != 0:
+        raise ValueError(f"qrdm_workspace_size: invalid argument {-rc}")
+    return int(out.value)
+
+
+def qrdm_strerror(code: int) -> str:
+    return load().qrdm_strerror(code).decode()
+
+
+def qrdm_factor(dA: int, m: int, n: int, lda: int, tau: float, delta: float, k_max: int, d_htau: int, d_perm: int,
+                opts: qrdm_opts | None, d_work: int, work_bytes: int, stream: int, d_trace: int = 0,
+                d_trace_J: int = 0, trace_cap: int = 0) -> tuple[int, qrdm_info]:
+    """Direct call of the C entry point (device addresses as ints)."""
+    info = qrdm_info()
+    rc = load().qrdm_factor(dA, m, n, lda, tau, delta, k_max, d_htau, d_perm, ctypes.byref(info),
+                            ctypes.byref(opts) if opts is not None else None, d_work, work_bytes, stream,
+                            d_trace or None, d_trace_J or None, trace_cap)
+    return rc, info

@@ -1,0 +1,1063 @@
+// QRDM block-step kernels for GB300 (sm_103a), FP64.
+//
+// One block step of QRDM2 (Algorithm 4) runs as the kernel sequence
+//   k_select -> k_gram -> k_gram_reduce -> k_pick -> k_permute -> k_panel
+//   -> k_trail_w -> k_trail_wreduce -> k_trail_update -> k_downdate
+// All kernels read the step state (n_s, k, l, ...) from device memory, so the
+// host never needs the values to launch them; grids are fixed and CTAs loop
+// over the work units of the current step.
+//
+// FP64 on GB300 issues about 2 FMA per clock per SM (1.2 TFLOP/s for the
+// chip), so every FP64-heavy phase is spread over all SMs; HBM traffic is a
+// secondary concern for this precision.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cg = cooperative_groups;
+
+namespace qrdm {
+
+constexpr int KMAX = 128;          // largest supported k_max
+constexpr double EPS = 2.220446049250313080847e-16;  // 2^-52
+constexpr int PANEL_THREADS = 256;
+constexpr int GEMM_THREADS = 256;
+
+// Step state, one per factorization, in the workspace.
+struct alignas(128) DevState {
+  int64_t ns;       // columns factored (n_s)
+  int64_t step;     // block steps started
+  int64_t rank;     // -1 until the Sec. 3.4 criterion holds
+  int64_t rank_colmax;
+  int64_t jstar;    // position of the largest partial norm
+  int64_t ncand_all;
+  double mu;        // largest partial norm at step start
+  double eps_s;     // tau * mu
+  double anorm;     // max_j ||a_j||
+  unsigned long long anorm_bits;
+  int32_t done;     // 1 once the factorization is finished
+  int32_t dm_on;    // DM pivoting on (1) or single-column pivoting (0)
+  int32_t kc;       // 1 + |I|: columns in the cosine matrix
+  int32_t k;        // |J|
+  int32_t l;        // reflectors accepted by the panel
+  int32_t npairs;   // column moves of the permutation
+  int32_t nonfinite;
+  int32_t pad;
+};
+
+struct StepRecord {  // layout of qrdm_step_record
+  int64_t ns, jstar, ncand_all, ncand, k, l, dm_on, nrecomp;
+  double mu, eps_s;
+};
+
+struct Params {
+  double* A;
+  int64_t m, n, lda, kmin;
+  double tau, delta, eps1;
+  int32_t kmax, stop_at_rank, check_last, no_break, sdd, max_steps;
+  double* htau;
+  int32_t* perm;
+  // workspace
+  DevState* st;
+  double* u;       // [n] partial norms
+  double* uref;    // [n] norms at the last exact computation
+  int32_t* cols;   // [KMAX] positions: j* then the sorted candidates
+  int32_t* mdst;   // [2*KMAX] permutation moves: column mdst[e] <- column msrc[e]
+  int32_t* msrc;
+  double* Gp;      // [gram_chunks][kmax*kmax] partial Gram matrices (packed upper)
+  double* G;       // [kmax*kmax] packed upper Gram matrix
+  double* T;       // [KMAX*KMAX] compact-WY T, column-major, ld KMAX
+  double* Wp;      // [wchunks][kmax][n] partial V^T A22
+  double* W;       // [kmax][n] T^T V^T A22
+  int32_t gram_chunks;  // CTAs of k_gram (= partial Gram matrices)
+  int32_t wchunks;      // most row chunks of the W phase
+  int32_t w_units;      // target work units of the W phase (same in k_trail_w and k_trail_wreduce)
+  int32_t pad0;
+  // optional trace
+  StepRecord* trace;
+  int32_t* traceJ;
+  int64_t trace_cap;
+};
+
+__device__ __forceinline__ double ld(const double* p) { return *p; }
+
+// ---------------------------------------------------------------------------
+// a1: column norms u_j = ||a_j||, uref = u, perm = identity, anorm = max u.
+// One warp per column, lanes stride the rows (coalesced).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_colnorm_init(Params P) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = warp; j < P.n; j += nwarps) {
+    const double* a = P.A + j * P.lda;
+    double s = 0.0;
+    for (int64_t i = lane; i < P.m; i += 32) {
+      double x = a[i];
+      s = fma(x, x, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      double nr = sqrt(s);
+      P.u[j] = nr;
+      P.uref[j] = nr;
+      P.perm[j] = (int32_t)j;
+      if (!isfinite(nr)) {
+        P.st->nonfinite = 1;
+      } else {
+        atomicMax(&P.st->anorm_bits, (unsigned long long)__double_as_longlong(nr));
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide helpers (1024-thread select kernel).
+// ---------------------------------------------------------------------------
+struct ArgMax {
+  double v;
+  int64_t p;
+};
+__device__ __forceinline__ bool better(double va, int64_t pa, double vb, int64_t pb) {
+  // larger value first, ties to the lower position
+  return va > vb || (va == vb && pa < pb);
+}
+
+// ---------------------------------------------------------------------------
+// a2/a3: stopping test, argmax, candidate set (one CTA of 1024 threads).
+// Also advances n_s by the previous step's l.
+// ---------------------------------------------------------------------------
+constexpr int SEL_THREADS = 1024;
+
+__device__ int block_sum_int(int v, int* red) {
+  // red: >= 32 ints of shared memory
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  int t = 0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Given a 256-bin histogram in shared memory, find the digit d (scanning from
+// the top when `desc`, else from the bottom) holding the krem-th element;
+// returns d and writes the count of elements strictly before bin d to *before.
+__device__ int hist_pick(const int* hist, int krem, bool desc, int* s_out) {
+  // executed by warp 0
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    // each lane owns 8 consecutive bins in scan order
+    int c[8];
+    int tot = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int bin = desc ? 255 - (lane * 8 + q) : lane * 8 + q;
+      c[q] = hist[bin];
+      tot += c[q];
+    }
+    // exclusive scan of tot across lanes
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int excl = incl - tot;
+    bool mine = (excl < krem) && (krem <= incl);
+    unsigned b = __ballot_sync(0xffffffffu, mine);
+    int owner = __ffs(b) - 1;
+    if (lane == owner) {
+      int run = excl;
+      for (int q = 0; q < 8; ++q) {
+        if (run + c[q] >= krem) {
+          int bin = desc ? 255 - (lane * 8 + q) : lane * 8 + q;
+          s_out[0] = bin;
+          s_out[1] = run;
+          break;
+        }
+        run += c[q];
+      }
+    }
+  }
+  __syncthreads();
+  return s_out[0];
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
+  DevState* st = P.st;
+  __shared__ double s_v[32];
+  __shared__ int64_t s_p[32];
+  __shared__ int s_red[40];
+  __shared__ int s_hist[256];
+  __shared__ int s_pick[2];
+  __shared__ int s_ctl[8];
+  __shared__ double s_ctld[4];
+  __shared__ int s_list[KMAX];
+  __shared__ double s_lu[KMAX];
+  __shared__ int s_cnt;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+
+  if (tid == 0) {
+    int go = 1;
+    if (st->done) go = 0;
+    if (go && (st->ns >= P.kmin || (P.max_steps > 0 && st->step >= P.max_steps))) {
+      st->done = 1;
+      go = 0;
+    }
+    s_ctl[0] = go;
+  }
+  __syncthreads();
+  if (!s_ctl[0]) return;
+  const int64_t ns = st->ns, n = P.n;
+
+  // argmax over u[ns..n), ties to the lowest position
+  double bv = -1.0;
+  int64_t bp = INT64_MAX;
+  for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
+    double x = P.u[j];
+    if (better(x, j, bv, bp)) {
+      bv = x;
+      bp = j;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    int64_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+    if (better(ov, op, bv, bp)) {
+      bv = ov;
+      bp = op;
+    }
+  }
+  if (lane == 0) {
+    s_v[w] = bv;
+    s_p[w] = bp;
+  }
+  __syncthreads();
+  if (w == 0) {
+    bv = s_v[lane];
+    bp = s_p[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int64_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (better(ov, op, bv, bp)) {
+        bv = ov;
+        bp = op;
+      }
+    }
+    if (lane == 0) {
+      const double mu = bv;
+      const int64_t jstar = bp;
+      const int64_t nrem = n - ns;
+      const double anorm = __longlong_as_double((long long)st->anorm_bits);
+      st->anorm = anorm;
+      const double rhs = P.eps1 * anorm;
+      if (st->rank_colmax < 0 && mu <= rhs) st->rank_colmax = ns;
+      int stop = 0;
+      if (st->rank < 0 && sqrt((double)nrem) * mu <= rhs) {
+        st->rank = ns;
+        st->dm_on = 0;
+        if (P.stop_at_rank) stop = 1;
+      }
+      if (stop) {
+        st->done = 1;
+      } else {
+        st->mu = mu;
+        st->jstar = jstar;
+        st->eps_s = P.tau * mu;
+        int64_t kcap = st->dm_on ? P.kmax : 1;
+        if (kcap > P.kmin - ns) kcap = P.kmin - ns;
+        s_ctl[2] = (int)kcap;
+        s_ctld[0] = P.tau * mu;
+        s_ctld[1] = mu;
+        const int64_t rec = st->step;
+        if (P.trace && rec < P.trace_cap) {
+          StepRecord* r = P.trace + rec;
+          r->ns = ns;
+          r->jstar = jstar;
+          r->dm_on = st->dm_on;
+          r->mu = mu;
+          r->eps_s = P.tau * mu;
+          r->nrecomp = 0;
+        }
+        P.cols[0] = (int32_t)jstar;
+      }
+      s_ctl[1] = stop;
+      s_p[0] = jstar;
+    }
+  }
+  __syncthreads();
+  if (s_ctl[1]) return;
+  const int64_t jstar = s_p[0];
+  const int K = s_ctl[2] - 1;  // candidates to keep
+  const double thr = s_ctld[0];
+
+  // count candidates
+  int c = 0;
+  if (K > 0) {
+    for (int64_t j = ns + tid; j < n; j += SEL_THREADS)
+      if (j != jstar && P.u[j] >= thr) ++c;
+  }
+  const int ncand_all = (K > 0) ? block_sum_int(c, s_red) : 0;
+  const int keep = ncand_all < K ? ncand_all : K;
+
+  // threshold key: select the keep-th largest (u desc) key, then positions
+  unsigned long long tkey = 0;  // take keys > tkey, and keys == tkey with pos <= tpos
+  int64_t tpos = INT64_MAX;
+  if (keep > 0 && ncand_all > keep) {
+    unsigned long long prefix = 0, pmask = 0;
+    int krem = keep;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      for (int b = tid; b < 256; b += SEL_THREADS) s_hist[b] = 0;
+      __syncthreads();
+      for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
+        double x = P.u[j];
+        if (j != jstar && x >= thr) {
+          unsigned long long key = (unsigned long long)__double_as_longlong(x);
+          if ((key & pmask) == prefix) atomicAdd(&s_hist[(key >> shift) & 255], 1);
+        }
+      }
+      __syncthreads();
+      int d = hist_pick(s_hist, krem, true, s_pick);
+      krem -= s_pick[1];
+      prefix |= ((unsigned long long)d) << shift;
+      pmask |= 255ull << shift;
+      __syncthreads();
+    }
+    tkey = prefix;
+    // krem = how many with key == tkey to take (lowest positions first)
+    int neq = 0;
+    for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
+      double x = P.u[j];
+      if (j != jstar && x >= thr && (unsigned long long)__double_as_longlong(x) == tkey) ++neq;
+    }
+    neq = block_sum_int(neq, s_red);
+    if (neq > krem) {
+      // krem-th smallest position among the ties (positions < 2^31)
+      uint32_t pprefix = 0, ppmask = 0;
+      int prem = krem;
+      for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int b = tid; b < 256; b += SEL_THREADS) s_hist[b] = 0;
+        __syncthreads();
+        for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
+          double x = P.u[j];
+          if (j != jstar && x >= thr && (unsigned long long)__double_as_longlong(x) == tkey) {
+            uint32_t pk = (uint32_t)j;
+            if ((pk & ppmask) == pprefix) atomicAdd(&s_hist[(pk >> shift) & 255], 1);
+          }
+        }
+        __syncthreads();
+        int d = hist_pick(s_hist, prem, false, s_pick);
+        prem -= s_pick[1];
+        pprefix |= ((uint32_t)d) << shift;
+        ppmask |= 255u << shift;
+        __syncthreads();
+      }
+      tpos = (int64_t)pprefix;
+    }
+  } else if (keep > 0) {
+    tkey = 0;  // take every candidate
+    tpos = INT64_MAX;
+  }
+
+  // gather the kept candidates
+  if (tid == 0) s_cnt = 0;
+  __syncthreads();
+  if (keep > 0) {
+    const bool all = (ncand_all <= keep);
+    for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
+      double x = P.u[j];
+      if (j == jstar || !(x >= thr)) continue;
+      unsigned long long key = (unsigned long long)__double_as_longlong(x);
+      bool take = all || key > tkey || (key == tkey && j <= tpos);
+      if (take) {
+        int slot = atomicAdd(&s_cnt, 1);
+        if (slot < KMAX) {
+          s_list[slot] = (int)j;
+          s_lu[slot] = x;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int got = s_cnt;
+  // order by (u desc, position asc): rank counting
+  if (tid < got && got <= KMAX) {
+    double xv = s_lu[tid];
+    int xp = s_list[tid];
+    int r = 0;
+    for (int b = 0; b < got; ++b) {
+      if (better(s_lu[b], s_list[b], xv, xp)) ++r;
+    }
+    P.cols[1 + r] = xp;
+  }
+  if (tid == 0) {
+    int bad = (got != keep);
+    st->kc = 1 + keep;
+    st->ncand_all = ncand_all;
+    if (bad) {
+      st->nonfinite = 2;  // internal inconsistency
+      st->done = 1;
+    }
+    const int64_t rec = st->step;
+    if (P.trace && rec < P.trace_cap) {
+      P.trace[rec].ncand_all = ncand_all;
+      P.trace[rec].ncand = keep;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a4: Gram matrix of the kc = 1 + |I| gathered columns over rows n_s..m-1.
+// Each CTA owns row chunks (grid-stride) and writes a partial upper triangle;
+// k_gram_reduce sums the partials in a fixed order (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int GRAM_ROWS = 64;  // rows staged per pass
+
+__global__ void __launch_bounds__(256) k_gram(Params P) {
+  const DevState* st = P.st;
+  if (st->done) return;
+  const int kc = st->kc;
+  if (kc <= 1) return;
+  const int64_t ns = st->ns, m = P.m;
+  const int64_t mr = m - ns;
+  extern __shared__ double smg[];  // [kc][GRAM_ROWS + 1]
+  const int LDS = GRAM_ROWS + 1;
+  const int npairs = kc * (kc + 1) / 2;
+  double acc[(KMAX * (KMAX + 1) / 2 + 255) / 256];
+  const int nper = (npairs + blockDim.x - 1) / blockDim.x;
+  for (int q = 0; q < nper; ++q) acc[q] = 0.0;
+  const int64_t nchunks = (mr + GRAM_ROWS - 1) / GRAM_ROWS;
+  // chunk c of this CTA: c = blockIdx.x, blockIdx.x + gridDim.x, ...
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int64_t r0 = ns + c * GRAM_ROWS;
+    const int rows = (int)min((int64_t)GRAM_ROWS, m - r0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kc * GRAM_ROWS; e += blockDim.x) {
+      int a = e / GRAM_ROWS, i = e % GRAM_ROWS;
+      double x = 0.0;
+      if (i < rows) x = P.A[(int64_t)P.cols[a] * P.lda + r0 + i];
+      smg[a * LDS + i] = x;
+    }
+    __syncthreads();
+    for (int q = 0; q < nper; ++q) {
+      int e = threadIdx.x + q * blockDim.x;
+      if (e >= npairs) break;
+      // e -> (a, b) with a <= b, column-major upper triangle enumeration
+      int b = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      while ((b + 1) * (b + 2) / 2 <= e) ++b;
+      while (b * (b + 1) / 2 > e) --b;
+      int a = e - b * (b + 1) / 2;
+      const double* xa = smg + a * LDS;
+      const double* xb = smg + b * LDS;
+      double s = acc[q];
+      for (int i = 0; i < rows; ++i) s = fma(xa[i], xb[i], s);
+      acc[q] = s;
+    }
+  }
+  double* out = P.Gp + (int64_t)blockIdx.x * P.kmax * P.kmax;
+  for (int q = 0; q < nper; ++q) {
+    int e = threadIdx.x + q * blockDim.x;
+    if (e < npairs) out[e] = acc[q];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_gram_reduce(Params P) {
+  const DevState* st = P.st;
+  if (st->done) return;
+  const int kc = st->kc;
+  if (kc <= 1) return;
+  const int npairs = kc * (kc + 1) / 2;
+  const int64_t mr = P.m - st->ns;
+  const int64_t nchunks = (mr + GRAM_ROWS - 1) / GRAM_ROWS;
+  const int nparts = (int)min((int64_t)P.gram_chunks, nchunks);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npairs; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nparts; ++c) s += P.Gp[(int64_t)c * P.kmax * P.kmax + e];
+    P.G[e] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a5/a6: greedy DM pick (Alg. 1 loop) and the pairwise-swap permutation.
+// One CTA; warp 0 does the sequential parts.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int tri(int a, int b) {  // packed upper index, a <= b
+  return b * (b + 1) / 2 + a;
+}
+
+__global__ void __launch_bounds__(256) k_pick(Params P) {
+  DevState* st = P.st;
+  if (st->done) return;
+  extern __shared__ double s_th[];  // kc*(kc+1)/2 packed cosines
+  __shared__ double s_d[KMAX];
+  __shared__ int s_J[KMAX];
+  __shared__ int s_k;
+  __shared__ int s_pos[2 * KMAX], s_cont[2 * KMAX];
+  __shared__ int s_np;
+  __shared__ double s_mv[2 * KMAX][2];
+  __shared__ int s_mvp[2 * KMAX];
+  const int kc = st->kc;
+  const int64_t ns = st->ns;
+  const int tid = threadIdx.x, lane = tid & 31;
+
+  if (kc > 1) {
+    const int npairs = kc * (kc + 1) / 2;
+    for (int a = tid; a < kc; a += blockDim.x) s_d[a] = sqrt(P.G[tri(a, a)]);
+    __syncthreads();
+    for (int e = tid; e < npairs; e += blockDim.x) {
+      int b = 0;
+      while ((b + 1) * (b + 2) / 2 <= e) ++b;
+      int a = e - b * (b + 1) / 2;
+      double g = P.G[e];
+      double d = s_d[a] * s_d[b];
+      s_th[e] = (d > 0.0) ? g / d : 1.0;
+      if (!(d > 0.0)) s_th[e] = 1.0;
+    }
+    __syncthreads();
+  }
+  if (tid < 32) {
+    double dlt = P.delta;
+    if (P.sdd && kc > 1) {
+      double dm = P.tau * P.tau / (double)((kc - 1) > 1 ? (kc - 1) : 1);
+      if (dm < dlt) dlt = dm;
+    }
+    int k = 1;
+    if (lane == 0) s_J[0] = 0;
+    __syncwarp();
+    for (int a = 1; a < kc; ++a) {
+      bool ok = true;
+      for (int b = lane; b < k; b += 32) {
+        int jb = s_J[b];
+        int lo = jb < a ? jb : a, hi = jb < a ? a : jb;
+        double th = fabs(s_th[tri(lo, hi)]);
+        if (s_d[a] <= 0.0 || s_d[jb] <= 0.0) th = 1.0;
+        if (!(th < dlt)) ok = false;
+      }
+      bool all = __all_sync(0xffffffffu, ok);
+      if (all) {
+        if (lane == 0) s_J[k] = a;
+        ++k;
+      }
+      __syncwarp();
+    }
+    // permutation by pairwise swaps: position ns+t <-> current position of J_t
+    if (lane == 0) {
+      int np = 0;
+      for (int t = 0; t < k; ++t) {
+        s_pos[np] = (int)(ns + t);
+        s_cont[np] = (int)(ns + t);
+        ++np;
+      }
+      for (int t = 0; t < k; ++t) {
+        int pj = P.cols[s_J[t]];
+        if (pj >= ns + k) {
+          s_pos[np] = pj;
+          s_cont[np] = pj;
+          ++np;
+        }
+      }
+      s_np = np;
+      s_k = k;
+    }
+    __syncwarp();
+    const int np = s_np;
+    for (int t = 0; t < k; ++t) {
+      const int orig = P.cols[s_J[t]];  // position of J_t at step start
+      // find the entry whose content is orig
+      int found = -1;
+      for (int e = lane; e < np; e += 32)
+        if (s_cont[e] == orig) found = e;
+      unsigned b = __ballot_sync(0xffffffffu, found >= 0);
+      if (b == 0u) {  // cannot happen: every selected column is in the list
+        if (lane == 0) st->nonfinite = 3;
+        continue;
+      }
+      int src_lane = __ffs(b) - 1;
+      int e_p = __shfl_sync(0xffffffffu, found, src_lane);
+      if (lane == 0) {
+        int tmp = s_cont[t];  // entry t is position ns+t
+        s_cont[t] = s_cont[e_p];
+        s_cont[e_p] = tmp;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const int k = s_k;
+  const int np = s_np;
+  // compact the moves and permute u, uref, perm
+  if (tid == 0) {
+    int nm = 0;
+    for (int e = 0; e < np; ++e) {
+      if (s_cont[e] != s_pos[e]) {
+        P.mdst[nm] = s_pos[e];
+        P.msrc[nm] = s_cont[e];
+        s_mvp[nm] = e;
+        ++nm;
+      }
+    }
+    st->npairs = nm;
+    st->k = k;
+    s_np = nm;
+  }
+  __syncthreads();
+  const int nm = s_np;
+  for (int q = tid; q < nm; q += blockDim.x) {
+    int e = s_mvp[q];
+    int src = s_cont[e];
+    s_mv[q][0] = P.u[src];
+    s_mv[q][1] = P.uref[src];
+    s_mvp[q] = P.perm[src];
+  }
+  __syncthreads();
+  for (int q = tid; q < nm; q += blockDim.x) {
+    int dst = P.mdst[q];
+    P.u[dst] = s_mv[q][0];
+    P.uref[dst] = s_mv[q][1];
+    P.perm[dst] = s_mvp[q];
+  }
+  __syncthreads();
+  if (P.trace && st->step < P.trace_cap) {
+    if (tid == 0) P.trace[st->step].k = k;
+    if (P.traceJ) {
+      for (int t = tid; t < P.kmax; t += blockDim.x)
+        P.traceJ[st->step * P.kmax + t] = (t < k) ? P.perm[ns + t] : -1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a6: apply the column moves to A (whole columns, rows 0..m-1).  Each CTA
+// stages 32 rows of every moved column in shared memory, then writes them to
+// their destinations, so overlapping sources and destinations are safe.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_permute(Params P) {
+  const DevState* st = P.st;
+  if (st->done) return;
+  const int nm = st->npairs;
+  if (nm == 0) return;
+  extern __shared__ double s[];  // [2*kmax][33]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  for (int64_t r0 = (int64_t)blockIdx.x * 32; r0 < P.m; r0 += (int64_t)gridDim.x * 32) {
+    const int64_t i = r0 + lane;
+    __syncthreads();
+    for (int e = w; e < nm; e += nw) s[e * 33 + lane] = (i < P.m) ? P.A[(int64_t)P.msrc[e] * P.lda + i] : 0.0;
+    __syncthreads();
+    for (int e = w; e < nm; e += nw)
+      if (i < P.m) P.A[(int64_t)P.mdst[e] * P.lda + i] = s[e * 33 + lane];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a7/a8: Householder panel with break check and the compact-WY T, on one
+// thread-block cluster.  CTA r of the cluster owns a contiguous slice of the
+// panel rows and only ever touches those rows.  Per reflector one cluster
+// barrier: every CTA reduces x^T [A panel] over its rows (x = current column
+// below the pivot) plus the pivot-row values, publishes the partial vector in
+// its shared memory, and after the barrier sums all partials (distributed
+// shared memory) in the same order, so every CTA derives identical scalars.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P) {
+  cg::cluster_group cluster = cg::this_cluster();
+  DevState* st = P.st;
+  if (st->done) return;  // uniform across the cluster
+  const int cs = (int)cluster.num_blocks();
+  const int crank = (int)cluster.block_rank();
+  const int64_t ns = st->ns, m = P.m, lda = P.lda;
+  const int k = st->k;
+  const int64_t mr = m - ns;
+  const int64_t rpc = (mr + cs - 1) / cs;
+  const int64_t r0 = ns + (int64_t)crank * rpc;
+  const int64_t r1 = min(m, r0 + rpc);
+  __shared__ double s_slot[2][2 * KMAX];
+  __shared__ double s_tot[2 * KMAX];
+  __shared__ double s_y[KMAX];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int nw = PANEL_THREADS / 32;
+  double* A = P.A;
+  const double eps_s = st->eps_s;
+  int lacc = k;
+  for (int l = 0; l < k; ++l) {
+    const int64_t p = ns + l;  // pivot row and column
+    const double* x = A + p * lda;
+    double* slot = s_slot[l & 1];
+    const int64_t i0 = max(r0, p + 1);
+    const bool own_p = (p >= r0 && p < r1);
+    for (int t = w; t < k; t += nw) {
+      const double* ct = A + (ns + t) * lda;
+      double acc = 0.0;
+      for (int64_t i = i0 + lane; i < r1; i += 32) acc = fma(x[i], ct[i], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        slot[t] = acc;
+        slot[KMAX + t] = own_p ? ct[p] : 0.0;
+      }
+    }
+    cluster.sync();
+    for (int e = tid; e < 2 * KMAX; e += PANEL_THREADS) {
+      int t = (e < KMAX) ? e : e - KMAX;
+      if (t >= k) continue;
+      double s = 0.0;
+      for (int c = 0; c < cs; ++c) {
+        const double* rs = cluster.map_shared_rank(&s_slot[l & 1][0], c);
+        s += rs[e];
+      }
+      s_tot[e] = s;
+    }
+    __syncthreads();
+    const double alpha = s_tot[KMAX + l];
+    const double s2 = s_tot[l];
+    const bool check = (l >= 1) && !P.no_break && (P.check_last ? (l < k) : (l + 1 < k));
+    if (check) {
+      double nrm = sqrt(alpha * alpha + s2);
+      if (nrm < eps_s) {
+        lacc = l;
+        break;
+      }
+    }
+    double beta, ht, rden;
+    if (s2 == 0.0) {
+      beta = alpha;
+      ht = 0.0;
+      rden = 0.0;
+    } else {
+      double nrm = sqrt(alpha * alpha + s2);
+      beta = (alpha >= 0.0) ? -nrm : nrm;
+      ht = (beta - alpha) / beta;
+      rden = 1.0 / (alpha - beta);
+    }
+    // compact-WY T column l (rank-0 CTA): y_t = v_t^T v_l for t < l
+    if (crank == 0) {
+      for (int t = tid; t < l; t += PANEL_THREADS) s_y[t] = s_tot[KMAX + t] + s_tot[t] * rden;
+      __syncthreads();
+      double* Tc = P.T + (int64_t)l * KMAX;
+      for (int t = tid; t < l; t += PANEL_THREADS) {
+        double s = 0.0;
+        for (int q = t; q < l; ++q) s += P.T[(int64_t)q * KMAX + t] * s_y[q];
+        Tc[t] = (ht == 0.0) ? 0.0 : -ht * s;
+      }
+      if (tid == 0) {
+        Tc[l] = ht;
+        P.htau[p] = ht;
+      }
+    }
+    // apply H_l to the remaining panel columns (own rows)
+    if (ht != 0.0) {
+      for (int t = l + 1 + w; t < k; t += nw) {
+        double* ct = A + (ns + t) * lda;
+        const double wt = s_tot[KMAX + t] + s_tot[t] * rden;
+        const double hw = ht * wt;
+        for (int64_t i = i0 + lane; i < r1; i += 32) ct[i] = fma(-hw, x[i] * rden, ct[i]);
+        if (own_p && lane == 0) ct[p] -= hw;
+      }
+    }
+    __syncthreads();
+    // store v_l and beta
+    {
+      double* xc = A + p * lda;
+      if (ht != 0.0)
+        for (int64_t i = i0 + tid; i < r1; i += PANEL_THREADS) xc[i] = xc[i] * rden;
+      if (own_p && tid == 0) xc[p] = beta;
+    }
+    __syncthreads();
+  }
+  if (crank == 0 && tid == 0) {
+    st->l = lacc;
+    if (P.trace && st->step < P.trace_cap) P.trace[st->step].l = lacc;
+  }
+  cluster.sync();  // no CTA leaves while others may still read its shared memory
+}
+
+// ---------------------------------------------------------------------------
+// a9: trailing update A22 -= V (T^T (V^T A22)), A22 = A[ns:m, ns+k:n].
+// V (mr x l) is unit lower trapezoidal, stored below the diagonal of the
+// panel columns.  Three kernels: partial W = V^T A22 over row chunks,
+// W = T^T sum(partials), A22 -= V W.  FFMA64 throughout.
+// ---------------------------------------------------------------------------
+constexpr int TW_COLS = 32;   // columns per W work unit
+constexpr int TW_SUB = 32;    // rows staged per pass
+constexpr int TU_ROWS = 64;   // update tile rows
+constexpr int TU_COLS = 64;   // update tile cols
+constexpr int TU_KC = 32;     // reflectors per staged chunk
+
+__device__ __forceinline__ double vget(const double* A, int64_t lda, int64_t ns, int64_t r, int t) {
+  // V(r, t), r relative to ns
+  if (r < t) return 0.0;
+  if (r == t) return 1.0;
+  return A[(ns + t) * lda + ns + r];
+}
+
+// number of row chunks for the W phase (same on every CTA)
+__device__ __forceinline__ int64_t wchunk_rows(int64_t mr, int64_t ncoltiles, int wchunks, int target_units) {
+  int64_t want = (target_units + ncoltiles - 1) / ncoltiles;
+  if (want > wchunks) want = wchunks;
+  if (want < 1) want = 1;
+  int64_t rows = (mr + want - 1) / want;
+  rows = (rows + TW_SUB - 1) / TW_SUB * TW_SUB;
+  if (rows < TW_SUB) rows = TW_SUB;
+  return rows;
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P) {
+  const DevState* st = P.st;
+  if (st->done) return;
+  const int l = st->l, k = st->k;
+  const int64_t ns = st->ns, m = P.m, lda = P.lda;
+  const int64_t j0 = ns + k;
+  const int64_t n2 = P.n - j0, mr = m - ns;
+  if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  const int64_t nct = (n2 + TW_COLS - 1) / TW_COLS;
+  const int64_t rows_per = wchunk_rows(mr, nct, P.wchunks, P.w_units);
+  const int64_t nrc = (mr + rows_per - 1) / rows_per;
+  const int64_t units = nct * nrc;
+  __shared__ double s_a[TW_SUB][TW_COLS + 1];
+  __shared__ double s_v[TW_SUB][KMAX + 1];
+  const int tid = threadIdx.x;
+  const int c = tid % TW_COLS;       // column within the tile
+  const int tg = tid / TW_COLS;      // 0..7 reflector group
+  const int TG = GEMM_THREADS / TW_COLS;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t ct = u % nct, rc = u / nct;
+    const int64_t cbase = j0 + ct * TW_COLS;
+    const int ncols = (int)min((int64_t)TW_COLS, P.n - cbase);
+    const int64_t rbeg = rc * rows_per, rend = min(mr, rbeg + rows_per);
+    constexpr int NQ = KMAX / (GEMM_THREADS / TW_COLS);
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    for (int64_t r0 = rbeg; r0 < rend; r0 += TW_SUB) {
+      const int rows = (int)min((int64_t)TW_SUB, rend - r0);
+      __syncthreads();
+      for (int e = tid; e < TW_SUB * TW_COLS; e += GEMM_THREADS) {
+        int cc = e / TW_SUB, rr = e % TW_SUB;
+        double v = 0.0;
+        if (rr < rows && cc < ncols) v = P.A[(cbase + cc) * lda + ns + r0 + rr];
+        s_a[rr][cc] = v;
+      }
+      for (int e = tid; e < TW_SUB * l; e += GEMM_THREADS) {
+        int t = e / TW_SUB, rr = e % TW_SUB;
+        s_v[rr][t] = (rr < rows) ? vget(P.A, lda, ns, r0 + rr, t) : 0.0;
+      }
+      __syncthreads();
+      for (int rr = 0; rr < rows; ++rr) {
+        const double a = s_a[rr][c];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int t = tg + q * TG;
+          if (t < l) acc[q] = fma(s_v[rr][t], a, acc[q]);
+        }
+      }
+    }
+    if (c < ncols) {
+      double* out = P.Wp + rc * (int64_t)P.kmax * P.n;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int t = tg + q * TG;
+        if (t < l) out[(int64_t)t * P.n + cbase + c] = acc[q];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P) {
+  const DevState* st = P.st;
+  if (st->done) return;
+  const int l = st->l, k = st->k;
+  const int64_t ns = st->ns, j0 = ns + k;
+  const int64_t n2 = P.n - j0, mr = P.m - ns;
+  if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  const int64_t nct = (n2 + TW_COLS - 1) / TW_COLS;
+  const int64_t rows_per = wchunk_rows(mr, nct, P.wchunks, P.w_units);
+  const int64_t nrc = (mr + rows_per - 1) / rows_per;
+  __shared__ double s_w[KMAX][TW_COLS + 1];
+  const int tid = threadIdx.x;
+  const int c = tid % TW_COLS, tg = tid / TW_COLS, TG = GEMM_THREADS / TW_COLS;
+  for (int64_t ct = blockIdx.x; ct < nct; ct += gridDim.x) {
+    const int64_t cbase = j0 + ct * TW_COLS;
+    const bool ok = (cbase + c) < P.n;
+    __syncthreads();
+    for (int t = tg; t < l; t += TG) {
+      double s = 0.0;
+      if (ok)
+        for (int64_t q = 0; q < nrc; ++q) s += P.Wp[q * (int64_t)P.kmax * P.n + (int64_t)t * P.n + cbase + c];
+      s_w[t][c] = s;
+    }
+    __syncthreads();
+    for (int t = tg; t < l; t += TG) {
+      // (T^T W)_t = sum_{q <= t} T(q, t) W_q
+      double s = 0.0;
+      const double* Tc = P.T + (int64_t)t * KMAX;
+      for (int q = 0; q <= t; ++q) s = fma(Tc[q], s_w[q][c], s);
+      if (ok) P.W[(int64_t)t * P.n + cbase + c] = s;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P) {
+  const DevState* st = P.st;
+  if (st->done) return;
+  const int l = st->l, k = st->k;
+  const int64_t ns = st->ns, m = P.m, lda = P.lda;
+  const int64_t j0 = ns + k;
+  const int64_t n2 = P.n - j0, mr = m - ns;
+  if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  const int64_t nrt = (mr + TU_ROWS - 1) / TU_ROWS;
+  const int64_t nct = (n2 + TU_COLS - 1) / TU_COLS;
+  const int64_t units = nrt * nct;
+  __shared__ double s_v[TU_KC][TU_ROWS];
+  __shared__ double s_w[TU_KC][TU_COLS];
+  const int tid = threadIdx.x;
+  const int tr = tid % 16, tc = tid / 16;  // 16 x 16 threads, 4 x 4 outputs each
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t rt = u % nrt, ct = u / nrt;
+    const int64_t rbase = rt * TU_ROWS;  // relative to ns
+    const int64_t cbase = j0 + ct * TU_COLS;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int t0 = 0; t0 < l; t0 += TU_KC) {
+      const int kcnt = min(TU_KC, l - t0);
+      __syncthreads();
+      for (int e = tid; e < TU_KC * TU_ROWS; e += GEMM_THREADS) {
+        int t = e / TU_ROWS, r = e % TU_ROWS;
+        double v = 0.0;
+        if (t < kcnt && rbase + r < mr) v = vget(P.A, lda, ns, rbase + r, t0 + t);
+        s_v[t][r] = v;
+      }
+      for (int e = tid; e < TU_KC * TU_COLS; e += GEMM_THREADS) {
+        int t = e / TU_COLS, c = e % TU_COLS;
+        double v = 0.0;
+        if (t < kcnt && cbase + c < P.n) v = P.W[(int64_t)(t0 + t) * P.n + cbase + c];
+        s_w[t][c] = v;
+      }
+      __syncthreads();
+      for (int t = 0; t < kcnt; ++t) {
+        double vv[4], ww[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) vv[i] = s_v[t][tr + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ww[j] = s_w[t][tc + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(vv[i], ww[j], acc[i][j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t col = cbase + tc + 16 * j;
+      if (col >= P.n) continue;
+      double* a = P.A + col * lda + ns;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int64_t r = rbase + tr + 16 * i;
+        if (r < mr) a[r] -= acc[i][j];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a10/a11: partial norm update.  One warp per column j >= ns + l:
+//   rejected panel columns (ns+l <= j < ns+k): recompute;
+//   trailing columns: block downdate over rows ns..ns+l-1, recompute when
+//   t (u/uref)^2 <= sqrt(eps).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_downdate(Params P) {
+  DevState* st = P.st;
+  if (st->done) return;
+  const int l = st->l, k = st->k;
+  const int64_t ns = st->ns, m = P.m, lda = P.lda;
+  const int64_t nsn = ns + l;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const double sqeps = sqrt(EPS);
+  int nrec = 0;
+  for (int64_t j = ns + gw; j < P.n; j += nwarps) {
+    const double* a = P.A + j * lda;
+    if (j < nsn) {
+      if (lane == 0) P.u[j] = 0.0;
+      continue;
+    }
+    bool recompute = (j < ns + k);
+    double uj = P.u[j];
+    double t = 0.0;
+    if (!recompute) {
+      if (uj == 0.0) continue;
+      double q = 0.0;
+      for (int64_t r = ns + lane; r < nsn; r += 32) {
+        double x = a[r] / uj;
+        q = fma(x, x, q);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      t = 1.0 - q;
+      if (t < 0.0) t = 0.0;
+      double ratio = uj / P.uref[j];
+      double test = t * ratio * ratio;
+      recompute = (test <= sqeps);
+    }
+    if (recompute) {
+      double s = 0.0;
+      for (int64_t r = nsn + lane; r < m; r += 32) s = fma(a[r], a[r], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        double nr = sqrt(s);
+        P.u[j] = nr;
+        P.uref[j] = nr;
+        ++nrec;
+      }
+    } else if (lane == 0) {
+      P.u[j] = uj * sqrt(t);
+    }
+  }
+  if (lane == 0 && nrec && P.trace && st->step < P.trace_cap)
+    atomicAdd((unsigned long long*)&P.trace[st->step].nrecomp, (unsigned long long)nrec);
+}
+
+// a11: end of a block step, n_s += l.  Runs after every other kernel of the
+// step, so all of them saw the same n_s.
+__global__ void k_step_end(Params P) {
+  DevState* st = P.st;
+  if (st->done) return;
+  st->ns += st->l;
+  st->step += 1;
+}
+
+__global__ void k_state_init(Params P) {
+  DevState* st = P.st;
+  st->ns = 0;
+  st->step = 0;
+  st->rank = -1;
+  st->rank_colmax = -1;
+  st->anorm_bits = 0ull;
+  st->done = 0;
+  st->dm_on = 1;
+  st->nonfinite = 0;
+  st->k = 0;
+  st->l = 0;
+  st->kc = 0;
+  st->npairs = 0;
+}
+
+}  // namespace qrdm

@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads without a GPU, and exports every function
+include/qrdm.h declares; argument checks run on the host (no compute)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qrdm.h")
+
+
+def declared_functions() -> list[str]:
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(qrdm_[a-z_]+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_03138_gb300 import _binding
+
+    return _binding.load()
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    assert "qrdm_factor" in names and "qrdm_workspace_size" in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2106_03138_gb300 import _binding
+
+    so = _binding.lib_path()
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for name in declared_functions():
+        assert name in exported, name
+        assert hasattr(lib, name)
+    assert set(_binding.EXPORTS) == set(declared_functions())
+
+
+def test_struct_layouts():
+    from paper_2106_03138_gb300 import _binding
+
+    assert ctypes.sizeof(_binding.qrdm_opts) == 32
+    assert ctypes.sizeof(_binding.qrdm_info) == 32
+    assert ctypes.sizeof(_binding.qrdm_step_record) == 80
+
+
+def test_workspace_size_and_argument_checks(lib):
+    from paper_2106_03138_gb300 import _binding as b
+
+    n1 = b.qrdm_workspace_size(256, 256, 32)
+    n2 = b.qrdm_workspace_size(4096, 4096, 64)
+    assert 0 < n1 < n2
+    with pytest.raises(ValueError):
+        b.qrdm_workspace_size(-1, 4, 4)
+    with pytest.raises(ValueError):
+        b.qrdm_workspace_size(4, 4, 0)
+    with pytest.raises(ValueError):
+        b.qrdm_workspace_size(4, 4, 129)
+    # invalid arguments are rejected before any CUDA call (LAPACK-style -i)
+    fake = 1 << 20  # never dereferenced
+    rc, _ = b.qrdm_factor(fake, -1, 4, 4, 0.5, 0.5, 4, fake, fake, None, fake, 1 << 30, 0)
+    assert rc == -1
+    rc, _ = b.qrdm_factor(fake, 4, 4, 3, 0.5, 0.5, 4, fake, fake, None, fake, 1 << 30, 0)
+    assert rc == -4
+    rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.0, 0.5, 4, fake, fake, None, fake, 1 << 30, 0)
+    assert rc == -5
+    rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 1.5, 4, fake, fake, None, fake, 1 << 30, 0)
+    assert rc == -6
+    rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 0, fake, fake, None, fake, 1 << 30, 0)
+    assert rc == -7
+    rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 4, 0, fake, None, fake, 1 << 30, 0)
+    assert rc == -8
+    o = b.qrdm_opts()
+    o.eps1_mode = 7
+    rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 4, fake, fake, o, fake, 1 << 30, 0)
+    assert rc == -11
+    assert b.qrdm_strerror(2).startswith("the matrix")
+    assert lib.qrdm_version() >= 100

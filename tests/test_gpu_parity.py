@@ -1,0 +1,258 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs, element by element at sizes the oracle finishes in
+seconds, and on sampled outputs plus invariants at the full benchmark sizes."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_03138_gb300 import inputs
+from tests._helpers import EPS, factorization_errors
+from tests._parity import compare
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2106_03138_gb300 as q  # noqa: E402
+
+
+def run_gpu(A, tau, delta, kmax, **kw):
+    dA = q.colmajor(A)
+    f = q.factor(dA, tau, delta, kmax, trace=True, **kw)
+    torch.cuda.synchronize()
+    return {
+        "A": dA.cpu().numpy(),
+        "htau": f.htau.cpu().numpy(),
+        "perm": f.perm.cpu().numpy().astype(np.int64),
+        "trace": f.trace,
+        "J": f.J.astype(np.int64),
+        "rank": f.rank,
+        "rank_colmax": f.rank_colmax,
+        "nsteps": f.nsteps,
+    }
+
+
+def _mat(kind, m, n, seed):
+    if kind == "gap":
+        return inputs.from_spectrum(m, n, inputs.sigma_gap(min(m, n), min(m, n) // 2), seed)
+    if kind == "geo":
+        return inputs.from_spectrum(m, n, inputs.sigma_geometric(min(m, n), 1e-15), seed)
+    if kind == "geo12":
+        return inputs.from_spectrum(m, n, inputs.sigma_geometric(min(m, n), 1e-12), seed)
+    if kind == "dense":
+        return inputs.random_dense(m, n, seed)
+    raise ValueError(kind)
+
+
+PARITY = [
+    # (kind, m, n, tau, delta, kmax)
+    ("gap", 256, 256, 0.9, 0.9, 32),  # the 256 x 256 rank-128 workload
+    ("gap", 256, 256, 0.15, 0.9, 64),
+    ("gap", 256, 256, 0.5, 0.3, 8),
+    ("gap", 256, 256, 1.0, 1.0, 128),
+    ("gap", 256, 256, 0.9, 0.9, 1),
+    ("dense", 300, 257, 0.9, 0.9, 32),
+    ("dense", 300, 257, 0.15, 0.95, 128),
+    ("geo12", 700, 130, 0.2, 0.95, 16),
+    ("geo12", 90, 333, 0.6, 0.8, 7),
+    ("geo", 513, 513, 0.15, 0.9, 64),
+    ("geo", 1024, 1024, 0.9, 0.9, 32),
+    ("geo", 1100, 380, 0.15, 0.9, 64),
+    ("dense", 64, 64, 0.3, 0.99, 128),
+    ("dense", 33, 65, 0.5, 0.5, 3),
+]
+
+
+@pytest.mark.parametrize("kind,m,n,tau,delta,kmax", PARITY)
+def test_parity_with_oracle(kind, m, n, tau, delta, kmax):
+    A = _mat(kind, m, n, 17 + m + n)
+    o = O.qrdm(A, tau, delta, kmax)
+    g = run_gpu(A, tau, delta, kmax)
+    rep = compare(A, g, o)
+    res, orth = factorization_errors(A, g["A"], g["htau"], g["perm"])
+    assert res <= 1e-13 and orth <= 1e-13, (res, orth)
+    assert rep["ncmp"] >= 1
+
+
+@pytest.mark.parametrize(
+    "opts",
+    [dict(stop_at_rank=True), dict(check_last=True), dict(no_break=True), dict(sdd=True), dict(eps1_mode=1),
+     dict(max_steps=3)],
+    ids=lambda d: next(iter(d)),
+)
+def test_parity_options(opts):
+    A = inputs.named("gap256").build()
+    o = O.qrdm(A, 0.9, 0.9, 32, **opts)
+    g = run_gpu(A, 0.9, 0.9, 32, **opts)
+    rep = compare(A, g, o)
+    # identical decisions give identical rank and step count (compare checks
+    # both); past a tie only the columns before it are compared
+    assert rep["ncmp"] >= min(128, int(o["trace"]["l"].sum()))
+    if "stop_at_rank" in opts:
+        assert np.all(g["htau"][g["rank"]:] == 0.0)
+        assert int(g["trace"]["l"].sum()) == g["rank"]
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (1, 5), (5, 1), (2, 2), (3, 7), (7, 3), (31, 33), (65, 64)])
+def test_small_shapes(m, n):
+    A = inputs.random_dense(m, n, 3 * m + n)
+    for kmax in (1, 4, 128):
+        o = O.qrdm(A, 0.5, 0.9, kmax)
+        g = run_gpu(A, 0.5, 0.9, kmax)
+        compare(A, g, o)
+        res, orth = factorization_errors(A, g["A"], g["htau"], g["perm"])
+        assert res <= 1e-14 and orth <= 1e-14
+
+
+def test_structured_inputs():
+    """Zero matrix, zero columns, duplicate columns (exact ties broken by position)."""
+    rng = np.random.default_rng(9)
+    Z = np.zeros((10, 6), order="F")
+    B = np.asfortranarray(rng.standard_normal((40, 12)))
+    B[:, [2, 7]] = 0.0
+    a = rng.standard_normal(40)
+    D = np.asfortranarray(np.stack([a, 2 * a, a, -a, rng.standard_normal(40), a], axis=1))
+    for A in (Z, B, D):
+        for kmax in (1, 5):
+            o = O.qrdm(A, 0.5, 0.9, kmax)
+            g = run_gpu(A, 0.5, 0.9, kmax)
+            compare(A, g, o)
+            assert g["rank"] == o["rank"]
+
+
+def test_empty_and_nonfinite():
+    for m, n in ((0, 0), (0, 5), (4, 0)):
+        dA = torch.zeros((m, n), dtype=torch.float64, device="cuda").t().contiguous().t()
+        f = q.factor(dA, 0.5, 0.5, 4)
+        assert f.rank == 0
+        assert f.perm.cpu().tolist() == list(range(n))
+    A = inputs.random_dense(20, 10, 1)
+    A[3, 4] = np.inf
+    dA = q.colmajor(A)
+    before = dA.clone()
+    with pytest.raises(q.QRDMError) as ei:
+        q.factor(dA, 0.5, 0.5, 4)
+    assert ei.value.code == q.QRDM_ERR_NONFINITE
+    assert torch.equal(torch.nan_to_num(dA, posinf=0), torch.nan_to_num(before, posinf=0))
+
+
+def test_leading_dimension_and_stream():
+    """lda > m (a submatrix of a larger allocation) on a non-default stream."""
+    A = inputs.from_spectrum(200, 150, inputs.sigma_geometric(150, 1e-10), 5)
+    big = torch.zeros((250, 150), dtype=torch.float64, device="cuda").t().contiguous().t()
+    big[:200] = torch.from_numpy(A).cuda()
+    sub = big[:200]
+    assert sub.stride() == (1, 250)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        f = q.factor(sub, 0.5, 0.9, 16, trace=True)
+    s.synchronize()
+    o = O.qrdm(A, 0.5, 0.9, 16)
+    g = {"A": sub.cpu().numpy(), "htau": f.htau.cpu().numpy(), "perm": f.perm.cpu().numpy().astype(np.int64),
+         "trace": f.trace, "J": f.J.astype(np.int64), "rank": f.rank, "rank_colmax": f.rank_colmax}
+    compare(A, g, o)
+    assert torch.all(big[200:] == 0)
+
+
+def test_kmax1_matches_oracle_qrp():
+    A = inputs.from_spectrum(400, 300, inputs.sigma_geometric(300, 1e-14), 44)
+    o = O.qrdm(A, 0.9, 0.9, 1)
+    g = run_gpu(A, 0.9, 0.9, 1)
+    rep = compare(A, g, o)
+    assert np.all(g["trace"]["k"] == 1)
+    assert rep["ncmp"] >= 200
+
+
+# ----------------------------------------------------------------- full size
+FULL = [
+    # name, tau, delta, kmax  (the benchmark's launch configuration)
+    ("geo4096", 0.15, 0.9, 64),
+    ("geo8192x2048", 0.15, 0.9, 64),
+    ("kahan2048", 0.15, 0.9, 64),
+    ("geo4096", 0.9, 0.9, 32),
+]
+
+
+def _apply_q(Afac, htau, X):
+    """Q X with Q = H_1 ... H_p applied from the stored reflectors."""
+    m = Afac.shape[0]
+    Y = X.copy()
+    for i in range(htau.shape[0] - 1, -1, -1):
+        if htau[i] == 0.0:
+            continue
+        v = np.concatenate([[1.0], Afac[i + 1:, i]])
+        Y[i:] -= htau[i] * np.outer(v, v @ Y[i:])
+    return Y
+
+
+def _norm2(A, iters=30):
+    """||A||_2 by power iteration on A^T A (a lower estimate converging from below)."""
+    x = np.random.default_rng(1).standard_normal(A.shape[1])
+    s = 0.0
+    for _ in range(iters):
+        y = A.T @ (A @ x)
+        s = np.linalg.norm(y)
+        x = y / s
+    return float(np.sqrt(s))
+
+
+@pytest.mark.parametrize("name,tau,delta,kmax", FULL)
+def test_full_size(name, tau, delta, kmax):
+    spec = inputs.named(name)
+    A = spec.build()
+    m, n = A.shape
+    g = run_gpu(A, tau, delta, kmax)
+    # sampled element-wise parity: the first steps against the oracle
+    steps = 3
+    o = O.qrdm(A, tau, delta, kmax, max_steps=steps)
+    gt = {"trace": g["trace"][:steps], "J": g["J"][:steps]}
+    from tests._parity import is_tie, rdiag_tol, walk
+
+    div, ns_div = walk(gt["trace"], gt["J"], o["trace"], o["J"])
+    ns_done = int(o["trace"]["ns"][-1] + o["trace"]["l"][-1])
+    if div is not None:
+        tie, score = is_tie(o["trace"], div)
+        assert tie, f"{name}: divergence at step {div} without a tie ({score})"
+        ns_done = ns_div
+    perm_g = g["perm"]
+    if ns_done > 0:
+        assert np.array_equal(perm_g[:ns_done], o["perm"][:ns_done])
+        anorm = float(np.max(np.linalg.norm(A, axis=0)))
+        Rg = np.triu(g["A"][:ns_done, :])
+        Ro = np.triu(o["A"][:ns_done, :])
+        # the first ns_done rows of R are final after those steps
+        tol = rdiag_tol(np.diag(Ro), anorm, m, n)
+        assert np.all(np.abs(np.abs(np.diag(Rg)) - np.abs(np.diag(Ro))) <= tol)
+        # later steps reorder the trailing columns: compare R rows by original column
+        Rg_o = np.empty_like(Rg)
+        Ro_o = np.empty_like(Ro)
+        Rg_o[:, perm_g] = Rg
+        Ro_o[:, o["perm"]] = Ro
+        rows_err = np.linalg.norm(Rg_o - Ro_o, axis=1) / anorm
+        assert np.all(rows_err <= 1e-11), rows_err.max()
+    # invariants at full size
+    perm = g["perm"]
+    assert sorted(perm.tolist()) == list(range(n))
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((n, 4))
+    R = np.triu(g["A"][: min(m, n), :])
+    lhs = A[:, perm] @ X
+    rhs = _apply_q(g["A"], g["htau"], np.vstack([R @ X, np.zeros((m - min(m, n), 4))]))
+    res = np.linalg.norm(lhs - rhs) / (_norm2(A) * np.linalg.norm(X))
+    assert res <= 1e-13, res
+    tr = g["trace"]
+    assert int(tr["l"].sum()) == min(m, n)
+    assert np.all(tr["l"] >= 1) and np.all(tr["k"] <= kmax)
+    sig = spec.sigma()
+    if sig is not None:
+        nr = int(np.sum(sig > 2 * EPS * n * sig[0]))
+        assert g["rank"] >= nr
+        # |R_ii| tracks sigma_i within the paper's factor-10 band where sigma_i is above roundoff
+        d = np.sort(np.abs(np.diag(R)))[::-1]
+        ok = sig > 1e4 * EPS * n * sig[0]
+        ratio = d[ok] / sig[ok]
+        assert ratio.min() > 1e-1 and ratio.max() < 10.0, (ratio.min(), ratio.max())
