@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""QRDM benchmark on GB300.
+
+One step = factor the plain-FP64 single-matrix workload: a 4096 x 4096 and an
+8192 x 2048 matrix with geometric singular values 1 -> 1e-15, and the Kahan
+matrix of order 2048 (c = 0.285), each A Pi = QR with QRDM2 at the paper's
+recommended tau = 0.15, delta = 0.9 and block size k_DM = 64 (Sec. 5).
+Metric: GFLOP/s = sum over the matrices of (4 m n^2 - 4 n^3 / 3) / time.
+
+Inputs are seeded synthetic matrices built on the host, copied to HBM once;
+before every step the factored matrices are restored from pristine device
+copies and L2 is flushed (a 256 MB write), both outside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank factors its own replica of the workload (the path
+does not shard; there is no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "QRDM GFLOP/s (4mn²−4n³/3) vs plain FP64 GPU QRDM at equal rank quality"
+TAU, DELTA, KMAX = 0.15, 0.9, 64
+WORKLOAD = ("geo4096", "geo8192x2048", "kahan2048")
+WORKLOAD_DESC = ("plain FP64 QRDM on single matrices: 4096x4096 and 8192x2048 with geometric sigma 1->1e-15, "
+                 "Kahan n=2048 (c=0.285)")
+# the CPU sample: the same recipes at half the linear size
+CPU_SAMPLE = (("geo", 2048, 2048), ("geo", 4096, 1024), ("kahan", 1024, 1024))
+FP64_FLOP_PER_CLK_PER_SM = 4.0  # 2 FP64 FMA per clock per SM on GB300 (1.25 TFLOP/s nominal at 2070 MHz)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def metric_flops(m: int, n: int) -> float:
+    return 4.0 * m * n * n - 4.0 * n ** 3 / 3.0
+
+
+def cpu_sample_matrices():
+    from paper_2106_03138_gb300 import inputs
+
+    out = []
+    for kind, m, n in CPU_SAMPLE:
+        if kind == "geo":
+            out.append(inputs.from_spectrum(m, n, inputs.sigma_geometric(n, 1e-15), 0))
+        else:
+            out.append(inputs.kahan(n))
+    return out
+
+
+def time_oracle_sample(mats) -> tuple[float, float]:
+    """(seconds, metric flops) of the CPU oracle on the sample (single thread)."""
+    from oracle import oracle as orc
+
+    t0 = time.perf_counter()
+    fl = 0.0
+    for A in mats:
+        r = orc.qrdm(A, TAU, DELTA, KMAX)
+        assert r["status"] == 0
+        fl += metric_flops(*A.shape)
+    return time.perf_counter() - t0, fl
+
+
+def sample_desc() -> str:
+    return ("oracle (single-threaded C, -O2) on the workload recipes at half linear size: " +
+            ", ".join(f"{k} {m}x{n}" for k, m, n in CPU_SAMPLE))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+        return False
+
+    def summary(self) -> dict:
+        if not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(kernel: str):
+    """dram bytes per launch from the committed ncu summary, if it still
+    matches the kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel") != kernel or rec.get("source_sha256") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("qrdm_kernels.cuh", "qrdm.cu"):
+        with open(os.path.join(ROOT, "paper_2106_03138_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args) -> int:
+    """The oracle timed on the host cores, one bounded CPU sample per step."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    mats = cpu_sample_matrices()
+    for _ in range(args.warmup):
+        time_oracle_sample(mats)
+    secs, fl = 0.0, 0.0
+    for _ in range(args.steps):
+        s, f = time_oracle_sample(mats)
+        secs += s
+        fl += f
+    value = fl / secs / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(world),
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample_desc()},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(world: int) -> dict:
+    return {"workload": WORKLOAD_DESC, "matrices": list(WORKLOAD), "tau": TAU, "delta": DELTA, "k_max": KMAX,
+            "global_batch": 3 * world, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "flushed (256 MB write) before every timed step; inputs restored from device copies untimed"}
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2106_03138_gb300 as q
+    from paper_2106_03138_gb300 import inputs
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    q.load()
+
+    specs = [inputs.named(nm) for nm in WORKLOAD]
+    host = [s.build() for s in specs]
+    shapes = [a.shape for a in host]
+    flops_step = sum(metric_flops(m, n) for m, n in shapes)
+    pristine = [q.colmajor(a, device=dev) for a in host]
+    work = [p.clone() for p in pristine]
+    wsz = max(q.qrdm_workspace_size(m, n, KMAX) for m, n in shapes)
+    ws = torch.empty(wsz, dtype=torch.uint8, device=dev)
+    htau = [torch.empty(min(m, n), dtype=torch.float64, device=dev) for m, n in shapes]
+    perm = [torch.empty(n, dtype=torch.int32, device=dev) for m, n in shapes]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def restore():
+        for w, p in zip(work, pristine):
+            w.copy_(p)
+        flush.fill_(1.0)
+
+    def step(profile=None):
+        launches = 0
+        infos = []
+        for i in range(len(work)):
+            f = q.factor(work[i], TAU, DELTA, KMAX, workspace=ws, out_htau=htau[i], out_perm=perm[i], stream=stream,
+                         profile=profile)
+            launches += f.launches
+            infos.append(f)
+        return launches, infos
+
+    for _ in range(args.warmup):
+        restore()
+        step()
+    torch.cuda.synchronize()
+
+    prof = q.qrdm_profile()
+    step_ms = []
+    launches = 0
+    infos = None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            restore()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nl, infos = step(prof)
+            e1.record(stream)
+            e1.synchronize()
+            launches += nl
+            step_ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * flops_step * args.steps / (total_ms * 1e-3) / 1e9
+
+    # dominant kernel and its roofline (FP64 ALU bound)
+    ms = list(prof.ms)
+    kid = max(range(len(q.KERNEL_NAMES)), key=lambda i: ms[i])
+    kname = q.KERNEL_NAMES[kid]
+    nlaunch = max(int(prof.launches[kid]), 1)
+    achieved = (prof.flops[kid] / nlaunch) / (ms[kid] / nlaunch * 1e-3) / 1e12 if ms[kid] > 0 else 0.0
+    csum = clk.summary()
+    sm_max = csum.get("sm_max_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    peak = FP64_FLOP_PER_CLK_PER_SM * props.multi_processor_count * sm_max * 1e6 / 1e12
+    total_kernel_ms = sum(ms)
+    roofline = {
+        "bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "frac": achieved / peak if peak else None, "traffic": traffic_for(kname),
+        "peak_source": "FP64 FMA rate 2/clk/SM x 152 SMs x sm_max_mhz (derived; nominal 1.25 TFLOP/s)",
+        "share_of_kernel_time": ms[kid] / total_kernel_ms if total_kernel_ms else None,
+        "kernel_ms": {q.KERNEL_NAMES[i]: round(ms[i], 3) for i in range(len(q.KERNEL_NAMES))},
+    }
+
+    # end to end through the public API with host buffers (pinned)
+    # pinned host buffers hold A^T in row-major order, i.e. A column-major
+    pin_in = []
+    for a in host:
+        t = torch.empty((a.shape[1], a.shape[0]), dtype=torch.float64).pin_memory()
+        t.copy_(torch.from_numpy(np.ascontiguousarray(a.T)))
+        pin_in.append(t)
+    pin_out = [torch.empty_like(p).pin_memory() for p in pin_in]
+    pin_ht = [torch.empty(min(m, n), dtype=torch.float64).pin_memory() for m, n in shapes]
+    pin_pm = [torch.empty(n, dtype=torch.int32).pin_memory() for m, n in shapes]
+    h2d = sum(p.numel() * 8 for p in pin_in)
+    d2h = sum(p.numel() * 8 for p in pin_in) + sum(h.numel() * 8 for h in pin_ht) + sum(p.numel() * 4 for p in pin_pm)
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_ms = 0.0
+    for _ in range(e2e_steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(len(work)):
+            # host -> device: the column-major input into the work buffer
+            work[i].t().copy_(pin_in[i], non_blocking=True)
+            q.factor(work[i], TAU, DELTA, KMAX, workspace=ws, out_htau=htau[i], out_perm=perm[i], stream=stream)
+            pin_out[i].copy_(work[i].t(), non_blocking=True)
+            pin_ht[i].copy_(htau[i], non_blocking=True)
+            pin_pm[i].copy_(perm[i], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_value = world * flops_step * e2e_steps / (e2e_ms * 1e-3) / 1e9
+
+    comparators = {}
+    if not args.no_comparators and rank == 0:
+        for label, tau, delta, kmax in (("qrp_kmax1", 0.9, 0.9, 1), ("tau0.9_delta0.9_kmax32", 0.9, 0.9, 32)):
+            wk = pristine[0].clone()
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f = q.factor(wk, tau, delta, kmax, workspace=ws, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            msc = e0.elapsed_time(e1)
+            m, n = shapes[0]
+            comparators[label] = {"matrix": WORKLOAD[0], "ms": msc, "GFLOP/s": metric_flops(m, n) / msc / 1e6,
+                                  "steps": f.nsteps, "rank": f.rank}
+            del wk
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        secs, fl = time_oracle_sample(cpu_sample_matrices())
+        cpu = {"value": fl / secs / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample_desc(),
+               "seconds": secs}
+
+    if rank == 0:
+        per = [{"matrix": nm, "m": m, "n": n, "rank": f.rank, "rank_colmax": f.rank_colmax, "steps": f.nsteps}
+               for nm, (m, n), f in zip(WORKLOAD, shapes, infos)]
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(world), "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": csum, "gpu_launches": launches, "wall_s": t_wall, "per_matrix": per,
+            "comparators": comparators,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

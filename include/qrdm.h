@@ -40,6 +40,33 @@ extern "C" {
 
 #define QRDM_KMAX_LIMIT 128 /* largest supported k_max */
 
+/* Kernel ids of qrdm_profile, in launch order within a block step. */
+#define QRDM_K_COLNORM 0       /* a1: initial column norms */
+#define QRDM_K_SELECT 1        /* a2/a3: stopping test, argmax, candidate set */
+#define QRDM_K_GRAM 2          /* a4: candidate Gram matrix, partial sums */
+#define QRDM_K_GRAM_REDUCE 3   /* a4: sum of the partial Gram matrices */
+#define QRDM_K_PICK 4          /* a5/a6: DM greedy pick, swap sequence */
+#define QRDM_K_PERMUTE 5       /* a6: column moves */
+#define QRDM_K_PANEL 6         /* a7/a8: Householder panel with break test, T */
+#define QRDM_K_TRAIL_W 7       /* a9: W = V^T A22 (partial) */
+#define QRDM_K_TRAIL_WREDUCE 8 /* a9: W = T^T sum(partials) */
+#define QRDM_K_TRAIL_UPDATE 9  /* a9: A22 -= V W */
+#define QRDM_K_DOWNDATE 10     /* a10: partial norm update */
+#define QRDM_K_STEP_END 11     /* a11: n_s += l */
+#define QRDM_NKERNELS 12
+
+/* Optional per-kernel timing (host struct, filled when opts->profile is set):
+   every launch is bracketed by CUDA events on the caller's stream; ms[] sums
+   the device time per kernel, flops[] the algorithmic FP64 flops its
+   launches performed (for the trailing update 4 m' n'' l + 2 l^2 n''), and
+   launches[] counts them.  Values accumulate across calls; zero the struct to
+   reset it. */
+typedef struct qrdm_profile {
+  double ms[16];
+  double flops[16];
+  int64_t launches[16];
+} qrdm_profile;
+
 /* Options; a NULL pointer means all zero (the defaults). */
 typedef struct qrdm_opts {
   /* eps1 in the stopping criterion sqrt(n - n_s) max||c_i|| <= eps1 max||a_i||
@@ -63,6 +90,8 @@ typedef struct qrdm_opts {
   int32_t max_steps;
   int32_t reserved0;
   int32_t reserved1;
+  /* host, optional: per-kernel event timing (see qrdm_profile). */
+  qrdm_profile* profile;
 } qrdm_opts;
 
 /* Host-side results of one factorization. */
@@ -70,6 +99,7 @@ typedef struct qrdm_info {
   int64_t rank;        /* n_s at which the criterion of Sec. 3.4 first held (min(m,n) if never) */
   int64_t rank_colmax; /* same test without the sqrt(n - n_s) factor */
   int64_t nsteps;      /* block steps executed */
+  int64_t launches;    /* kernels this call launched */
   int32_t cuda_error;  /* cudaError_t of the failing call when QRDM_ERR_CUDA */
   int32_t reserved;
 } qrdm_info;

@@ -25,7 +25,9 @@ from ._binding import (  # noqa: F401
     load,
     qrdm_factor,
     qrdm_info,
+    KERNEL_NAMES,
     qrdm_opts,
+    qrdm_profile,
     qrdm_step_record,
     qrdm_strerror,
     qrdm_workspace_size,
@@ -51,12 +53,18 @@ class Factorization:
     rank: int
     rank_colmax: int
     nsteps: int
+    launches: int = 0
     trace: np.ndarray | None = None   # TRACE_DTYPE records, one per block step
     J: np.ndarray | None = None       # (nsteps, k_max) original indices of the picked columns
 
 
-def make_opts(eps1_mode=0, stop_at_rank=False, check_last=False, no_break=False, sdd=False, max_steps=0) -> qrdm_opts:
+def make_opts(eps1_mode=0, stop_at_rank=False, check_last=False, no_break=False, sdd=False, max_steps=0,
+              profile: qrdm_profile | None = None) -> qrdm_opts:
+    import ctypes
+
     o = qrdm_opts()
+    if profile is not None:
+        o.profile = ctypes.pointer(profile)
     o.eps1_mode = int(eps1_mode)
     o.stop_at_rank = int(bool(stop_at_rank))
     o.check_last = int(bool(check_last))
@@ -86,7 +94,7 @@ def colmajor(A, device="cuda"):
 def factor(A, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mode: int = 0,
            stop_at_rank: bool = False, check_last: bool = False, no_break: bool = False, sdd: bool = False,
            max_steps: int = 0, trace: bool = False, workspace=None, out_htau=None, out_perm=None,
-           stream=None) -> Factorization:
+           stream=None, profile: qrdm_profile | None = None) -> Factorization:
     """Factor A Pi = Q R in place.  ``A`` is a CUDA float64 tensor with
     stride(0) == 1 (column-major, lda = stride(1))."""
     import torch
@@ -113,7 +121,7 @@ def factor(A, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mod
         tr = torch.zeros(cap * TRACE_DTYPE.itemsize, dtype=torch.uint8, device=dev)
         trJ = torch.empty(cap * k_max, dtype=torch.int32, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
-    opts = make_opts(eps1_mode, stop_at_rank, check_last, no_break, sdd, max_steps)
+    opts = make_opts(eps1_mode, stop_at_rank, check_last, no_break, sdd, max_steps, profile)
     rc, info = qrdm_factor(A.data_ptr() if m * n else 0, m, n, lda, float(tau), float(delta), int(k_max),
                            htau.data_ptr(), perm.data_ptr(), opts, workspace.data_ptr(), workspace.numel(),
                            s.cuda_stream, tr.data_ptr() if tr is not None else 0,
@@ -121,7 +129,7 @@ def factor(A, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mod
     if rc != 0:
         raise QRDMError(rc)
     out = Factorization(A=A, htau=htau[:kmin], perm=perm[:n], rank=int(info.rank), rank_colmax=int(info.rank_colmax),
-                        nsteps=int(info.nsteps))
+                        nsteps=int(info.nsteps), launches=int(info.launches))
     if trace:
         ns = min(out.nsteps, cap)
         out.trace = np.frombuffer(tr.cpu().numpy().tobytes(), dtype=TRACE_DTYPE)[:ns].copy()

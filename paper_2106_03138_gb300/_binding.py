@@ -23,14 +23,23 @@ QRDM_ERR_INTERNAL = 5
 QRDM_KMAX_LIMIT = 128
 
 
+KERNEL_NAMES = ("k_colnorm_init", "k_select", "k_gram", "k_gram_reduce", "k_pick", "k_permute", "k_panel",
+                "k_trail_w", "k_trail_wreduce", "k_trail_update", "k_downdate", "k_step_end")
+
+
+class qrdm_profile(ctypes.Structure):
+    _fields_ = [("ms", c_f64 * 16), ("flops", c_f64 * 16), ("launches", c_i64 * 16)]
+
+
 class qrdm_opts(ctypes.Structure):
     _fields_ = [("eps1_mode", c_i32), ("stop_at_rank", c_i32), ("check_last", c_i32), ("no_break", c_i32),
-                ("sdd", c_i32), ("max_steps", c_i32), ("reserved0", c_i32), ("reserved1", c_i32)]
+                ("sdd", c_i32), ("max_steps", c_i32), ("reserved0", c_i32), ("reserved1", c_i32),
+                ("profile", ctypes.POINTER(qrdm_profile))]
 
 
 class qrdm_info(ctypes.Structure):
-    _fields_ = [("rank", c_i64), ("rank_colmax", c_i64), ("nsteps", c_i64), ("cuda_error", c_i32),
-                ("reserved", c_i32)]
+    _fields_ = [("rank", c_i64), ("rank_colmax", c_i64), ("nsteps", c_i64), ("launches", c_i64),
+                ("cuda_error", c_i32), ("reserved", c_i32)]
 
 
 class qrdm_step_record(ctypes.Structure):

@@ -64,6 +64,8 @@ struct DeviceConfig {
   int sms = 0;
   int cluster = 0;  // panel cluster size
   bool ok = false;
+  cudaEvent_t ev[2 * QRDM_NKERNELS] = {};  // profile events, created on first use
+  bool have_events = false;
 };
 
 thread_local DeviceConfig g_cfg;
@@ -80,10 +82,9 @@ int configure(DeviceConfig* cfg) {
   c.device = dev;
   e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return (int)e;
-  const int pick_smem = (int)(KMAX * (KMAX + 1) / 2 * sizeof(double));
   const int perm_smem = (int)(2 * KMAX * 33 * sizeof(double));
   const int gram_smem = (int)(KMAX * (GRAM_ROWS + 1) * sizeof(double));
-  if ((e = cudaFuncSetAttribute(k_pick, cudaFuncAttributeMaxDynamicSharedMemorySize, pick_smem)) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(k_trail_w, cudaFuncAttributeMaxDynamicSharedMemorySize, TRAIL_W_SMEM)) != cudaSuccess)
     return (int)e;
   if ((e = cudaFuncSetAttribute(k_permute, cudaFuncAttributeMaxDynamicSharedMemorySize, perm_smem)) != cudaSuccess)
     return (int)e;
@@ -258,18 +259,30 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   if (d_trace_J && trace_cap > 0)
     CK(cudaMemsetAsync(d_trace_J, 0xff, sizeof(int32_t) * (size_t)trace_cap * (size_t)k_max, stream));
   k_state_init<<<1, 1, 0, stream>>>(P);
+  if (o.profile && !g_cfg.have_events) {
+    for (int i = 0; i < 2 * QRDM_NKERNELS; ++i) CK(cudaEventCreate(&g_cfg.ev[i]));
+    g_cfg.have_events = true;
+  }
+  if (o.profile) CK(cudaEventRecord(g_cfg.ev[2 * QRDM_K_COLNORM], stream));
   {
     int64_t g = (n + 7) / 8;
     if (g > (int64_t)sms * 16) g = (int64_t)sms * 16;
     k_colnorm_init<<<(unsigned)g, 256, 0, stream>>>(P);
   }
   CK(cudaGetLastError());
+  if (o.profile) CK(cudaEventRecord(g_cfg.ev[2 * QRDM_K_COLNORM + 1], stream));
   DevState hs;
   CK(cudaMemcpyAsync(&hs, P.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
   if (hs.nonfinite) return QRDM_ERR_NONFINITE;
+  if (o.profile) {
+    float msk = 0.f;
+    CK(cudaEventElapsedTime(&msk, g_cfg.ev[2 * QRDM_K_COLNORM], g_cfg.ev[2 * QRDM_K_COLNORM + 1]));
+    o.profile->ms[QRDM_K_COLNORM] += msk;
+    o.profile->launches[QRDM_K_COLNORM] += 1;
+    o.profile->flops[QRDM_K_COLNORM] += 2.0 * (double)m * (double)n;
+  }
 
-  const int pick_smem = (int)((k_max * (k_max + 1) / 2) * sizeof(double));
   const int perm_smem = (int)(2 * k_max * 33 * sizeof(double));
   const int gram_smem = (int)(k_max * (GRAM_ROWS + 1) * sizeof(double));
   unsigned perm_grid = (unsigned)((m + 31) / 32);
@@ -291,24 +304,71 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   pc.attrs = pat;
   pc.numAttrs = 1;
 
+  qrdm_profile* prof = o.profile;
+  if (prof && !g_cfg.have_events) {
+    for (int i = 0; i < 2 * QRDM_NKERNELS; ++i) CK(cudaEventCreate(&g_cfg.ev[i]));
+    g_cfg.have_events = true;
+  }
+  cudaEvent_t* ev = g_cfg.ev;
+  int64_t launches = 2;
+  // launch helper: brackets the launch with events when profiling
+  auto run = [&](int kid, auto&& launch) -> cudaError_t {
+    if (prof) {
+      cudaError_t e = cudaEventRecord(ev[2 * kid], stream);
+      if (e != cudaSuccess) return e;
+    }
+    launch();
+    ++launches;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && prof) e = cudaEventRecord(ev[2 * kid + 1], stream);
+    return e;
+  };
+  const int step_kernels[] = {QRDM_K_SELECT, QRDM_K_GRAM, QRDM_K_GRAM_REDUCE, QRDM_K_PICK, QRDM_K_PERMUTE,
+                              QRDM_K_PANEL, QRDM_K_TRAIL_W, QRDM_K_TRAIL_WREDUCE, QRDM_K_TRAIL_UPDATE,
+                              QRDM_K_DOWNDATE, QRDM_K_STEP_END};
+  int64_t ns_prev = 0;
   const int64_t max_iter = kmin + 2;
   for (int64_t it = 0; it < max_iter; ++it) {
-    k_select<<<1, SEL_THREADS, 0, stream>>>(P);
-    k_gram<<<P.gram_chunks, 256, gram_smem, stream>>>(P);
-    k_gram_reduce<<<gred_grid, 256, 0, stream>>>(P);
-    k_pick<<<1, 256, pick_smem, stream>>>(P);
-    k_permute<<<perm_grid, 256, perm_smem, stream>>>(P);
-    CK(cudaLaunchKernelEx(&pc, k_panel, P));
-    k_trail_w<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P);
-    k_trail_wreduce<<<sms, GEMM_THREADS, 0, stream>>>(P);
-    k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P);
-    k_downdate<<<dd_grid, 256, 0, stream>>>(P);
-    k_step_end<<<1, 1, 0, stream>>>(P);
-    CK(cudaGetLastError());
+    CK(run(QRDM_K_SELECT, [&] { k_select<<<1, SEL_THREADS, 0, stream>>>(P); }));
+    CK(run(QRDM_K_GRAM, [&] { k_gram<<<P.gram_chunks, 256, gram_smem, stream>>>(P); }));
+    CK(run(QRDM_K_GRAM_REDUCE, [&] { k_gram_reduce<<<gred_grid, 256, 0, stream>>>(P); }));
+    CK(run(QRDM_K_PICK, [&] { k_pick<<<1, 256, 0, stream>>>(P); }));
+    CK(run(QRDM_K_PERMUTE, [&] { k_permute<<<perm_grid, 256, perm_smem, stream>>>(P); }));
+    CK(run(QRDM_K_PANEL, [&] { cudaLaunchKernelEx(&pc, k_panel, P); }));
+    CK(run(QRDM_K_TRAIL_W, [&] { k_trail_w<<<gemm_grid, GEMM_THREADS, TRAIL_W_SMEM, stream>>>(P); }));
+    CK(run(QRDM_K_TRAIL_WREDUCE, [&] { k_trail_wreduce<<<sms, GEMM_THREADS, 0, stream>>>(P); }));
+    CK(run(QRDM_K_TRAIL_UPDATE, [&] { k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P); }));
+    CK(run(QRDM_K_DOWNDATE, [&] { k_downdate<<<dd_grid, 256, 0, stream>>>(P); }));
+    CK(run(QRDM_K_STEP_END, [&] { k_step_end<<<1, 1, 0, stream>>>(P); }));
     CK(cudaMemcpyAsync(&hs, P.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
+    if (prof) {
+      for (int kid : step_kernels) {
+        float msk = 0.f;
+        CK(cudaEventElapsedTime(&msk, ev[2 * kid], ev[2 * kid + 1]));
+        prof->ms[kid] += msk;
+        prof->launches[kid] += 1;
+      }
+      if (hs.ns > ns_prev) {
+        // algorithmic flops of the step that just ran (n_s was ns_prev)
+        const double mr = (double)(m - ns_prev), l = hs.l, k = hs.k, kc = hs.kc;
+        const double n2 = (double)(n - ns_prev) - k;
+        if (n2 > 0 && l > 0) {
+          prof->flops[QRDM_K_TRAIL_W] += 2.0 * mr * n2 * l;
+          prof->flops[QRDM_K_TRAIL_WREDUCE] += l * (l + 1.0) * n2;
+          prof->flops[QRDM_K_TRAIL_UPDATE] += 2.0 * mr * n2 * l;
+        }
+        if (kc > 1) prof->flops[QRDM_K_GRAM] += mr * kc * (kc + 1.0);
+        // panel: per reflector a reduction over k columns and an update of the rest
+        double pf = 0.0;
+        for (int64_t i = 0; i < (int64_t)l && i < (int64_t)k; ++i) pf += 2.0 * (mr - i) * (k + (k - i - 1));
+        prof->flops[QRDM_K_PANEL] += pf;
+      }
+    }
+    ns_prev = hs.ns;
     if (hs.done) break;
   }
+  info->launches = launches;
   if (!hs.done) return QRDM_ERR_INTERNAL;
   if (hs.nonfinite) return QRDM_ERR_INTERNAL;
   info->rank = hs.rank >= 0 ? hs.rank : (hs.ns >= kmin ? kmin : hs.ns);

@@ -502,8 +502,8 @@ __device__ __forceinline__ int tri(int a, int b) {  // packed upper index, a <= 
 __global__ void __launch_bounds__(256) k_pick(Params P) {
   DevState* st = P.st;
   if (st->done) return;
-  extern __shared__ double s_th[];  // kc*(kc+1)/2 packed cosines
-  __shared__ double s_d[KMAX];
+  __shared__ double s_d[KMAX];   // column norms sqrt(G_aa)
+  __shared__ int s_col[KMAX];    // positions of the kc gathered columns
   __shared__ int s_J[KMAX];
   __shared__ int s_k;
   __shared__ int s_pos[2 * KMAX], s_cont[2 * KMAX];
@@ -514,41 +514,33 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
   const int64_t ns = st->ns;
   const int tid = threadIdx.x, lane = tid & 31;
 
-  if (kc > 1) {
-    const int npairs = kc * (kc + 1) / 2;
-    for (int a = tid; a < kc; a += blockDim.x) s_d[a] = sqrt(P.G[tri(a, a)]);
-    __syncthreads();
-    for (int e = tid; e < npairs; e += blockDim.x) {
-      int b = 0;
-      while ((b + 1) * (b + 2) / 2 <= e) ++b;
-      int a = e - b * (b + 1) / 2;
-      double g = P.G[e];
-      double d = s_d[a] * s_d[b];
-      s_th[e] = (d > 0.0) ? g / d : 1.0;
-      if (!(d > 0.0)) s_th[e] = 1.0;
-    }
-    __syncthreads();
+  for (int a = tid; a < kc; a += blockDim.x) {
+    s_col[a] = P.cols[a];
+    s_d[a] = (kc > 1) ? sqrt(P.G[tri(a, a)]) : 1.0;
   }
+  __syncthreads();
   if (tid < 32) {
     double dlt = P.delta;
     if (P.sdd && kc > 1) {
       double dm = P.tau * P.tau / (double)((kc - 1) > 1 ? (kc - 1) : 1);
       if (dm < dlt) dlt = dm;
     }
+    // greedy DM pick (Alg. 1 loop): candidates in order, accept when
+    // |theta(a, b)| = |G_ab| / (||c_a|| ||c_b||) < delta for every accepted b
     int k = 1;
     if (lane == 0) s_J[0] = 0;
     __syncwarp();
     for (int a = 1; a < kc; ++a) {
       bool ok = true;
+      const double da = s_d[a];
       for (int b = lane; b < k; b += 32) {
-        int jb = s_J[b];
-        int lo = jb < a ? jb : a, hi = jb < a ? a : jb;
-        double th = fabs(s_th[tri(lo, hi)]);
-        if (s_d[a] <= 0.0 || s_d[jb] <= 0.0) th = 1.0;
+        const int jb = s_J[b];
+        const int lo = jb < a ? jb : a, hi = jb < a ? a : jb;
+        const double d = da * s_d[jb];
+        double th = (d > 0.0) ? fabs(P.G[tri(lo, hi)] / d) : 1.0;
         if (!(th < dlt)) ok = false;
       }
-      bool all = __all_sync(0xffffffffu, ok);
-      if (all) {
+      if (__all_sync(0xffffffffu, ok)) {
         if (lane == 0) s_J[k] = a;
         ++k;
       }
@@ -563,7 +555,7 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
         ++np;
       }
       for (int t = 0; t < k; ++t) {
-        int pj = P.cols[s_J[t]];
+        const int pj = s_col[s_J[t]];
         if (pj >= ns + k) {
           s_pos[np] = pj;
           s_cont[np] = pj;
@@ -576,8 +568,7 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
     __syncwarp();
     const int np = s_np;
     for (int t = 0; t < k; ++t) {
-      const int orig = P.cols[s_J[t]];  // position of J_t at step start
-      // find the entry whose content is orig
+      const int orig = s_col[s_J[t]];  // position of J_t at step start
       int found = -1;
       for (int e = lane; e < np; e += 32)
         if (s_cont[e] == orig) found = e;
@@ -586,10 +577,9 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
         if (lane == 0) st->nonfinite = 3;
         continue;
       }
-      int src_lane = __ffs(b) - 1;
-      int e_p = __shfl_sync(0xffffffffu, found, src_lane);
+      const int e_p = __shfl_sync(0xffffffffu, found, __ffs(b) - 1);
       if (lane == 0) {
-        int tmp = s_cont[t];  // entry t is position ns+t
+        const int tmp = s_cont[t];  // entry t is position ns+t
         s_cont[t] = s_cont[e_p];
         s_cont[e_p] = tmp;
       }
@@ -616,19 +606,18 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
   }
   __syncthreads();
   const int nm = s_np;
-  for (int q = tid; q < nm; q += blockDim.x) {
-    int e = s_mvp[q];
-    int src = s_cont[e];
-    s_mv[q][0] = P.u[src];
-    s_mv[q][1] = P.uref[src];
-    s_mvp[q] = P.perm[src];
+  for (int qq = tid; qq < nm; qq += blockDim.x) {
+    const int src = s_cont[s_mvp[qq]];
+    s_mv[qq][0] = P.u[src];
+    s_mv[qq][1] = P.uref[src];
+    s_mvp[qq] = P.perm[src];
   }
   __syncthreads();
-  for (int q = tid; q < nm; q += blockDim.x) {
-    int dst = P.mdst[q];
-    P.u[dst] = s_mv[q][0];
-    P.uref[dst] = s_mv[q][1];
-    P.perm[dst] = s_mvp[q];
+  for (int qq = tid; qq < nm; qq += blockDim.x) {
+    const int dst = P.mdst[qq];
+    P.u[dst] = s_mv[qq][0];
+    P.uref[dst] = s_mv[qq][1];
+    P.perm[dst] = s_mvp[qq];
   }
   __syncthreads();
   if (P.trace && st->step < P.trace_cap) {
@@ -814,53 +803,65 @@ __device__ __forceinline__ int64_t wchunk_rows(int64_t mr, int64_t ncoltiles, in
   return rows;
 }
 
-__global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P) {
-  const DevState* st = P.st;
-  if (st->done) return;
-  const int l = st->l, k = st->k;
-  const int64_t ns = st->ns, m = P.m, lda = P.lda;
-  const int64_t j0 = ns + k;
-  const int64_t n2 = P.n - j0, mr = m - ns;
-  if (l <= 0 || n2 <= 0 || mr <= 0) return;
-  const int64_t nct = (n2 + TW_COLS - 1) / TW_COLS;
-  const int64_t rows_per = wchunk_rows(mr, nct, P.wchunks, P.w_units);
-  const int64_t nrc = (mr + rows_per - 1) / rows_per;
-  const int64_t units = nct * nrc;
-  __shared__ double s_a[TW_SUB][TW_COLS + 1];
-  __shared__ double s_v[TW_SUB][KMAX + 1];
+// Thread layout of the W phase: TG reflector groups x (256/TG) columns; each
+// thread accumulates NQ = ceil(l/TG) reflectors of one column, so no FMA slot
+// is wasted on reflectors past l (a predicated-off FFMA64 still costs issue).
+__device__ __forceinline__ int w_tg(int l) { return l >= 8 ? 8 : (l >= 4 ? 4 : (l >= 2 ? 2 : 1)); }
+
+struct WGeom {
+  int64_t nct, rows_per, nrc;
+  int cols;
+};
+
+__device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int64_t mr) {
+  WGeom g;
+  g.cols = GEMM_THREADS / w_tg(l);
+  g.nct = (n2 + g.cols - 1) / g.cols;
+  g.rows_per = wchunk_rows(mr, g.nct, P.wchunks, P.w_units);
+  g.nrc = (mr + g.rows_per - 1) / g.rows_per;
+  return g;
+}
+
+template <int TG, int NQ>
+__device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int l, int64_t ns, int64_t j0,
+                                             int64_t mr, const WGeom& g) {
+  constexpr int COLS = GEMM_THREADS / TG;
+  constexpr int LDA_S = COLS + 1;
+  constexpr int LDV_S = KMAX + 1;
+  double* s_a = smem;                   // [TW_SUB][COLS + 1]
+  double* s_v = smem + TW_SUB * LDA_S;  // [TW_SUB][KMAX + 1]
+  const int64_t lda = P.lda;
   const int tid = threadIdx.x;
-  const int c = tid % TW_COLS;       // column within the tile
-  const int tg = tid / TW_COLS;      // 0..7 reflector group
-  const int TG = GEMM_THREADS / TW_COLS;
+  const int c = tid % COLS, tg = tid / COLS;
+  const int64_t units = g.nct * g.nrc;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int64_t ct = u % nct, rc = u / nct;
-    const int64_t cbase = j0 + ct * TW_COLS;
-    const int ncols = (int)min((int64_t)TW_COLS, P.n - cbase);
-    const int64_t rbeg = rc * rows_per, rend = min(mr, rbeg + rows_per);
-    constexpr int NQ = KMAX / (GEMM_THREADS / TW_COLS);
+    const int64_t ct = u % g.nct, rc = u / g.nct;
+    const int64_t cbase = j0 + ct * COLS;
+    const int ncols = (int)min((int64_t)COLS, P.n - cbase);
+    const int64_t rbeg = rc * g.rows_per, rend = min(mr, rbeg + g.rows_per);
     double acc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     for (int64_t r0 = rbeg; r0 < rend; r0 += TW_SUB) {
       const int rows = (int)min((int64_t)TW_SUB, rend - r0);
       __syncthreads();
-      for (int e = tid; e < TW_SUB * TW_COLS; e += GEMM_THREADS) {
-        int cc = e / TW_SUB, rr = e % TW_SUB;
+      for (int e = tid; e < TW_SUB * COLS; e += GEMM_THREADS) {
+        const int cc = e / TW_SUB, rr = e % TW_SUB;
         double v = 0.0;
         if (rr < rows && cc < ncols) v = P.A[(cbase + cc) * lda + ns + r0 + rr];
-        s_a[rr][cc] = v;
+        s_a[rr * LDA_S + cc] = v;
       }
       for (int e = tid; e < TW_SUB * l; e += GEMM_THREADS) {
-        int t = e / TW_SUB, rr = e % TW_SUB;
-        s_v[rr][t] = (rr < rows) ? vget(P.A, lda, ns, r0 + rr, t) : 0.0;
+        const int t = e / TW_SUB, rr = e % TW_SUB;
+        s_v[rr * LDV_S + t] = (rr < rows) ? vget(P.A, lda, ns, r0 + rr, t) : 0.0;
       }
       __syncthreads();
       for (int rr = 0; rr < rows; ++rr) {
-        const double a = s_a[rr][c];
+        const double a = s_a[rr * LDA_S + c];
+        const double* vr = s_v + rr * LDV_S + tg;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-          const int t = tg + q * TG;
-          if (t < l) acc[q] = fma(s_v[rr][t], a, acc[q]);
+          if (q < NQ - 1 || tg + q * TG < l) acc[q] = fma(vr[q * TG], a, acc[q]);
         }
       }
     }
@@ -875,6 +876,50 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P) {
   }
 }
 
+constexpr int TRAIL_W_SMEM = (TW_SUB * (GEMM_THREADS + 1) + TW_SUB * (KMAX + 1)) * (int)sizeof(double);
+
+__global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P) {
+  const DevState* st = P.st;
+  if (st->done) return;
+  const int l = st->l, k = st->k;
+  const int64_t ns = st->ns;
+  const int64_t j0 = ns + k;
+  const int64_t n2 = P.n - j0, mr = P.m - ns;
+  if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  extern __shared__ double smw[];
+  const WGeom g = w_geom(P, l, n2, mr);
+  const int tg = w_tg(l);
+  const int nq = (l + tg - 1) / tg;
+  if (tg == 1) {
+    trail_w_body<1, 1>(P, smw, l, ns, j0, mr, g);
+  } else if (tg == 2) {
+    if (nq == 1) trail_w_body<2, 1>(P, smw, l, ns, j0, mr, g);
+    else trail_w_body<2, 2>(P, smw, l, ns, j0, mr, g);
+  } else if (tg == 4) {
+    if (nq == 1) trail_w_body<4, 1>(P, smw, l, ns, j0, mr, g);
+    else trail_w_body<4, 2>(P, smw, l, ns, j0, mr, g);
+  } else {
+    switch (nq) {
+      case 1: trail_w_body<8, 1>(P, smw, l, ns, j0, mr, g); break;
+      case 2: trail_w_body<8, 2>(P, smw, l, ns, j0, mr, g); break;
+      case 3: trail_w_body<8, 3>(P, smw, l, ns, j0, mr, g); break;
+      case 4: trail_w_body<8, 4>(P, smw, l, ns, j0, mr, g); break;
+      case 5: trail_w_body<8, 5>(P, smw, l, ns, j0, mr, g); break;
+      case 6: trail_w_body<8, 6>(P, smw, l, ns, j0, mr, g); break;
+      case 7: trail_w_body<8, 7>(P, smw, l, ns, j0, mr, g); break;
+      case 8: trail_w_body<8, 8>(P, smw, l, ns, j0, mr, g); break;
+      case 9: trail_w_body<8, 9>(P, smw, l, ns, j0, mr, g); break;
+      case 10: trail_w_body<8, 10>(P, smw, l, ns, j0, mr, g); break;
+      case 11: trail_w_body<8, 11>(P, smw, l, ns, j0, mr, g); break;
+      case 12: trail_w_body<8, 12>(P, smw, l, ns, j0, mr, g); break;
+      case 13: trail_w_body<8, 13>(P, smw, l, ns, j0, mr, g); break;
+      case 14: trail_w_body<8, 14>(P, smw, l, ns, j0, mr, g); break;
+      case 15: trail_w_body<8, 15>(P, smw, l, ns, j0, mr, g); break;
+      default: trail_w_body<8, 16>(P, smw, l, ns, j0, mr, g); break;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P) {
   const DevState* st = P.st;
   if (st->done) return;
@@ -883,8 +928,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P) {
   const int64_t n2 = P.n - j0, mr = P.m - ns;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
   const int64_t nct = (n2 + TW_COLS - 1) / TW_COLS;
-  const int64_t rows_per = wchunk_rows(mr, nct, P.wchunks, P.w_units);
-  const int64_t nrc = (mr + rows_per - 1) / rows_per;
+  const int64_t nrc = w_geom(P, l, n2, mr).nrc;  // row chunks of k_trail_w
   __shared__ double s_w[KMAX][TW_COLS + 1];
   const int tid = threadIdx.x;
   const int c = tid % TW_COLS, tg = tid / TW_COLS, TG = GEMM_THREADS / TW_COLS;

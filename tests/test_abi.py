@@ -46,8 +46,9 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layouts():
     from paper_2106_03138_gb300 import _binding
 
-    assert ctypes.sizeof(_binding.qrdm_opts) == 32
-    assert ctypes.sizeof(_binding.qrdm_info) == 32
+    assert ctypes.sizeof(_binding.qrdm_opts) == 40
+    assert ctypes.sizeof(_binding.qrdm_info) == 40
+    assert ctypes.sizeof(_binding.qrdm_profile) == 16 * 8 * 3
     assert ctypes.sizeof(_binding.qrdm_step_record) == 80
 
 
