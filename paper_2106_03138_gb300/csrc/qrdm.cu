@@ -6,6 +6,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "../../include/qrdm.h"
 #include "qrdm_kernels.cuh"
 
@@ -69,6 +71,7 @@ struct DeviceConfig {
 };
 
 thread_local DeviceConfig g_cfg;
+thread_local std::vector<cudaEvent_t> g_events;
 
 int configure(DeviceConfig* cfg) {
   int dev = 0;
@@ -85,6 +88,9 @@ int configure(DeviceConfig* cfg) {
   const int perm_smem = (int)(2 * KMAX * 33 * sizeof(double));
   const int gram_smem = (int)(KMAX * (GRAM_ROWS + 1) * sizeof(double));
   if ((e = cudaFuncSetAttribute(k_trail_w, cudaFuncAttributeMaxDynamicSharedMemorySize, TRAIL_W_SMEM)) != cudaSuccess)
+    return (int)e;
+  const int pick_smem_max = (int)(KMAX * (KMAX + 1) / 2 * sizeof(double));
+  if ((e = cudaFuncSetAttribute(k_pick, cudaFuncAttributeMaxDynamicSharedMemorySize, pick_smem_max)) != cudaSuccess)
     return (int)e;
   if ((e = cudaFuncSetAttribute(k_permute, cudaFuncAttributeMaxDynamicSharedMemorySize, perm_smem)) != cudaSuccess)
     return (int)e;
@@ -280,11 +286,11 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     CK(cudaEventElapsedTime(&msk, g_cfg.ev[2 * QRDM_K_COLNORM], g_cfg.ev[2 * QRDM_K_COLNORM + 1]));
     o.profile->ms[QRDM_K_COLNORM] += msk;
     o.profile->launches[QRDM_K_COLNORM] += 1;
-    o.profile->flops[QRDM_K_COLNORM] += 2.0 * (double)m * (double)n;
   }
 
   const int perm_smem = (int)(2 * k_max * 33 * sizeof(double));
   const int gram_smem = (int)(k_max * (GRAM_ROWS + 1) * sizeof(double));
+  const int pick_smem = (int)((k_max * (k_max + 1) / 2) * sizeof(double));
   unsigned perm_grid = (unsigned)((m + 31) / 32);
   if (perm_grid > (unsigned)(4 * sms)) perm_grid = 4 * sms;
   unsigned dd_grid = (unsigned)((n + 7) / 8);
@@ -305,68 +311,104 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   pc.numAttrs = 1;
 
   qrdm_profile* prof = o.profile;
-  if (prof && !g_cfg.have_events) {
-    for (int i = 0; i < 2 * QRDM_NKERNELS; ++i) CK(cudaEventCreate(&g_cfg.ev[i]));
-    g_cfg.have_events = true;
+  const int nsub_full = (k_max + PB - 1) / PB;
+  // events for profiling: two pools (the previous batch is read while the
+  // next one runs), each with a start/end pair per launch
+  constexpr int MAX_BATCH = 16;
+  const int per_step = 7 + 4 * nsub_full;
+  const int pool = MAX_BATCH * per_step;
+  if (prof && (int)g_events.size() < 2 * 2 * pool) {
+    while ((int)g_events.size() < 2 * 2 * pool) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      g_events.push_back(e);
+    }
   }
-  cudaEvent_t* ev = g_cfg.ev;
   int64_t launches = 2;
-  // launch helper: brackets the launch with events when profiling
+  struct Rec {
+    int kid;
+    int ev;
+  };
+  std::vector<Rec> recs[2];
+  int cur = 0;
   auto run = [&](int kid, auto&& launch) -> cudaError_t {
+    int evi = -1;
     if (prof) {
-      cudaError_t e = cudaEventRecord(ev[2 * kid], stream);
+      evi = 2 * pool * cur + 2 * (int)recs[cur].size();
+      cudaError_t e = cudaEventRecord(g_events[evi], stream);
       if (e != cudaSuccess) return e;
     }
     launch();
     ++launches;
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && prof) e = cudaEventRecord(ev[2 * kid + 1], stream);
+    if (e == cudaSuccess && prof) {
+      e = cudaEventRecord(g_events[evi + 1], stream);
+      recs[cur].push_back({kid, evi});
+    }
     return e;
   };
-  const int step_kernels[] = {QRDM_K_SELECT, QRDM_K_GRAM, QRDM_K_GRAM_REDUCE, QRDM_K_PICK, QRDM_K_PERMUTE,
-                              QRDM_K_PANEL, QRDM_K_TRAIL_W, QRDM_K_TRAIL_WREDUCE, QRDM_K_TRAIL_UPDATE,
-                              QRDM_K_DOWNDATE, QRDM_K_STEP_END};
-  int64_t ns_prev = 0;
-  const int64_t max_iter = kmin + 2;
-  for (int64_t it = 0; it < max_iter; ++it) {
-    CK(run(QRDM_K_SELECT, [&] { k_select<<<1, SEL_THREADS, 0, stream>>>(P); }));
-    CK(run(QRDM_K_GRAM, [&] { k_gram<<<P.gram_chunks, 256, gram_smem, stream>>>(P); }));
-    CK(run(QRDM_K_GRAM_REDUCE, [&] { k_gram_reduce<<<gred_grid, 256, 0, stream>>>(P); }));
-    CK(run(QRDM_K_PICK, [&] { k_pick<<<1, 256, 0, stream>>>(P); }));
-    CK(run(QRDM_K_PERMUTE, [&] { k_permute<<<perm_grid, 256, perm_smem, stream>>>(P); }));
-    CK(run(QRDM_K_PANEL, [&] { cudaLaunchKernelEx(&pc, k_panel, P); }));
-    CK(run(QRDM_K_TRAIL_W, [&] { k_trail_w<<<gemm_grid, GEMM_THREADS, TRAIL_W_SMEM, stream>>>(P); }));
-    CK(run(QRDM_K_TRAIL_WREDUCE, [&] { k_trail_wreduce<<<sms, GEMM_THREADS, 0, stream>>>(P); }));
-    CK(run(QRDM_K_TRAIL_UPDATE, [&] { k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P); }));
-    CK(run(QRDM_K_DOWNDATE, [&] { k_downdate<<<dd_grid, 256, 0, stream>>>(P); }));
-    CK(run(QRDM_K_STEP_END, [&] { k_step_end<<<1, 1, 0, stream>>>(P); }));
+  auto harvest = [&](int which) -> cudaError_t {
+    for (const Rec& r : recs[which]) {
+      float msk = 0.f;
+      cudaError_t e = cudaEventElapsedTime(&msk, g_events[r.ev], g_events[r.ev + 1]);
+      if (e != cudaSuccess) return e;
+      prof->ms[r.kid] += msk;
+      prof->launches[r.kid] += 1;
+    }
+    recs[which].clear();
+    return cudaSuccess;
+  };
+  auto enqueue_step = [&](int nsub) -> cudaError_t {
+    cudaError_t e;
+    if ((e = run(QRDM_K_SELECT, [&] { k_select<<<1, SEL_THREADS, 0, stream>>>(P); })) != cudaSuccess) return e;
+    if ((e = run(QRDM_K_GRAM, [&] { k_gram<<<P.gram_chunks, 256, gram_smem, stream>>>(P); })) != cudaSuccess)
+      return e;
+    if ((e = run(QRDM_K_GRAM_REDUCE, [&] { k_gram_reduce<<<gred_grid, 256, 0, stream>>>(P); })) != cudaSuccess)
+      return e;
+    if ((e = run(QRDM_K_PICK, [&] { k_pick<<<1, 256, pick_smem, stream>>>(P); })) != cudaSuccess) return e;
+    if ((e = run(QRDM_K_PERMUTE, [&] { k_permute<<<perm_grid, 256, perm_smem, stream>>>(P); })) != cudaSuccess)
+      return e;
+    for (int j = 0; j < nsub; ++j) {
+      if ((e = run(QRDM_K_PANEL, [&] { cudaLaunchKernelEx(&pc, k_panel, P, j); })) != cudaSuccess) return e;
+      if ((e = run(QRDM_K_TRAIL_W,
+                   [&] { k_trail_w<<<gemm_grid, GEMM_THREADS, TRAIL_W_SMEM, stream>>>(P, j); })) != cudaSuccess)
+        return e;
+      if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] { k_trail_wreduce<<<sms, GEMM_THREADS, 0, stream>>>(P, j); })) !=
+          cudaSuccess)
+        return e;
+      if ((e = run(QRDM_K_TRAIL_UPDATE, [&] { k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P, j); })) !=
+          cudaSuccess)
+        return e;
+    }
+    if ((e = run(QRDM_K_DOWNDATE, [&] { k_downdate<<<dd_grid, 256, 0, stream>>>(P); })) != cudaSuccess) return e;
+    return run(QRDM_K_STEP_END, [&] { k_step_end<<<1, 1, 0, stream>>>(P); });
+  };
+
+  // Steps are enqueued in batches; the state is read back once per batch.
+  // Kernels of steps past the end return at once (the state says done).
+  int64_t iters = 0, last_ns = 0;
+  int batch = 1;
+  bool dm_off = (k_max == 1);
+  for (;;) {
+    const int nsub = dm_off ? 1 : nsub_full;
+    for (int b = 0; b < batch; ++b) CK(enqueue_step(nsub));
+    iters += batch;
+    if (prof) CK(harvest(cur ^ 1));
     CK(cudaMemcpyAsync(&hs, P.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
-    if (prof) {
-      for (int kid : step_kernels) {
-        float msk = 0.f;
-        CK(cudaEventElapsedTime(&msk, ev[2 * kid], ev[2 * kid + 1]));
-        prof->ms[kid] += msk;
-        prof->launches[kid] += 1;
-      }
-      if (hs.ns > ns_prev) {
-        // algorithmic flops of the step that just ran (n_s was ns_prev)
-        const double mr = (double)(m - ns_prev), l = hs.l, k = hs.k, kc = hs.kc;
-        const double n2 = (double)(n - ns_prev) - k;
-        if (n2 > 0 && l > 0) {
-          prof->flops[QRDM_K_TRAIL_W] += 2.0 * mr * n2 * l;
-          prof->flops[QRDM_K_TRAIL_WREDUCE] += l * (l + 1.0) * n2;
-          prof->flops[QRDM_K_TRAIL_UPDATE] += 2.0 * mr * n2 * l;
-        }
-        if (kc > 1) prof->flops[QRDM_K_GRAM] += mr * kc * (kc + 1.0);
-        // panel: per reflector a reduction over k columns and an update of the rest
-        double pf = 0.0;
-        for (int64_t i = 0; i < (int64_t)l && i < (int64_t)k; ++i) pf += 2.0 * (mr - i) * (k + (k - i - 1));
-        prof->flops[QRDM_K_PANEL] += pf;
-      }
-    }
-    ns_prev = hs.ns;
-    if (hs.done) break;
+    if (prof) cur ^= 1;
+    if (hs.done || iters > kmin + 2) break;
+    dm_off = (hs.dm_on == 0);
+    // next batch: about half the steps the recent progress says remain
+    const int64_t adv = hs.ns - last_ns;
+    last_ns = hs.ns;
+    const double per = adv > 0 ? (double)adv / batch : 1.0;
+    int64_t guess = (int64_t)((double)(kmin - hs.ns) / per / 2.0);
+    batch = (int)(guess < 1 ? 1 : (guess > MAX_BATCH ? MAX_BATCH : guess));
+  }
+  if (prof) {
+    CK(harvest(cur ^ 1));
+    for (int i = 0; i < QRDM_NKERNELS; ++i) prof->flops[i] += hs.flops[i];
   }
   info->launches = launches;
   if (!hs.done) return QRDM_ERR_INTERNAL;

@@ -21,6 +21,7 @@ namespace cg = cooperative_groups;
 namespace qrdm {
 
 constexpr int KMAX = 128;          // largest supported k_max
+constexpr int PB = 16;             // sub-panel width of the blocked panel
 constexpr double EPS = 2.220446049250313080847e-16;  // 2^-52
 constexpr int PANEL_THREADS = 256;
 constexpr int GEMM_THREADS = 256;
@@ -44,7 +45,10 @@ struct alignas(128) DevState {
   int32_t l;        // reflectors accepted by the panel
   int32_t npairs;   // column moves of the permutation
   int32_t nonfinite;
-  int32_t pad;
+  int32_t pbreak;   // 1 once the panel's break test fired in this step
+  int32_t cur_lj;   // reflectors accepted by the current sub-panel (0: inactive)
+  int32_t pad[3];
+  double flops[16]; // algorithmic FP64 flops per kernel id (profile)
 };
 
 struct StepRecord {  // layout of qrdm_step_record
@@ -81,7 +85,13 @@ struct Params {
   int64_t trace_cap;
 };
 
-__device__ __forceinline__ double ld(const double* p) { return *p; }
+// kernel ids (same numbering as QRDM_K_* in the C header)
+enum KernelId {
+  KID_COLNORM = 0, KID_SELECT, KID_GRAM, KID_GRAM_REDUCE, KID_PICK, KID_PERMUTE, KID_PANEL, KID_TRAIL_W,
+  KID_TRAIL_WREDUCE, KID_TRAIL_UPDATE, KID_DOWNDATE, KID_STEP_END
+};
+
+__device__ __forceinline__ void add_flops(DevState* st, int kid, double f) { atomicAdd(&st->flops[kid], f); }
 
 // ---------------------------------------------------------------------------
 // a1: column norms u_j = ||a_j||, uref = u, perm = identity, anorm = max u.
@@ -105,6 +115,7 @@ __global__ void __launch_bounds__(256) k_colnorm_init(Params P) {
       P.u[j] = nr;
       P.uref[j] = nr;
       P.perm[j] = (int32_t)j;
+      if (j == 0) add_flops(P.st, KID_COLNORM, 2.0 * (double)P.m * (double)P.n);
       if (!isfinite(nr)) {
         P.st->nonfinite = 1;
       } else {
@@ -215,6 +226,11 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
     if (go && (st->ns >= P.kmin || (P.max_steps > 0 && st->step >= P.max_steps))) {
       st->done = 1;
       go = 0;
+    }
+    if (go) {
+      st->l = 0;
+      st->pbreak = 0;
+      st->cur_lj = 0;
     }
     s_ctl[0] = go;
   }
@@ -428,7 +444,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
 constexpr int GRAM_ROWS = 64;  // rows staged per pass
 
 __global__ void __launch_bounds__(256) k_gram(Params P) {
-  const DevState* st = P.st;
+  DevState* st = P.st;
   if (st->done) return;
   const int kc = st->kc;
   if (kc <= 1) return;
@@ -468,6 +484,7 @@ __global__ void __launch_bounds__(256) k_gram(Params P) {
       acc[q] = s;
     }
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(P.st, KID_GRAM, (double)mr * kc * (kc + 1.0));
   double* out = P.Gp + (int64_t)blockIdx.x * P.kmax * P.kmax;
   for (int q = 0; q < nper; ++q) {
     int e = threadIdx.x + q * blockDim.x;
@@ -510,14 +527,16 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
   __shared__ int s_np;
   __shared__ double s_mv[2 * KMAX][2];
   __shared__ int s_mvp[2 * KMAX];
+  extern __shared__ double s_g[];  // packed upper Gram matrix, kc*(kc+1)/2
   const int kc = st->kc;
   const int64_t ns = st->ns;
   const int tid = threadIdx.x, lane = tid & 31;
 
-  for (int a = tid; a < kc; a += blockDim.x) {
-    s_col[a] = P.cols[a];
-    s_d[a] = (kc > 1) ? sqrt(P.G[tri(a, a)]) : 1.0;
-  }
+  if (kc > 1)
+    for (int e = tid; e < kc * (kc + 1) / 2; e += blockDim.x) s_g[e] = P.G[e];
+  for (int a = tid; a < kc; a += blockDim.x) s_col[a] = P.cols[a];
+  __syncthreads();
+  for (int a = tid; a < kc; a += blockDim.x) s_d[a] = (kc > 1) ? sqrt(s_g[tri(a, a)]) : 1.0;
   __syncthreads();
   if (tid < 32) {
     double dlt = P.delta;
@@ -537,7 +556,7 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
         const int jb = s_J[b];
         const int lo = jb < a ? jb : a, hi = jb < a ? a : jb;
         const double d = da * s_d[jb];
-        double th = (d > 0.0) ? fabs(P.G[tri(lo, hi)] / d) : 1.0;
+        double th = (d > 0.0) ? fabs(s_g[tri(lo, hi)] / d) : 1.0;
         if (!(th < dlt)) ok = false;
       }
       if (__all_sync(0xffffffffu, ok)) {
@@ -653,70 +672,102 @@ __global__ void __launch_bounds__(256) k_permute(Params P) {
 }
 
 // ---------------------------------------------------------------------------
-// a7/a8: Householder panel with break check and the compact-WY T, on one
-// thread-block cluster.  CTA r of the cluster owns a contiguous slice of the
-// panel rows and only ever touches those rows.  Per reflector one cluster
-// barrier: every CTA reduces x^T [A panel] over its rows (x = current column
-// below the pivot) plus the pivot-row values, publishes the partial vector in
-// its shared memory, and after the barrier sums all partials (distributed
-// shared memory) in the same order, so every CTA derives identical scalars.
+// a7/a8: the Householder panel, blocked.  The k panel columns are factored in
+// sub-panels of PB columns; k_panel(j) factors sub-panel j on one thread-block
+// cluster, applying the break test of Alg. 4 with the panel-wide column index,
+// and builds the sub-panel's compact-WY T_j.  The trailing kernels then apply
+// (I - V_j T_j V_j^T)^T to every column right of the sub-panel (the rest of the
+// panel and the trailing matrix), which is right-looking blocked QR.
+//
+// CTA r of the cluster owns a contiguous slice of the rows and only touches
+// those rows.  Per reflector there is one cluster barrier: every CTA reduces
+// x^T [sub-panel] over its rows (x = current column below the pivot), plus
+// the pivot-row values, into a partial vector in its shared memory; after the
+// barrier each CTA gathers all partials (distributed shared memory) and sums
+// them in the same order, so all CTAs derive identical scalars and take the
+// same break decision.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P) {
+constexpr int MAX_CLUSTER = 16;
+
+__global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P, int j) {
   cg::cluster_group cluster = cg::this_cluster();
   DevState* st = P.st;
   if (st->done) return;  // uniform across the cluster
-  const int cs = (int)cluster.num_blocks();
-  const int crank = (int)cluster.block_rank();
-  const int64_t ns = st->ns, m = P.m, lda = P.lda;
   const int k = st->k;
-  const int64_t mr = m - ns;
+  const int jb = j * PB;
+  const int crank = (int)cluster.block_rank();
+  const int tid = threadIdx.x;
+  if (jb >= k || st->pbreak) {  // sub-panel beyond the panel, or the panel stopped
+    if (crank == 0 && tid == 0) st->cur_lj = 0;
+    return;
+  }
+  const int cs = (int)cluster.num_blocks();
+  const int w = min(PB, k - jb);
+  const int64_t m = P.m, lda = P.lda;
+  const int64_t r0 = st->ns + jb;  // the sub-panel's first row and first column
+  const int64_t mr = m - r0;
   const int64_t rpc = (mr + cs - 1) / cs;
-  const int64_t r0 = ns + (int64_t)crank * rpc;
-  const int64_t r1 = min(m, r0 + rpc);
-  __shared__ double s_slot[2][2 * KMAX];
-  __shared__ double s_tot[2 * KMAX];
-  __shared__ double s_y[KMAX];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t rb = r0 + (int64_t)crank * rpc;
+  const int64_t re = min(m, rb + rpc);
+  __shared__ double s_slot[2][2 * PB];
+  __shared__ double s_part[MAX_CLUSTER][2 * PB];
+  __shared__ double s_tot[2 * PB];
+  __shared__ double s_y[PB];
+  __shared__ double s_T[PB][PB];
+  const int lane = tid & 31, wp = tid >> 5;
   const int nw = PANEL_THREADS / 32;
   double* A = P.A;
   const double eps_s = st->eps_s;
-  int lacc = k;
-  for (int l = 0; l < k; ++l) {
-    const int64_t p = ns + l;  // pivot row and column
+  int lacc = w;
+  bool broke = false;
+  double flops = 0.0;
+  for (int l = 0; l < w; ++l) {
+    const int64_t p = r0 + l;  // pivot row and column
     const double* x = A + p * lda;
     double* slot = s_slot[l & 1];
-    const int64_t i0 = max(r0, p + 1);
-    const bool own_p = (p >= r0 && p < r1);
-    for (int t = w; t < k; t += nw) {
-      const double* ct = A + (ns + t) * lda;
+    const int64_t i0 = max(rb, p + 1);
+    const bool own_p = (p >= rb && p < re);
+    for (int t = wp; t < w; t += nw) {
+      const double* ct = A + (r0 + t) * lda;
       double acc = 0.0;
-      for (int64_t i = i0 + lane; i < r1; i += 32) acc = fma(x[i], ct[i], acc);
+      for (int64_t i = i0 + lane; i < re; i += 32) acc = fma(x[i], ct[i], acc);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) {
         slot[t] = acc;
-        slot[KMAX + t] = own_p ? ct[p] : 0.0;
+        slot[PB + t] = own_p ? ct[p] : 0.0;
       }
     }
     cluster.sync();
-    for (int e = tid; e < 2 * KMAX; e += PANEL_THREADS) {
-      int t = (e < KMAX) ? e : e - KMAX;
-      if (t >= k) continue;
-      double s = 0.0;
-      for (int c = 0; c < cs; ++c) {
+    // gather every CTA's partial vector in parallel, then sum in rank order
+    for (int e = tid; e < cs * 2 * PB; e += PANEL_THREADS) {
+      const int c = e / (2 * PB), f = e % (2 * PB);
+      const int t = (f < PB) ? f : f - PB;
+      if (t < w) {
         const double* rs = cluster.map_shared_rank(&s_slot[l & 1][0], c);
-        s += rs[e];
+        s_part[c][f] = rs[f];
       }
-      s_tot[e] = s;
     }
     __syncthreads();
-    const double alpha = s_tot[KMAX + l];
+    if (tid < 2 * PB) {
+      const int t = (tid < PB) ? tid : tid - PB;
+      if (t < w) {
+        double s = 0.0;
+        for (int c = 0; c < cs; ++c) s += s_part[c][tid];
+        s_tot[tid] = s;
+      }
+    }
+    __syncthreads();
+    const double alpha = s_tot[PB + l];
     const double s2 = s_tot[l];
-    const bool check = (l >= 1) && !P.no_break && (P.check_last ? (l < k) : (l + 1 < k));
+    const int lg = jb + l;  // column index within the whole panel
+    const bool check = (lg >= 1) && !P.no_break && (P.check_last ? (lg < k) : (lg + 1 < k));
+    flops += 2.0 * (double)(m - p - 1) * w;
     if (check) {
-      double nrm = sqrt(alpha * alpha + s2);
+      const double nrm = sqrt(alpha * alpha + s2);
       if (nrm < eps_s) {
         lacc = l;
+        broke = true;
         break;
       }
     }
@@ -726,59 +777,82 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P) {
       ht = 0.0;
       rden = 0.0;
     } else {
-      double nrm = sqrt(alpha * alpha + s2);
+      const double nrm = sqrt(alpha * alpha + s2);
       beta = (alpha >= 0.0) ? -nrm : nrm;
       ht = (beta - alpha) / beta;
       rden = 1.0 / (alpha - beta);
     }
-    // compact-WY T column l (rank-0 CTA): y_t = v_t^T v_l for t < l
+    // compact-WY T_j column l (rank-0 CTA): y_t = v_t^T v_l for t < l
     if (crank == 0) {
-      for (int t = tid; t < l; t += PANEL_THREADS) s_y[t] = s_tot[KMAX + t] + s_tot[t] * rden;
+      if (tid < l) s_y[tid] = s_tot[PB + tid] + s_tot[tid] * rden;
       __syncthreads();
-      double* Tc = P.T + (int64_t)l * KMAX;
-      for (int t = tid; t < l; t += PANEL_THREADS) {
-        double s = 0.0;
-        for (int q = t; q < l; ++q) s += P.T[(int64_t)q * KMAX + t] * s_y[q];
-        Tc[t] = (ht == 0.0) ? 0.0 : -ht * s;
+      if (tid < l) {
+        double sacc = 0.0;
+        for (int q = tid; q < l; ++q) sacc += s_T[tid][q] * s_y[q];
+        s_T[tid][l] = (ht == 0.0) ? 0.0 : -ht * sacc;
       }
       if (tid == 0) {
-        Tc[l] = ht;
+        s_T[l][l] = ht;
         P.htau[p] = ht;
       }
     }
-    // apply H_l to the remaining panel columns (own rows)
+    // apply H_l to the rest of the sub-panel (own rows)
     if (ht != 0.0) {
-      for (int t = l + 1 + w; t < k; t += nw) {
-        double* ct = A + (ns + t) * lda;
-        const double wt = s_tot[KMAX + t] + s_tot[t] * rden;
-        const double hw = ht * wt;
-        for (int64_t i = i0 + lane; i < r1; i += 32) ct[i] = fma(-hw, x[i] * rden, ct[i]);
+      for (int t = l + 1 + wp; t < w; t += nw) {
+        double* ct = A + (r0 + t) * lda;
+        const double hw = ht * (s_tot[PB + t] + s_tot[t] * rden);
+        for (int64_t i = i0 + lane; i < re; i += 32) ct[i] = fma(-hw, x[i] * rden, ct[i]);
         if (own_p && lane == 0) ct[p] -= hw;
       }
+      flops += 2.0 * (double)(m - p) * (w - l - 1);
     }
     __syncthreads();
-    // store v_l and beta
-    {
+    {  // store v_l (scaled tail) and beta
       double* xc = A + p * lda;
       if (ht != 0.0)
-        for (int64_t i = i0 + tid; i < r1; i += PANEL_THREADS) xc[i] = xc[i] * rden;
+        for (int64_t i = i0 + tid; i < re; i += PANEL_THREADS) xc[i] = xc[i] * rden;
       if (own_p && tid == 0) xc[p] = beta;
     }
     __syncthreads();
   }
-  if (crank == 0 && tid == 0) {
-    st->l = lacc;
-    if (P.trace && st->step < P.trace_cap) P.trace[st->step].l = lacc;
+  cluster.sync();  // every gather of this CTA's shared memory is done
+  if (crank == 0) {
+    for (int e = tid; e < lacc * lacc; e += PANEL_THREADS) {
+      const int r = e % lacc, c = e / lacc;
+      P.T[(int64_t)c * KMAX + r] = (r <= c) ? s_T[r][c] : 0.0;
+    }
+    if (tid == 0) {
+      st->cur_lj = lacc;
+      st->l += lacc;
+      if (broke) st->pbreak = 1;
+      if (P.trace && st->step < P.trace_cap) P.trace[st->step].l = st->l;
+      add_flops(st, KID_PANEL, flops);
+    }
   }
-  cluster.sync();  // no CTA leaves while others may still read its shared memory
 }
 
 // ---------------------------------------------------------------------------
-// a9: trailing update A22 -= V (T^T (V^T A22)), A22 = A[ns:m, ns+k:n].
-// V (mr x l) is unit lower trapezoidal, stored below the diagonal of the
-// panel columns.  Three kernels: partial W = V^T A22 over row chunks,
-// W = T^T sum(partials), A22 -= V W.  FFMA64 throughout.
+// a9: block reflector application after sub-panel j:
+//   A[r0:m, c0:n] -= V_j (T_j^T (V_j^T A[r0:m, c0:n])),
+// r0 = n_s + j PB (the sub-panel's first row and column), c0 = the first
+// column right of the sub-panel, l = reflectors the sub-panel accepted.
+// V_j (mr x l) is unit lower trapezoidal, stored below the diagonal of the
+// sub-panel columns.  Three kernels: partial W = V^T A over row chunks,
+// W = T^T sum(partials), A -= V W.  FFMA64 throughout.
 // ---------------------------------------------------------------------------
+struct SubGeom {
+  int64_t r0, c0;
+  int l;
+};
+
+__device__ __forceinline__ SubGeom sub_geom(const DevState* st, int j) {
+  SubGeom g;
+  const int k = st->k;
+  g.r0 = st->ns + (int64_t)j * PB;
+  g.c0 = st->ns + min((j + 1) * PB, k);
+  g.l = st->cur_lj;
+  return g;
+}
 constexpr int TW_COLS = 32;   // columns per W work unit
 constexpr int TW_SUB = 32;    // rows staged per pass
 constexpr int TU_ROWS = 64;   // update tile rows
@@ -878,14 +952,16 @@ __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int 
 
 constexpr int TRAIL_W_SMEM = (TW_SUB * (GEMM_THREADS + 1) + TW_SUB * (KMAX + 1)) * (int)sizeof(double);
 
-__global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P) {
-  const DevState* st = P.st;
+__global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P, int j) {
+  DevState* st = P.st;
   if (st->done) return;
-  const int l = st->l, k = st->k;
-  const int64_t ns = st->ns;
-  const int64_t j0 = ns + k;
+  const SubGeom sg = sub_geom(st, j);
+  const int l = sg.l;
+  const int64_t ns = sg.r0;  // base row/column of V
+  const int64_t j0 = sg.c0;
   const int64_t n2 = P.n - j0, mr = P.m - ns;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_W, 2.0 * (double)mr * (double)n2 * l);
   extern __shared__ double smw[];
   const WGeom g = w_geom(P, l, n2, mr);
   const int tg = w_tg(l);
@@ -920,15 +996,18 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P) {
   }
 }
 
-__global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P) {
-  const DevState* st = P.st;
+__global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j) {
+  DevState* st = P.st;
   if (st->done) return;
-  const int l = st->l, k = st->k;
-  const int64_t ns = st->ns, j0 = ns + k;
-  const int64_t n2 = P.n - j0, mr = P.m - ns;
+  const SubGeom sg = sub_geom(st, j);
+  const int l = sg.l;
+  const int64_t j0 = sg.c0;
+  const int64_t n2 = P.n - j0, mr = P.m - sg.r0;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
   const int64_t nct = (n2 + TW_COLS - 1) / TW_COLS;
   const int64_t nrc = w_geom(P, l, n2, mr).nrc;  // row chunks of k_trail_w
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    add_flops(st, KID_TRAIL_WREDUCE, (double)n2 * l * ((double)(nrc - 1) + (l + 1.0)));
   __shared__ double s_w[KMAX][TW_COLS + 1];
   const int tid = threadIdx.x;
   const int c = tid % TW_COLS, tg = tid / TW_COLS, TG = GEMM_THREADS / TW_COLS;
@@ -953,14 +1032,16 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P) {
   }
 }
 
-__global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P) {
-  const DevState* st = P.st;
+__global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P, int j) {
+  DevState* st = P.st;
   if (st->done) return;
-  const int l = st->l, k = st->k;
-  const int64_t ns = st->ns, m = P.m, lda = P.lda;
-  const int64_t j0 = ns + k;
+  const SubGeom sg = sub_geom(st, j);
+  const int l = sg.l;
+  const int64_t ns = sg.r0, m = P.m, lda = P.lda;
+  const int64_t j0 = sg.c0;
   const int64_t n2 = P.n - j0, mr = m - ns;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_UPDATE, 2.0 * (double)mr * (double)n2 * l);
   const int64_t nrt = (mr + TU_ROWS - 1) / TU_ROWS;
   const int64_t nct = (n2 + TU_COLS - 1) / TU_COLS;
   const int64_t units = nrt * nct;
@@ -1077,6 +1158,8 @@ __global__ void __launch_bounds__(256) k_downdate(Params P) {
   }
   if (lane == 0 && nrec && P.trace && st->step < P.trace_cap)
     atomicAdd((unsigned long long*)&P.trace[st->step].nrecomp, (unsigned long long)nrec);
+  if (lane == 0 && nrec) add_flops(st, KID_DOWNDATE, 2.0 * (double)(m - nsn) * nrec);
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_DOWNDATE, 3.0 * (double)l * (double)(P.n - ns - k));
 }
 
 // a11: end of a block step, n_s += l.  Runs after every other kernel of the
@@ -1102,6 +1185,9 @@ __global__ void k_state_init(Params P) {
   st->l = 0;
   st->kc = 0;
   st->npairs = 0;
+  st->pbreak = 0;
+  st->cur_lj = 0;
+  for (int i = 0; i < 16; ++i) st->flops[i] = 0.0;
 }
 
 }  // namespace qrdm
