@@ -519,7 +519,7 @@ __device__ __forceinline__ int tri(int a, int b) {  // packed upper index, a <= 
 __global__ void __launch_bounds__(256) k_pick(Params P) {
   DevState* st = P.st;
   if (st->done) return;
-  __shared__ double s_d[KMAX];   // column norms sqrt(G_aa)
+  __shared__ double s_d[KMAX];   // reciprocal column norms 1/sqrt(G_aa)
   __shared__ int s_col[KMAX];    // positions of the kc gathered columns
   __shared__ int s_J[KMAX];
   __shared__ int s_k;
@@ -536,7 +536,10 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
     for (int e = tid; e < kc * (kc + 1) / 2; e += blockDim.x) s_g[e] = P.G[e];
   for (int a = tid; a < kc; a += blockDim.x) s_col[a] = P.cols[a];
   __syncthreads();
-  for (int a = tid; a < kc; a += blockDim.x) s_d[a] = (kc > 1) ? sqrt(s_g[tri(a, a)]) : 1.0;
+  for (int a = tid; a < kc; a += blockDim.x) {
+    const double d = (kc > 1) ? sqrt(s_g[tri(a, a)]) : 1.0;
+    s_d[a] = (d > 0.0) ? 1.0 / d : 0.0;  // reciprocal norm; 0 marks a zero column
+  }
   __syncthreads();
   if (tid < 32) {
     double dlt = P.delta;
@@ -551,12 +554,13 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
     __syncwarp();
     for (int a = 1; a < kc; ++a) {
       bool ok = true;
-      const double da = s_d[a];
+      const double ra = s_d[a];
       for (int b = lane; b < k; b += 32) {
         const int jb = s_J[b];
         const int lo = jb < a ? jb : a, hi = jb < a ? a : jb;
-        const double d = da * s_d[jb];
-        double th = (d > 0.0) ? fabs(s_g[tri(lo, hi)] / d) : 1.0;
+        const double rr = ra * s_d[jb];
+        // |theta_ab| = |G_ab| / (||c_a|| ||c_b||); a zero column counts as |theta| = 1
+        const double th = (rr > 0.0) ? fabs(s_g[tri(lo, hi)]) * rr : 1.0;
         if (!(th < dlt)) ok = false;
       }
       if (__all_sync(0xffffffffu, ok)) {
@@ -714,6 +718,7 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P, int j) {
   __shared__ double s_tot[2 * PB];
   __shared__ double s_y[PB];
   __shared__ double s_T[PB][PB];
+  __shared__ double s_sc[8];
   const int lane = tid & 31, wp = tid >> 5;
   const int nw = PANEL_THREADS / 32;
   double* A = P.A;
@@ -758,30 +763,34 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P, int j) {
       }
     }
     __syncthreads();
-    const double alpha = s_tot[PB + l];
-    const double s2 = s_tot[l];
+    // the reflector's scalars, once per CTA (FP64 sqrt and division are long
+    // instruction sequences on this GPU; one thread computes, all read)
     const int lg = jb + l;  // column index within the whole panel
-    const bool check = (lg >= 1) && !P.no_break && (P.check_last ? (lg < k) : (lg + 1 < k));
-    flops += 2.0 * (double)(m - p - 1) * w;
-    if (check) {
+    if (tid == 0) {
+      const double alpha = s_tot[PB + l];
+      const double s2 = s_tot[l];
       const double nrm = sqrt(alpha * alpha + s2);
-      if (nrm < eps_s) {
-        lacc = l;
-        broke = true;
-        break;
+      const bool check = (lg >= 1) && !P.no_break && (P.check_last ? (lg < k) : (lg + 1 < k));
+      s_sc[4] = (check && nrm < eps_s) ? 1.0 : 0.0;
+      if (s2 == 0.0) {
+        s_sc[0] = alpha;  // beta
+        s_sc[1] = 0.0;    // htau
+        s_sc[2] = 0.0;    // 1 / (alpha - beta)
+      } else {
+        const double beta = (alpha >= 0.0) ? -nrm : nrm;
+        s_sc[0] = beta;
+        s_sc[1] = (beta - alpha) / beta;
+        s_sc[2] = 1.0 / (alpha - beta);
       }
     }
-    double beta, ht, rden;
-    if (s2 == 0.0) {
-      beta = alpha;
-      ht = 0.0;
-      rden = 0.0;
-    } else {
-      const double nrm = sqrt(alpha * alpha + s2);
-      beta = (alpha >= 0.0) ? -nrm : nrm;
-      ht = (beta - alpha) / beta;
-      rden = 1.0 / (alpha - beta);
+    __syncthreads();
+    flops += 2.0 * (double)(m - p - 1) * w;
+    if (s_sc[4] != 0.0) {  // break test of Alg. 4 (identical in every CTA)
+      lacc = l;
+      broke = true;
+      break;
     }
+    const double beta = s_sc[0], ht = s_sc[1], rden = s_sc[2];
     // compact-WY T_j column l (rank-0 CTA): y_t = v_t^T v_l for t < l
     if (crank == 0) {
       if (tid < l) s_y[tid] = s_tot[PB + tid] + s_tot[tid] * rden;
@@ -801,7 +810,8 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P, int j) {
       for (int t = l + 1 + wp; t < w; t += nw) {
         double* ct = A + (r0 + t) * lda;
         const double hw = ht * (s_tot[PB + t] + s_tot[t] * rden);
-        for (int64_t i = i0 + lane; i < re; i += 32) ct[i] = fma(-hw, x[i] * rden, ct[i]);
+        const double hwr = hw * rden;  // v_i = x_i / (alpha - beta) folded into the scale
+        for (int64_t i = i0 + lane; i < re; i += 32) ct[i] = fma(-hwr, x[i], ct[i]);
         if (own_p && lane == 0) ct[p] -= hw;
       }
       flops += 2.0 * (double)(m - p) * (w - l - 1);
