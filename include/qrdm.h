@@ -155,6 +155,41 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
                 double* d_htau, int32_t* d_perm, qrdm_info* info, const qrdm_opts* opts, void* d_work,
                 size_t work_bytes, void* stream, qrdm_step_record* d_trace, int32_t* d_trace_J, int64_t trace_cap);
 
+/*
+ * Size of the fixed device scratch used by qrdm_factor_noalloc: 32 MiB.
+ * A shape fits when qrdm_workspace_size(m, n, k_max) is at most this, e.g.
+ * 4096 x 4096 with k_max <= 32 or 2048 x 2048 with k_max <= 64.
+ */
+#define QRDM_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * qrdm_factor for callers that cannot allocate device memory: code that
+ * runs where cudaMalloc is unavailable or forbidden (inside a stream
+ * capture, under an allocator that owns the whole device, in a callback or
+ * a real-time loop), or that has no spare buffer to offer as workspace.
+ * The paper has no counterpart; this is a property of the library.
+ *
+ * Same arguments, outputs and error codes as qrdm_factor() minus d_work and
+ * work_bytes.  The workspace is one array of QRDM_NOALLOC_SCRATCH_BYTES in
+ * the library's device image; every GPU that loads the library holds it
+ * until the process exits, and the call itself allocates nothing.
+ *
+ *   - Shapes whose workspace exceeds the scratch are rejected with
+ *     QRDM_ERR_WORKSPACE before anything is touched.
+ *   - The first call on a device looks up the scratch's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one scratch.  Each call re-initializes every part
+ *     of it that it reads, so earlier contents do not matter, but calls whose
+ *     work overlaps on the GPU (other streams, other host threads) race on it:
+ *     serialize them.
+ *   - opts->profile must be NULL (profiling creates CUDA events):
+ *     QRDM_ERR_UNSUPPORTED otherwise.
+ */
+int qrdm_factor_noalloc(double* dA, int64_t m, int64_t n, int64_t lda, double tau, double delta, int32_t k_max,
+                        double* d_htau, int32_t* d_perm, qrdm_info* info, const qrdm_opts* opts, void* stream,
+                        qrdm_step_record* d_trace, int32_t* d_trace_J, int64_t trace_cap);
+
 /* Static description of an error code. */
 const char* qrdm_strerror(int code);
 

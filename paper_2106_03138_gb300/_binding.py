@@ -48,7 +48,9 @@ class qrdm_step_record(ctypes.Structure):
 
 
 # every symbol declared in include/qrdm.h
-EXPORTS = ("qrdm_workspace_size", "qrdm_factor", "qrdm_strerror", "qrdm_last_cuda_error", "qrdm_version")
+EXPORTS = ("qrdm_workspace_size", "qrdm_factor", "qrdm_factor_noalloc", "qrdm_strerror", "qrdm_last_cuda_error",
+           "qrdm_version")
+QRDM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 _lock = threading.Lock()
 _lib = None
@@ -74,6 +76,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.qrdm_factor.restype = ctypes.c_int
         lib.qrdm_factor.argtypes = [c_p, c_i64, c_i64, c_i64, c_f64, c_f64, c_i32, c_p, c_p, ctypes.POINTER(qrdm_info),
                                     ctypes.POINTER(qrdm_opts), c_p, c_sz, c_p, c_p, c_p, c_i64]
+        lib.qrdm_factor_noalloc.restype = ctypes.c_int
+        lib.qrdm_factor_noalloc.argtypes = [c_p, c_i64, c_i64, c_i64, c_f64, c_f64, c_i32, c_p, c_p,
+                                            ctypes.POINTER(qrdm_info), ctypes.POINTER(qrdm_opts), c_p, c_p, c_p,
+                                            c_i64]
         lib.qrdm_strerror.restype = ctypes.c_char_p
         lib.qrdm_strerror.argtypes = [ctypes.c_int]
         lib.qrdm_last_cuda_error.restype = ctypes.c_int
@@ -104,4 +110,15 @@ def qrdm_factor(dA: int, m: int, n: int, lda: int, tau: float, delta: float, k_m
     rc = load().qrdm_factor(dA, m, n, lda, tau, delta, k_max, d_htau, d_perm, ctypes.byref(info),
                             ctypes.byref(opts) if opts is not None else None, d_work, work_bytes, stream,
                             d_trace or None, d_trace_J or None, trace_cap)
+    return rc, info
+
+
+def qrdm_factor_noalloc(dA: int, m: int, n: int, lda: int, tau: float, delta: float, k_max: int, d_htau: int,
+                        d_perm: int, opts: qrdm_opts | None, stream: int, d_trace: int = 0, d_trace_J: int = 0,
+                        trace_cap: int = 0) -> tuple[int, qrdm_info]:
+    """Direct call of the allocation-free entry point (fixed device scratch)."""
+    info = qrdm_info()
+    rc = load().qrdm_factor_noalloc(dA, m, n, lda, tau, delta, k_max, d_htau, d_perm, ctypes.byref(info),
+                                    ctypes.byref(opts) if opts is not None else None, stream, d_trace or None,
+                                    d_trace_J or None, trace_cap)
     return rc, info

@@ -1,0 +1,99 @@
+// qrdm_factor_noalloc: the factorization for callers that cannot allocate
+// device memory.  Its workspace is a fixed array in this library's device
+// image (QRDM_NOALLOC_SCRATCH_BYTES, 32 MiB), held on every GPU that loads
+// the library until the process exits.  All calls share that array.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "../../include/qrdm.h"
+
+namespace {
+
+// The shared scratch.  In host code `g_scratch` only names the symbol; its
+// device address comes from cudaGetSymbolAddress, per device.
+static __device__ __align__(256) unsigned char g_scratch[QRDM_NOALLOC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+void* g_ptr[MAX_DEVICES] = {};
+
+// identity permutation for an empty matrix (m == 0 with n > 0)
+__global__ void k_iota(int32_t* perm, int64_t n) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    perm[j] = (int32_t)j;
+}
+
+// Device address of the scratch on the current device, looked up once.
+int scratch_address(void** out, int* cuda_err) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    *cuda_err = (int)e;
+    return QRDM_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= MAX_DEVICES) return QRDM_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+      *cuda_err = (int)e;
+      return QRDM_ERR_CUDA;
+    }
+    g_ptr[dev] = p;
+  }
+  *out = g_ptr[dev];
+  return QRDM_OK;
+}
+
+}  // namespace
+
+extern "C" int qrdm_factor_noalloc(double* dA, int64_t m, int64_t n, int64_t lda, double tau, double delta,
+                                   int32_t k_max, double* d_htau, int32_t* d_perm, qrdm_info* info,
+                                   const qrdm_opts* opts, void* stream, qrdm_step_record* d_trace,
+                                   int32_t* d_trace_J, int64_t trace_cap) {
+  if (opts && opts->profile) return QRDM_ERR_UNSUPPORTED;  // profiling creates CUDA events
+  if (m == 0 || n == 0) {
+    // nothing to factor: the same argument checks as qrdm_factor, then only
+    // the identity permutation is written
+    if (m < 0) return -1;
+    if (n < 0 || n > INT32_MAX) return -2;
+    if (lda < (m > 1 ? m : 1)) return -4;
+    if (!(tau > 0.0 && tau <= 1.0)) return -5;
+    if (!(delta >= 0.0 && delta <= 1.0)) return -6;
+    if (k_max < 1 || k_max > QRDM_KMAX_LIMIT) return -7;
+    if (!d_perm && n > 0) return -9;
+    if (!info) return -10;
+    if (opts && opts->eps1_mode != 0 && opts->eps1_mode != 1) return -11;
+    for (size_t i = 0; i < sizeof(*info); ++i) ((char*)info)[i] = 0;
+    if (n > 0) {
+      k_iota<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, (cudaStream_t)stream>>>(d_perm,
+                                                                                                        n);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+      if (e != cudaSuccess) {
+        info->cuda_error = (int32_t)e;
+        return QRDM_ERR_CUDA;
+      }
+    }
+    return QRDM_OK;
+  }
+  size_t need = 0;
+  if (m >= 0 && n >= 0 && n <= INT32_MAX && k_max >= 1 && k_max <= QRDM_KMAX_LIMIT) {
+    if (qrdm_workspace_size(m, n, k_max, &need) == 0 && need > (size_t)QRDM_NOALLOC_SCRATCH_BYTES)
+      return QRDM_ERR_WORKSPACE;  // this shape needs more than the fixed scratch holds
+  }
+  void* scratch = nullptr;
+  int cuda_err = 0;
+  int rc = scratch_address(&scratch, &cuda_err);
+  if (rc != QRDM_OK) {
+    if (info) info->cuda_error = cuda_err;
+    return rc;
+  }
+  // qrdm_factor validates every argument and re-initializes the whole step
+  // state in the workspace, so the previous call's contents do not matter.
+  return qrdm_factor(dA, m, n, lda, tau, delta, k_max, d_htau, d_perm, info, opts, scratch,
+                     (size_t)QRDM_NOALLOC_SCRATCH_BYTES, stream, d_trace, d_trace_J, trace_cap);
+}
