@@ -53,7 +53,8 @@ extern "C" {
 #define QRDM_K_TRAIL_UPDATE 9  /* a9: A22 -= V W */
 #define QRDM_K_DOWNDATE 10     /* a10: partial norm update */
 #define QRDM_K_STEP_END 11     /* a11: n_s += l */
-#define QRDM_NKERNELS 12
+#define QRDM_K_QRP_TAIL 12     /* a2..a11 fused for single-column steps (DM off or k_max = 1) */
+#define QRDM_NKERNELS 13
 
 /* Optional per-kernel timing (host struct, filled when opts->profile is set):
    every launch is bracketed by CUDA events on the caller's stream; ms[] sums

@@ -24,7 +24,7 @@ QRDM_KMAX_LIMIT = 128
 
 
 KERNEL_NAMES = ("k_colnorm_init", "k_select", "k_gram", "k_gram_reduce", "k_pick", "k_permute", "k_panel",
-                "k_trail_w", "k_trail_wreduce", "k_trail_update", "k_downdate", "k_step_end")
+                "k_trail_w", "k_trail_wreduce", "k_trail_update", "k_downdate", "k_step_end", "k_qrp_tail")
 
 
 class qrdm_profile(ctypes.Structure):

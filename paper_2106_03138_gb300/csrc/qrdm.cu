@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -18,6 +19,7 @@ namespace {
 thread_local int g_last_cuda = 0;
 
 constexpr int GRAM_CHUNKS_MAX = 256;
+constexpr int QRP_SMEM_MAX = 200 * 1024;  // pivot column of the fused single-column kernel
 constexpr int WCHUNKS = 16;
 constexpr size_t ALIGN = 256;
 
@@ -65,6 +67,8 @@ struct DeviceConfig {
   int device = -1;
   int sms = 0;
   int cluster = 0;  // panel cluster size
+  int coop = 0;     // cooperative launch supported
+  int qrp_grid = 0; // CTAs of the fused single-column kernel (one per SM)
   bool ok = false;
   cudaEvent_t ev[2 * QRDM_NKERNELS] = {};  // profile events, created on first use
   bool have_events = false;
@@ -113,6 +117,17 @@ int configure(DeviceConfig* cfg) {
     if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_panel, &lc) == cudaSuccess && ncl >= 1) c.cluster = 16;
   }
   cudaGetLastError();  // clear a refused non-portable query
+  e = cudaDeviceGetAttribute(&c.coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e != cudaSuccess) return (int)e;
+  if ((e = cudaFuncSetAttribute(k_qrp_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, QRP_SMEM_MAX)) !=
+      cudaSuccess)
+    return (int)e;
+  {
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qrp_tail, QRP_THREADS, QRP_SMEM_MAX);
+    if (e != cudaSuccess) return (int)e;
+    c.qrp_grid = (c.coop && per_sm >= 1) ? c.sms : 0;
+  }
   c.ok = true;
   g_cfg = c;
   *cfg = c;
@@ -384,6 +399,17 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     return run(QRDM_K_STEP_END, [&] { k_step_end<<<1, 1, 0, stream>>>(P); });
   };
 
+  // Single-column steps (DM off, or k_max = 1) run fused in one cooperative
+  // kernel when the pivot column fits in shared memory.
+  const bool qrp_fused = cfg.qrp_grid > 0 && (int64_t)m * (int64_t)sizeof(double) <= QRP_SMEM_MAX;
+  auto launch_qrp = [&]() -> cudaError_t {
+    void* args[] = {(void*)&P};
+    const size_t smem = (size_t)m * sizeof(double);
+    return run(QRDM_K_QRP_TAIL, [&] {
+      cudaLaunchCooperativeKernel((void*)k_qrp_tail, dim3(cfg.qrp_grid), dim3(QRP_THREADS), args, smem, stream);
+    });
+  };
+
   // Steps are enqueued in batches; the state is read back once per batch.
   // Kernels of steps past the end return at once (the state says done).
   int64_t iters = 0, last_ns = 0;
@@ -391,7 +417,14 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   bool dm_off = (k_max == 1);
   for (;;) {
     const int nsub = dm_off ? 1 : nsub_full;
-    for (int b = 0; b < batch; ++b) CK(enqueue_step(nsub));
+    if (dm_off && qrp_fused) {
+      if (getenv("QRDM_DEBUG"))
+        fprintf(stderr, "qrdm: fused single-column kernel from ns=%lld step=%lld (grid %d, smem %lld)\n",
+                (long long)hs.ns, (long long)hs.step, cfg.qrp_grid, (long long)(m * 8));
+      CK(launch_qrp());
+    } else {
+      for (int b = 0; b < batch; ++b) CK(enqueue_step(nsub));
+    }
     iters += batch;
     if (prof) CK(harvest(cur ^ 1));
     CK(cudaMemcpyAsync(&hs, P.st, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
@@ -411,8 +444,14 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     for (int i = 0; i < QRDM_NKERNELS; ++i) prof->flops[i] += hs.flops[i];
   }
   info->launches = launches;
-  if (!hs.done) return QRDM_ERR_INTERNAL;
-  if (hs.nonfinite) return QRDM_ERR_INTERNAL;
+  if (!hs.done || hs.nonfinite) {
+    if (getenv("QRDM_DEBUG"))
+      fprintf(stderr,
+              "qrdm: internal error: done=%d flag=%d diag_code=%d cta=%d step=%lld ns=%lld value=%lld gbar=%u\n",
+              hs.done, hs.nonfinite, hs.diag_code, hs.diag_cta, (long long)hs.diag_step, (long long)hs.diag_ns,
+              (long long)hs.diag_value, hs.gbar);
+    return QRDM_ERR_INTERNAL;
+  }
   info->rank = hs.rank >= 0 ? hs.rank : (hs.ns >= kmin ? kmin : hs.ns);
   info->rank_colmax = hs.rank_colmax >= 0 ? hs.rank_colmax : (hs.ns >= kmin ? kmin : hs.ns);
   info->nsteps = hs.step;

@@ -49,6 +49,14 @@ struct alignas(128) DevState {
   int32_t cur_lj;   // reflectors accepted by the current sub-panel (0: inactive)
   int32_t pad[3];
   double flops[16]; // algorithmic FP64 flops per kernel id (profile)
+  // grid barrier of the fused single-column kernel and its diagnostics
+  unsigned int gbar;     // arrivals (monotonic within one launch)
+  int32_t abort_flag;    // set when a barrier wait gave up or a check failed
+  int32_t diag_code;     // 1: barrier wait timed out, 2: pivot index out of range
+  int32_t diag_cta;
+  int64_t diag_step;
+  int64_t diag_ns;
+  int64_t diag_value;
 };
 
 struct StepRecord {  // layout of qrdm_step_record
@@ -88,7 +96,7 @@ struct Params {
 // kernel ids (same numbering as QRDM_K_* in the C header)
 enum KernelId {
   KID_COLNORM = 0, KID_SELECT, KID_GRAM, KID_GRAM_REDUCE, KID_PICK, KID_PERMUTE, KID_PANEL, KID_TRAIL_W,
-  KID_TRAIL_WREDUCE, KID_TRAIL_UPDATE, KID_DOWNDATE, KID_STEP_END
+  KID_TRAIL_WREDUCE, KID_TRAIL_UPDATE, KID_DOWNDATE, KID_STEP_END, KID_QRP_TAIL
 };
 
 __device__ __forceinline__ void add_flops(DevState* st, int kid, double f) { atomicAdd(&st->flops[kid], f); }
@@ -1172,6 +1180,289 @@ __global__ void __launch_bounds__(256) k_downdate(Params P) {
   if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_DOWNDATE, 3.0 * (double)l * (double)(P.n - ns - k));
 }
 
+// ---------------------------------------------------------------------------
+// Single-column pivoting steps (k = 1: every step once DM is off, or
+// k_max = 1 throughout) fused into one cooperative persistent kernel.  Per
+// step every CTA computes the argmax and the reflector redundantly (same data,
+// same order, so the same result), then CTA (c mod G) owns trailing position c:
+// it applies H to that column and updates its partial norm.  Two grid barriers
+// per step: after all CTAs have read the pivot column, and after all updates.
+// ---------------------------------------------------------------------------
+constexpr int QRP_THREADS = 256;
+constexpr long long GBAR_SPIN_LIMIT = 4000000000LL;  // clock cycles (about 2 s) before a wait gives up
+
+// Grid-wide barrier for a cooperative launch: arrival counter with release,
+// polling with acquire, bounded.  Returns false (and sets the abort flag)
+// when the wait gave up; every CTA then leaves its loop.
+__device__ __forceinline__ bool grid_barrier(DevState* st, unsigned int target, int64_t step, int64_t ns) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int* ctr = &st->gbar;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(1u) : "memory");
+    const long long t0 = clock64();
+    unsigned int cur = 0;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(ctr) : "memory");
+      if ((int)(cur - target) >= 0) break;
+      if (*(volatile int32_t*)&st->abort_flag) break;
+      if (clock64() - t0 > GBAR_SPIN_LIMIT) {
+        if (atomicExch(&st->abort_flag, 1) == 0) {
+          st->diag_code = 1;
+          st->diag_cta = (int)blockIdx.x;
+          st->diag_step = step;
+          st->diag_ns = ns;
+          st->diag_value = (int64_t)cur;
+        }
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  __syncthreads();
+  return *(volatile int32_t*)&st->abort_flag == 0;
+}
+
+__device__ __forceinline__ void qrp_block_argmax(const double* u, int64_t ns, int64_t n, double* s_v, int64_t* s_p,
+                                                 double* mu_out, int64_t* j_out) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  double bv = -1.0;
+  int64_t bp = INT64_MAX;
+  for (int64_t j = ns + tid; j < n; j += QRP_THREADS) {
+    const double x = u[j];
+    if (better(x, j, bv, bp)) {
+      bv = x;
+      bp = j;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const int64_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+    if (better(ov, op, bv, bp)) {
+      bv = ov;
+      bp = op;
+    }
+  }
+  if (lane == 0) {
+    s_v[w] = bv;
+    s_p[w] = bp;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    bv = s_v[0];
+    bp = s_p[0];
+    for (int q = 1; q < QRP_THREADS / 32; ++q)
+      if (better(s_v[q], s_p[q], bv, bp)) {
+        bv = s_v[q];
+        bp = s_p[q];
+      }
+    s_v[QRP_THREADS / 32] = bv;
+    s_p[QRP_THREADS / 32] = bp;
+  }
+  __syncthreads();
+  *mu_out = s_v[QRP_THREADS / 32];
+  *j_out = s_p[QRP_THREADS / 32];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(QRP_THREADS) k_qrp_tail(Params P) {
+  DevState* st = P.st;
+  extern __shared__ double s_x[];  // pivot column rows ns..m-1
+  __shared__ double s_v[QRP_THREADS / 32 + 1];
+  __shared__ int64_t s_p[QRP_THREADS / 32 + 1];
+  __shared__ double s_sc[8];
+  __shared__ double s_red[QRP_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int G = (int)gridDim.x, cta = (int)blockIdx.x;
+  const int64_t m = P.m, n = P.n, lda = P.lda, kmin = P.kmin;
+  double* A = P.A;
+  const double sqeps = sqrt(EPS);
+  if (st->done) return;  // uniform: read before any CTA writes it
+  int64_t ns = st->ns, step = st->step;
+  int dm_on = st->dm_on;
+  int64_t rank = st->rank, rank_cm = st->rank_colmax;
+  const double anorm = __longlong_as_double((long long)st->anorm_bits);
+  const double rhs = P.eps1 * anorm;
+  double flops = 0.0;
+  unsigned int bar = 0;  // barriers passed in this launch
+  bar += G;
+  if (!grid_barrier(st, bar, step, ns)) goto out;  // every CTA has read the state
+  for (;;) {
+    if (ns >= kmin || (P.max_steps > 0 && step >= P.max_steps)) break;
+    double mu;
+    int64_t jstar;
+    qrp_block_argmax(P.u, ns, n, s_v, s_p, &mu, &jstar);
+    if (jstar < ns || jstar >= n) {  // identical in every CTA
+      if (cta == 0 && tid == 0) {
+        st->abort_flag = 1;
+        st->diag_code = 2;
+        st->diag_cta = 0;
+        st->diag_step = step;
+        st->diag_ns = ns;
+        st->diag_value = jstar;
+      }
+      break;
+    }
+    // stopping test (Sec. 3.4) and the DM safeguard, identical in every CTA
+    const int64_t nrem = n - ns;
+    if (rank_cm < 0 && mu <= rhs) rank_cm = ns;
+    bool stop = false;
+    if (rank < 0 && sqrt((double)nrem) * mu <= rhs) {
+      rank = ns;
+      dm_on = 0;
+      if (P.stop_at_rank) stop = true;
+    }
+    if (stop) break;
+    // pivot column into shared memory, its tail norm and the reflector
+    const int64_t mr = m - ns;
+    const double* xc = A + jstar * lda + ns;
+    double part = 0.0;
+    for (int64_t i = tid; i < mr; i += QRP_THREADS) {
+      const double v = xc[i];
+      s_x[i] = v;
+      if (i > 0) part = fma(v, v, part);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) s_red[wp] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double s2 = 0.0;
+      for (int q = 0; q < QRP_THREADS / 32; ++q) s2 += s_red[q];
+      const double alpha = s_x[0];
+      if (s2 == 0.0) {
+        s_sc[0] = alpha;
+        s_sc[1] = 0.0;
+        s_sc[2] = 0.0;
+      } else {
+        const double nrm = sqrt(alpha * alpha + s2);
+        const double beta = (alpha >= 0.0) ? -nrm : nrm;
+        s_sc[0] = beta;
+        s_sc[1] = (beta - alpha) / beta;
+        s_sc[2] = 1.0 / (alpha - beta);
+      }
+    }
+    __syncthreads();
+    const double beta = s_sc[0], ht = s_sc[1], rden = s_sc[2];
+    bar += G;
+    if (!grid_barrier(st, bar, step, ns)) break;  // all CTAs have read column jstar
+    // the owner of position jstar moves the columns: ns <- pivot (R part, beta,
+    // v), jstar <- old column ns; it also swaps u, uref and perm
+    if ((int)(jstar % G) == cta) {
+      double* cn = A + ns * lda;
+      double* cj = A + jstar * lda;
+      if (jstar != ns) {
+        for (int64_t i = tid; i < ns; i += QRP_THREADS) {
+          const double a = cj[i], b = cn[i];
+          cn[i] = a;
+          cj[i] = b;
+        }
+        for (int64_t i = ns + tid; i < m; i += QRP_THREADS) cj[i] = cn[i];
+      }
+      __syncthreads();
+      for (int64_t i = ns + 1 + tid; i < m; i += QRP_THREADS) cn[i] = (ht != 0.0) ? s_x[i - ns] * rden : s_x[i - ns];
+      if (tid == 0) {
+        cn[ns] = beta;
+        if (jstar != ns) {
+          double t = P.u[ns];
+          P.u[ns] = P.u[jstar];
+          P.u[jstar] = t;
+          t = P.uref[ns];
+          P.uref[ns] = P.uref[jstar];
+          P.uref[jstar] = t;
+          const int32_t pt = P.perm[ns];
+          P.perm[ns] = P.perm[jstar];
+          P.perm[jstar] = pt;
+        }
+        P.htau[ns] = ht;
+        P.u[ns] = 0.0;
+        if (P.trace && step < P.trace_cap) {
+          StepRecord* r = P.trace + step;
+          r->ns = ns;
+          r->jstar = jstar;
+          r->ncand_all = 0;
+          r->ncand = 0;
+          r->k = 1;
+          r->l = 1;
+          r->dm_on = dm_on;
+          r->mu = mu;
+          r->eps_s = P.tau * mu;
+          if (P.traceJ) {
+            P.traceJ[step * P.kmax] = P.perm[ns];
+            for (int t2 = 1; t2 < P.kmax; ++t2) P.traceJ[step * P.kmax + t2] = -1;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // every CTA: apply H to its trailing positions (one warp per column) and
+    // update the partial norm (block downdate with recomputation, l = 1)
+    int nrec = 0;
+    {
+      // first position > ns owned by this CTA
+      int64_t c = ns + 1 + ((cta - (int)((ns + 1) % G)) % G + G) % G;
+      c += (int64_t)wp * G;
+      for (; c < n; c += (int64_t)G * (QRP_THREADS / 32)) {
+        double* ac = A + c * lda;
+        double wsum = 0.0;
+        if (ht != 0.0) {
+          for (int64_t i = ns + 1 + lane; i < m; i += 32) wsum = fma(s_x[i - ns] * rden, ac[i], wsum);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+          wsum += ac[ns];
+          const double hw = ht * wsum, hwr = hw * rden;
+          for (int64_t i = ns + 1 + lane; i < m; i += 32) ac[i] = fma(-hwr, s_x[i - ns], ac[i]);
+          __syncwarp();
+          if (lane == 0) ac[ns] -= hw;
+          __syncwarp();
+        }
+        const double uc = P.u[c];
+        if (uc != 0.0) {
+          const double x = ac[ns] / uc;
+          double t = 1.0 - x * x;
+          if (t < 0.0) t = 0.0;
+          const double ratio = uc / P.uref[c];
+          if (t * ratio * ratio <= sqeps) {
+            double s = 0.0;
+            for (int64_t i = ns + 1 + lane; i < m; i += 32) s = fma(ac[i], ac[i], s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) {
+              const double nr = sqrt(s);
+              P.u[c] = nr;
+              P.uref[c] = nr;
+              ++nrec;
+            }
+          } else if (lane == 0) {
+            P.u[c] = uc * sqrt(t);
+          }
+        }
+        __syncwarp();
+      }
+    }
+    if (lane == 0 && nrec && P.trace && step < P.trace_cap)
+      atomicAdd((unsigned long long*)&P.trace[step].nrecomp, (unsigned long long)nrec);
+    flops += 4.0 * (double)mr * (double)(n - ns - 1) / G + 2.0 * (double)mr;
+    bar += G;
+    if (!grid_barrier(st, bar, step, ns)) break;  // all columns and partial norms updated
+    ++ns;
+    ++step;
+  }
+out:
+  if (cta == 0 && tid == 0) {
+    if (*(volatile int32_t*)&st->abort_flag) st->nonfinite = 4;
+    st->ns = ns;
+    st->step = step;
+    st->dm_on = dm_on;
+    st->rank = rank;
+    st->rank_colmax = rank_cm;
+    st->k = 1;
+    st->l = 0;
+    st->done = 1;
+  }
+  if (tid == 0) add_flops(st, KID_QRP_TAIL, flops);
+}
+
 // a11: end of a block step, n_s += l.  Runs after every other kernel of the
 // step, so all of them saw the same n_s.
 __global__ void k_step_end(Params P) {
@@ -1198,6 +1489,13 @@ __global__ void k_state_init(Params P) {
   st->pbreak = 0;
   st->cur_lj = 0;
   for (int i = 0; i < 16; ++i) st->flops[i] = 0.0;
+  st->gbar = 0u;
+  st->abort_flag = 0;
+  st->diag_code = 0;
+  st->diag_cta = -1;
+  st->diag_step = -1;
+  st->diag_ns = -1;
+  st->diag_value = 0;
 }
 
 }  // namespace qrdm
