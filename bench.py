@@ -143,11 +143,13 @@ def traffic_for(kernel: str):
 
 
 def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    for f in ("qrdm_kernels.cuh", "qrdm.cu"):
-        with open(os.path.join(ROOT, "paper_2106_03138_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()
+    """sha256 of the trailing-update section of the kernel source (the code
+    of k_trail_w, k_trail_wreduce and k_trail_update)."""
+    with open(os.path.join(ROOT, "paper_2106_03138_gb300", "csrc", "qrdm_kernels.cuh")) as fh:
+        src = fh.read()
+    a = src.index("// a9: block reflector application")
+    b = src.index("// a10/a11: partial norm update")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()
 
 
 def dist_env():
@@ -183,6 +185,23 @@ def run_reference(args) -> int:
     return 0
 
 
+def run_profile_case(name: str, max_steps: int) -> int:
+    """One factorization of a named workload matrix (tau, delta, k_max as in
+    the benchmark), for capturing kernels under a profiler."""
+    import torch
+
+    import paper_2106_03138_gb300 as q
+    from paper_2106_03138_gb300 import inputs
+
+    A = inputs.named(name).build()
+    dA = q.colmajor(A)
+    f = q.factor(dA, TAU, DELTA, KMAX, max_steps=max_steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "m": A.shape[0], "n": A.shape[1], "steps": f.nsteps,
+                      "launches": f.launches}), flush=True)
+    return 0
+
+
 def config_dict(world: int) -> dict:
     return {"workload": WORKLOAD_DESC, "matrices": list(WORKLOAD), "tau": TAU, "delta": DELTA, "k_max": KMAX,
             "global_batch": 3 * world, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -197,9 +216,14 @@ def main() -> int:
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--profile-case", default=None,
+                    help="factor one named matrix once at the benchmark's parameters and exit (profiler target)")
+    ap.add_argument("--max-steps", type=int, default=0, help="with --profile-case: stop after this many block steps")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args.profile_case, args.max_steps)
 
     import numpy as np
     import torch
@@ -257,6 +281,7 @@ def main() -> int:
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t_wall0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("timed")
         for _ in range(args.steps):
             restore()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -267,6 +292,7 @@ def main() -> int:
             e1.synchronize()
             launches += nl
             step_ms.append(e0.elapsed_time(e1))
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
     if world > 1:
