@@ -102,7 +102,11 @@ int configure(DeviceConfig* cfg) {
     return (int)e;
   // panel cluster: 16 CTAs when the device allows it, else 8
   c.cluster = 8;
-  if (cudaFuncSetAttribute(k_panel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+  if ((e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_MAX)) !=
+      cudaSuccess)
+    return (int)e;
+  if (cudaFuncSetAttribute(k_panel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(k_panel_g, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
     cudaLaunchConfig_t lc = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -111,10 +115,15 @@ int configure(DeviceConfig* cfg) {
     at[0].val.clusterDim.z = 1;
     lc.gridDim = dim3(16);
     lc.blockDim = dim3(PANEL_THREADS);
+    lc.dynamicSmemBytes = PANEL_SMEM_MAX;
     lc.attrs = at;
     lc.numAttrs = 1;
-    int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_panel, &lc) == cudaSuccess && ncl >= 1) c.cluster = 16;
+    int ncl = 0, ncl_g = 0;
+    lc.dynamicSmemBytes = PANEL_SMEM_MAX;
+    const bool ok_s = cudaOccupancyMaxActiveClusters(&ncl, (void*)k_panel, &lc) == cudaSuccess && ncl >= 1;
+    lc.dynamicSmemBytes = 0;
+    const bool ok_g = cudaOccupancyMaxActiveClusters(&ncl_g, (void*)k_panel_g, &lc) == cudaSuccess && ncl_g >= 1;
+    if (ok_s && ok_g) c.cluster = 16;
   }
   cudaGetLastError();  // clear a refused non-portable query
   e = cudaDeviceGetAttribute(&c.coop, cudaDevAttrCooperativeLaunch, dev);
@@ -320,7 +329,11 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   pat[0].val.clusterDim.z = 1;
   pc.gridDim = dim3(cfg.cluster);
   pc.blockDim = dim3(PANEL_THREADS);
-  pc.dynamicSmemBytes = 0;
+  // each CTA holds ceil(m / cluster) rows of up to PB columns in shared memory
+  const int64_t panel_lds = ((m + cfg.cluster - 1) / cfg.cluster) | 1;
+  const int64_t panel_smem = (int64_t)PB * panel_lds * (int64_t)sizeof(double);
+  const bool panel_in_smem = panel_smem <= PANEL_SMEM_MAX;
+  pc.dynamicSmemBytes = panel_in_smem ? (size_t)panel_smem : 0;
   pc.stream = stream;
   pc.attrs = pat;
   pc.numAttrs = 1;
@@ -384,7 +397,13 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     if ((e = run(QRDM_K_PERMUTE, [&] { k_permute<<<perm_grid, 256, perm_smem, stream>>>(P); })) != cudaSuccess)
       return e;
     for (int j = 0; j < nsub; ++j) {
-      if ((e = run(QRDM_K_PANEL, [&] { cudaLaunchKernelEx(&pc, k_panel, P, j); })) != cudaSuccess) return e;
+      if ((e = run(QRDM_K_PANEL, [&] {
+             if (panel_in_smem)
+               cudaLaunchKernelEx(&pc, k_panel, P, j);
+             else
+               cudaLaunchKernelEx(&pc, k_panel_g, P, j);
+           })) != cudaSuccess)
+        return e;
       if ((e = run(QRDM_K_TRAIL_W,
                    [&] { k_trail_w<<<gemm_grid, GEMM_THREADS, TRAIL_W_SMEM, stream>>>(P, j); })) != cudaSuccess)
         return e;

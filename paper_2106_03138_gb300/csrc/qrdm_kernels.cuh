@@ -700,8 +700,23 @@ __global__ void __launch_bounds__(256) k_permute(Params P) {
 // same break decision.
 // ---------------------------------------------------------------------------
 constexpr int MAX_CLUSTER = 16;
+constexpr int PANEL_SMEM_MAX = 200 * 1024;  // sub-panel slice held in shared memory up to this size
 
-__global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P, int j) {
+// Element (i, t) of the sub-panel: absolute row i, sub-panel column t.  With
+// SMEM the CTA's rows [rb, re) live in shared memory (column stride lds).
+template <bool SMEM>
+struct PanelView {
+  double* base;  // SMEM: shared slice; else: A
+  int64_t ld;    // SMEM: lds; else: lda
+  int64_t rb;    // SMEM: first row held; else: 0
+  int64_t c0;    // first column (absolute) of the sub-panel
+  __device__ __forceinline__ double& at(int64_t i, int t) const {
+    return SMEM ? base[(int64_t)t * ld + (i - rb)] : base[(c0 + t) * ld + i];
+  }
+};
+
+template <bool SMEM>
+__device__ __forceinline__ void panel_body(Params& P, int j) {
   cg::cluster_group cluster = cg::this_cluster();
   DevState* st = P.st;
   if (st->done) return;  // uniform across the cluster
@@ -727,28 +742,46 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P, int j) {
   __shared__ double s_y[PB];
   __shared__ double s_T[PB][PB];
   __shared__ double s_sc[8];
+  extern __shared__ double s_pan[];  // SMEM: [PB][lds]
   const int lane = tid & 31, wp = tid >> 5;
   const int nw = PANEL_THREADS / 32;
   double* A = P.A;
+  PanelView<SMEM> V;
+  if (SMEM) {
+    const int64_t lds = ((m + cs - 1) / cs) | 1;  // odd stride: spreads columns over banks
+    V.base = s_pan;
+    V.ld = lds;
+    V.rb = rb;
+    V.c0 = r0;
+    // this CTA's rows of the sub-panel, columns in rows (coalesced)
+    for (int t = wp; t < w; t += nw) {
+      const double* src = A + (r0 + t) * lda;
+      for (int64_t i = rb + lane; i < re; i += 32) V.at(i, t) = src[i];
+    }
+    __syncthreads();
+  } else {
+    V.base = A;
+    V.ld = lda;
+    V.rb = 0;
+    V.c0 = r0;
+  }
   const double eps_s = st->eps_s;
   int lacc = w;
   bool broke = false;
   double flops = 0.0;
   for (int l = 0; l < w; ++l) {
     const int64_t p = r0 + l;  // pivot row and column
-    const double* x = A + p * lda;
     double* slot = s_slot[l & 1];
     const int64_t i0 = max(rb, p + 1);
     const bool own_p = (p >= rb && p < re);
     for (int t = wp; t < w; t += nw) {
-      const double* ct = A + (r0 + t) * lda;
       double acc = 0.0;
-      for (int64_t i = i0 + lane; i < re; i += 32) acc = fma(x[i], ct[i], acc);
+      for (int64_t i = i0 + lane; i < re; i += 32) acc = fma(V.at(i, l), V.at(i, t), acc);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) {
         slot[t] = acc;
-        slot[PB + t] = own_p ? ct[p] : 0.0;
+        slot[PB + t] = own_p ? V.at(p, t) : 0.0;
       }
     }
     cluster.sync();
@@ -816,22 +849,25 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P, int j) {
     // apply H_l to the rest of the sub-panel (own rows)
     if (ht != 0.0) {
       for (int t = l + 1 + wp; t < w; t += nw) {
-        double* ct = A + (r0 + t) * lda;
         const double hw = ht * (s_tot[PB + t] + s_tot[t] * rden);
         const double hwr = hw * rden;  // v_i = x_i / (alpha - beta) folded into the scale
-        for (int64_t i = i0 + lane; i < re; i += 32) ct[i] = fma(-hwr, x[i], ct[i]);
-        if (own_p && lane == 0) ct[p] -= hw;
+        for (int64_t i = i0 + lane; i < re; i += 32) V.at(i, t) = fma(-hwr, V.at(i, l), V.at(i, t));
+        if (own_p && lane == 0) V.at(p, t) -= hw;
       }
       flops += 2.0 * (double)(m - p) * (w - l - 1);
     }
     __syncthreads();
-    {  // store v_l (scaled tail) and beta
-      double* xc = A + p * lda;
-      if (ht != 0.0)
-        for (int64_t i = i0 + tid; i < re; i += PANEL_THREADS) xc[i] = xc[i] * rden;
-      if (own_p && tid == 0) xc[p] = beta;
-    }
+    // store v_l (scaled tail) and beta
+    if (ht != 0.0)
+      for (int64_t i = i0 + tid; i < re; i += PANEL_THREADS) V.at(i, l) = V.at(i, l) * rden;
+    if (own_p && tid == 0) V.at(p, l) = beta;
     __syncthreads();
+  }
+  if (SMEM) {  // write the slice back
+    for (int t = wp; t < w; t += nw) {
+      double* dst = A + (r0 + t) * lda;
+      for (int64_t i = rb + lane; i < re; i += 32) dst[i] = V.at(i, t);
+    }
   }
   cluster.sync();  // every gather of this CTA's shared memory is done
   if (crank == 0) {
@@ -848,6 +884,10 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P, int j) {
     }
   }
 }
+
+// the sub-panel slice in shared memory (when it fits) or in global memory
+__global__ void __launch_bounds__(PANEL_THREADS) k_panel(Params P, int j) { panel_body<true>(P, j); }
+__global__ void __launch_bounds__(PANEL_THREADS) k_panel_g(Params P, int j) { panel_body<false>(P, j); }
 
 // ---------------------------------------------------------------------------
 // a9: block reflector application after sub-panel j:
