@@ -159,12 +159,32 @@ def dist_env():
     return world, rank, local
 
 
-def run_reference(args) -> int:
-    """The oracle timed on the host cores, one bounded CPU sample per step."""
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over all ranks of the default process group (the
+    benchmark's step time is the slowest replica's)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gflops(world: int, flops_per_step: float, steps: int, total_ms: float) -> float:
+    """Whole-job GFLOP/s: every replica factors the workload once per step;
+    the job takes as long as the slowest replica."""
+    return world * flops_per_step * steps / (total_ms * 1e-3) / 1e9
+
+
+def run_reference(args, sample=None) -> int:
+    """The oracle timed on the host cores, one bounded CPU sample per step.
+    Under torchrun only rank 0 runs; the other ranks exit at once."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    mats = cpu_sample_matrices()
+    mats = cpu_sample_matrices() if sample is None else sample
     for _ in range(args.warmup):
         time_oracle_sample(mats)
     secs, fl = 0.0, 0.0
@@ -298,12 +318,8 @@ def main() -> int:
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * flops_step * args.steps / (total_ms * 1e-3) / 1e9
+    total_ms = max_over_ranks(sum(step_ms), device=dev)
+    value = aggregate_gflops(world, flops_step, args.steps, total_ms)
 
     # dominant kernel and its roofline (FP64 ALU bound)
     ms = list(prof.ms)
@@ -354,7 +370,7 @@ def main() -> int:
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    e2e_value = world * flops_step * e2e_steps / (e2e_ms * 1e-3) / 1e9
+    e2e_value = aggregate_gflops(world, flops_step, e2e_steps, max_over_ranks(e2e_ms, device=dev))
 
     comparators = {}
     if not args.no_comparators and rank == 0:
