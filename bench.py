@@ -205,7 +205,7 @@ def run_reference(args, sample=None) -> int:
     return 0
 
 
-def run_profile_case(name: str, max_steps: int) -> int:
+def run_profile_case(name: str, max_steps: int, precision: int = 0) -> int:
     """One factorization of a named workload matrix (tau, delta, k_max as in
     the benchmark), for capturing kernels under a profiler."""
     import torch
@@ -215,9 +215,9 @@ def run_profile_case(name: str, max_steps: int) -> int:
 
     A = inputs.named(name).build()
     dA = q.colmajor(A)
-    f = q.factor(dA, TAU, DELTA, KMAX, max_steps=max_steps)
+    f = q.factor(dA, TAU, DELTA, KMAX, max_steps=max_steps, precision=precision)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": name, "m": A.shape[0], "n": A.shape[1], "steps": f.nsteps,
+    print(json.dumps({"profile_case": name, "precision": precision, "m": A.shape[0], "n": A.shape[1], "steps": f.nsteps,
                       "launches": f.launches}), flush=True)
     return 0
 
@@ -239,11 +239,12 @@ def main() -> int:
     ap.add_argument("--profile-case", default=None,
                     help="factor one named matrix once at the benchmark's parameters and exit (profiler target)")
     ap.add_argument("--max-steps", type=int, default=0, help="with --profile-case: stop after this many block steps")
+    ap.add_argument("--precision", type=int, default=0, help="with --profile-case: 0 FP64, 1 FP32-class mixed")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_case:
-        return run_profile_case(args.profile_case, args.max_steps)
+        return run_profile_case(args.profile_case, args.max_steps, args.precision)
 
     import numpy as np
     import torch

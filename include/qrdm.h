@@ -89,7 +89,14 @@ typedef struct qrdm_opts {
   int32_t sdd;
   /* > 0: stop after this many block steps (partial factorization). */
   int32_t max_steps;
-  int32_t reserved0;
+  /* 0 (default): everything in FP64.  1: FP32-class mixed precision: the
+     trailing update and the candidate Gram matrix convert their FP64
+     operands to FP32 on load and accumulate in FP32 (A stays FP64 and is
+     updated in FP64); reflectors, panel, partial norms, recomputation and the
+     rank decision stay FP64.  The stopping criterion then uses
+     eps1 = max(eps1, 8 * 2^-24 * sqrt(n)), since FP32 updates leave roundoff
+     of about 2^-24 ||A|| in the trailing block. */
+  int32_t precision;
   int32_t reserved1;
   /* host, optional: per-kernel event timing (see qrdm_profile). */
   qrdm_profile* profile;

@@ -33,7 +33,7 @@ class qrdm_profile(ctypes.Structure):
 
 class qrdm_opts(ctypes.Structure):
     _fields_ = [("eps1_mode", c_i32), ("stop_at_rank", c_i32), ("check_last", c_i32), ("no_break", c_i32),
-                ("sdd", c_i32), ("max_steps", c_i32), ("reserved0", c_i32), ("reserved1", c_i32),
+                ("sdd", c_i32), ("max_steps", c_i32), ("precision", c_i32), ("reserved1", c_i32),
                 ("profile", ctypes.POINTER(qrdm_profile))]
 
 

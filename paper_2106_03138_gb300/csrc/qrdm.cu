@@ -93,6 +93,14 @@ int configure(DeviceConfig* cfg) {
   const int gram_smem = (int)(KMAX * (GRAM_ROWS + 1) * sizeof(double));
   if ((e = cudaFuncSetAttribute(k_trail_w, cudaFuncAttributeMaxDynamicSharedMemorySize, TRAIL_W_SMEM)) != cudaSuccess)
     return (int)e;
+  if ((e = cudaFuncSetAttribute(k_trail_w32, cudaFuncAttributeMaxDynamicSharedMemorySize, S32_SMEM)) != cudaSuccess)
+    return (int)e;
+  if ((e = cudaFuncSetAttribute(k_trail_update32, cudaFuncAttributeMaxDynamicSharedMemorySize, S32_SMEM)) !=
+      cudaSuccess)
+    return (int)e;
+  if ((e = cudaFuncSetAttribute(k_gram32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(KMAX * (GRAM_ROWS + 1) * sizeof(double)))) != cudaSuccess)
+    return (int)e;
   const int pick_smem_max = (int)(KMAX * (KMAX + 1) / 2 * sizeof(double));
   if ((e = cudaFuncSetAttribute(k_pick, cudaFuncAttributeMaxDynamicSharedMemorySize, pick_smem_max)) != cudaSuccess)
     return (int)e;
@@ -208,6 +216,7 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
   if (o.eps1_mode != 0 && o.eps1_mode != 1) return -11;
+  if (o.precision != 0 && o.precision != 1) return -11;
   cudaStream_t stream = (cudaStream_t)stream_;
 
   if (n == 0 || m == 0) {
@@ -256,6 +265,14 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   P.tau = tau;
   P.delta = delta;
   P.eps1 = (o.eps1_mode == 1) ? EPS * sqrt((double)n) : EPS * (double)n;
+  if (o.precision == 1) {
+    // FP32-class updates leave roundoff of about 2^-24 ||A|| in the trailing
+    // block; the rank threshold must sit above it
+    const double e32 = 8.0 * 5.9604644775390625e-8 * sqrt((double)n);
+    if (e32 > P.eps1) P.eps1 = e32;
+  }
+  const bool mixed = (o.precision == 1);
+  P.mixed = mixed ? 1 : 0;
   P.kmax = k_max;
   P.stop_at_rank = o.stop_at_rank;
   P.check_last = o.check_last;
@@ -389,7 +406,12 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   auto enqueue_step = [&](int nsub) -> cudaError_t {
     cudaError_t e;
     if ((e = run(QRDM_K_SELECT, [&] { k_select<<<1, SEL_THREADS, 0, stream>>>(P); })) != cudaSuccess) return e;
-    if ((e = run(QRDM_K_GRAM, [&] { k_gram<<<P.gram_chunks, 256, gram_smem, stream>>>(P); })) != cudaSuccess)
+    if ((e = run(QRDM_K_GRAM, [&] {
+           if (mixed)
+             k_gram32<<<P.gram_chunks, 256, gram_smem, stream>>>(P);
+           else
+             k_gram<<<P.gram_chunks, 256, gram_smem, stream>>>(P);
+         })) != cudaSuccess)
       return e;
     if ((e = run(QRDM_K_GRAM_REDUCE, [&] { k_gram_reduce<<<gred_grid, 256, 0, stream>>>(P); })) != cudaSuccess)
       return e;
@@ -404,14 +426,22 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
                cudaLaunchKernelEx(&pc, k_panel_g, P, j);
            })) != cudaSuccess)
         return e;
-      if ((e = run(QRDM_K_TRAIL_W,
-                   [&] { k_trail_w<<<gemm_grid, GEMM_THREADS, TRAIL_W_SMEM, stream>>>(P, j); })) != cudaSuccess)
+      if ((e = run(QRDM_K_TRAIL_W, [&] {
+             if (mixed)
+               k_trail_w32<<<gemm_grid, GEMM_THREADS, S32_SMEM, stream>>>(P, j);
+             else
+               k_trail_w<<<gemm_grid, GEMM_THREADS, TRAIL_W_SMEM, stream>>>(P, j);
+           })) != cudaSuccess)
         return e;
       if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] { k_trail_wreduce<<<sms, GEMM_THREADS, 0, stream>>>(P, j); })) !=
           cudaSuccess)
         return e;
-      if ((e = run(QRDM_K_TRAIL_UPDATE, [&] { k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P, j); })) !=
-          cudaSuccess)
+      if ((e = run(QRDM_K_TRAIL_UPDATE, [&] {
+             if (mixed)
+               k_trail_update32<<<gemm_grid, GEMM_THREADS, S32_SMEM, stream>>>(P, j);
+             else
+               k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P, j);
+           })) != cudaSuccess)
         return e;
     }
     if ((e = run(QRDM_K_DOWNDATE, [&] { k_downdate<<<dd_grid, 256, 0, stream>>>(P); })) != cudaSuccess) return e;

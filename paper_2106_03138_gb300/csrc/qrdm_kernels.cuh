@@ -86,7 +86,7 @@ struct Params {
   int32_t gram_chunks;  // CTAs of k_gram (= partial Gram matrices)
   int32_t wchunks;      // most row chunks of the W phase
   int32_t w_units;      // target work units of the W phase (same in k_trail_w and k_trail_wreduce)
-  int32_t pad0;
+  int32_t mixed;        // 1: FP32-class trailing update and Gram (geometry of k_trail_w32)
   // optional trace
   StepRecord* trace;
   int32_t* traceJ;
@@ -100,6 +100,47 @@ enum KernelId {
 };
 
 __device__ __forceinline__ void add_flops(DevState* st, int kid, double f) { atomicAdd(&st->flops[kid], f); }
+
+// FP64 <-> FP32 by integer operations on the IEEE-754 fields.  GB300 executes
+// F2F conversions that involve FP64 on its narrow FP64 pipe (about 2 per clock
+// per SM), which would bound the streaming FP32-class kernels; the integer
+// pipe is far wider.  Finite inputs only (the matrix is checked on entry).
+//   to FP32: the magnitude's exponent|mantissa field is rounded to 23 mantissa
+//   bits by adding half a unit of the last kept bit (round to nearest, ties
+//   away from zero; a carry moves into the exponent as it should), then the
+//   exponent is rebiased; magnitudes below 2^-126 flush to a signed zero.
+//   to FP64: exact; FP32 subnormals (never produced with flushing) map to zero.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+  const long long em = (long long)((mag + (1ull << 28)) >> 29) - ((long long)(1023 - 127) << 23);
+  unsigned bits = sign | (unsigned)em;
+  bits = (em < (1ll << 23)) ? sign : bits;  // biased FP32 exponent <= 0: flush to signed zero
+  bits = (em >= (255ll << 23)) ? (sign | 0x7F800000u) : bits;
+  return __uint_as_float(bits);
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned mant = b & 0x7FFFFFu;
+  unsigned hi = sign | ((e + (1023u - 127u)) << 20) | (mant >> 3);
+  unsigned lo = mant << 29;
+  hi = (e == 0u) ? sign : hi;
+  lo = (e == 0u) ? 0u : lo;
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
+// operand load in a kernel's compute type
+__device__ __forceinline__ double to_tc(double x, double) { return x; }
+__device__ __forceinline__ float to_tc(double x, float) { return f64_to_f32_rn(x); }
+
+// multiply-add in the compute type of a kernel (FP64, or FP32 in the
+// mixed-precision form)
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
 
 // ---------------------------------------------------------------------------
 // a1: column norms u_j = ||a_j||, uref = u, perm = identity, anorm = max u.
@@ -451,19 +492,21 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
 // ---------------------------------------------------------------------------
 constexpr int GRAM_ROWS = 64;  // rows staged per pass
 
-__global__ void __launch_bounds__(256) k_gram(Params P) {
+template <typename TC>
+__device__ __forceinline__ void gram_body(Params& P) {
   DevState* st = P.st;
   if (st->done) return;
   const int kc = st->kc;
   if (kc <= 1) return;
   const int64_t ns = st->ns, m = P.m;
   const int64_t mr = m - ns;
-  extern __shared__ double smg[];  // [kc][GRAM_ROWS + 1]
+  extern __shared__ double smg_raw[];
+  TC* smg = reinterpret_cast<TC*>(smg_raw);  // [kc][GRAM_ROWS + 1]
   const int LDS = GRAM_ROWS + 1;
   const int npairs = kc * (kc + 1) / 2;
-  double acc[(KMAX * (KMAX + 1) / 2 + 255) / 256];
+  TC acc[(KMAX * (KMAX + 1) / 2 + 255) / 256];
   const int nper = (npairs + blockDim.x - 1) / blockDim.x;
-  for (int q = 0; q < nper; ++q) acc[q] = 0.0;
+  for (int q = 0; q < nper; ++q) acc[q] = (TC)0;
   const int64_t nchunks = (mr + GRAM_ROWS - 1) / GRAM_ROWS;
   // chunk c of this CTA: c = blockIdx.x, blockIdx.x + gridDim.x, ...
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
@@ -474,7 +517,7 @@ __global__ void __launch_bounds__(256) k_gram(Params P) {
       int a = e / GRAM_ROWS, i = e % GRAM_ROWS;
       double x = 0.0;
       if (i < rows) x = P.A[(int64_t)P.cols[a] * P.lda + r0 + i];
-      smg[a * LDS + i] = x;
+      smg[a * LDS + i] = to_tc(x, (TC)0);
     }
     __syncthreads();
     for (int q = 0; q < nper; ++q) {
@@ -485,10 +528,10 @@ __global__ void __launch_bounds__(256) k_gram(Params P) {
       while ((b + 1) * (b + 2) / 2 <= e) ++b;
       while (b * (b + 1) / 2 > e) --b;
       int a = e - b * (b + 1) / 2;
-      const double* xa = smg + a * LDS;
-      const double* xb = smg + b * LDS;
-      double s = acc[q];
-      for (int i = 0; i < rows; ++i) s = fma(xa[i], xb[i], s);
+      const TC* xa = smg + a * LDS;
+      const TC* xb = smg + b * LDS;
+      TC s = acc[q];
+      for (int i = 0; i < rows; ++i) s = fmat(xa[i], xb[i], s);
       acc[q] = s;
     }
   }
@@ -496,9 +539,13 @@ __global__ void __launch_bounds__(256) k_gram(Params P) {
   double* out = P.Gp + (int64_t)blockIdx.x * P.kmax * P.kmax;
   for (int q = 0; q < nper; ++q) {
     int e = threadIdx.x + q * blockDim.x;
-    if (e < npairs) out[e] = acc[q];
+    if (e < npairs) out[e] = (double)acc[q];
   }
 }
+
+__global__ void __launch_bounds__(256) k_gram(Params P) { gram_body<double>(P); }
+// mixed-precision form: the candidate Gram matrix in FP32, partials summed in FP64
+__global__ void __launch_bounds__(256) k_gram32(Params P) { gram_body<float>(P); }
 
 __global__ void __launch_bounds__(256) k_gram_reduce(Params P) {
   const DevState* st = P.st;
@@ -945,8 +992,19 @@ struct WGeom {
   int cols;
 };
 
+// Row chunks of k_trail_w32: passes of at least S32_ROWS rows (one staged V
+// block per pass), at most wchunks of them.
+__device__ __forceinline__ int64_t w32_rows_per(const Params& P, int64_t mr);
+
 __device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int64_t mr) {
   WGeom g;
+  if (P.mixed) {
+    g.cols = 0;
+    g.nct = 0;
+    g.rows_per = w32_rows_per(P, mr);
+    g.nrc = (mr + g.rows_per - 1) / g.rows_per;
+    return g;
+  }
   g.cols = GEMM_THREADS / w_tg(l);
   g.nct = (n2 + g.cols - 1) / g.cols;
   g.rows_per = wchunk_rows(mr, g.nct, P.wchunks, P.w_units);
@@ -954,14 +1012,14 @@ __device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int6
   return g;
 }
 
-template <int TG, int NQ>
+template <int TG, int NQ, typename TC>
 __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int l, int64_t ns, int64_t j0,
                                              int64_t mr, const WGeom& g) {
   constexpr int COLS = GEMM_THREADS / TG;
   constexpr int LDA_S = COLS + 1;
   constexpr int LDV_S = KMAX + 1;
-  double* s_a = smem;                   // [TW_SUB][COLS + 1]
-  double* s_v = smem + TW_SUB * LDA_S;  // [TW_SUB][KMAX + 1]
+  TC* s_a = reinterpret_cast<TC*>(smem);  // [TW_SUB][COLS + 1]
+  TC* s_v = s_a + TW_SUB * LDA_S;         // [TW_SUB][KMAX + 1]
   const int64_t lda = P.lda;
   const int tid = threadIdx.x;
   const int c = tid % COLS, tg = tid / COLS;
@@ -971,9 +1029,9 @@ __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int 
     const int64_t cbase = j0 + ct * COLS;
     const int ncols = (int)min((int64_t)COLS, P.n - cbase);
     const int64_t rbeg = rc * g.rows_per, rend = min(mr, rbeg + g.rows_per);
-    double acc[NQ];
+    TC acc[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) acc[q] = (TC)0;
     for (int64_t r0 = rbeg; r0 < rend; r0 += TW_SUB) {
       const int rows = (int)min((int64_t)TW_SUB, rend - r0);
       __syncthreads();
@@ -981,19 +1039,19 @@ __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int 
         const int cc = e / TW_SUB, rr = e % TW_SUB;
         double v = 0.0;
         if (rr < rows && cc < ncols) v = P.A[(cbase + cc) * lda + ns + r0 + rr];
-        s_a[rr * LDA_S + cc] = v;
+        s_a[rr * LDA_S + cc] = (TC)v;
       }
       for (int e = tid; e < TW_SUB * l; e += GEMM_THREADS) {
         const int t = e / TW_SUB, rr = e % TW_SUB;
-        s_v[rr * LDV_S + t] = (rr < rows) ? vget(P.A, lda, ns, r0 + rr, t) : 0.0;
+        s_v[rr * LDV_S + t] = (TC)((rr < rows) ? vget(P.A, lda, ns, r0 + rr, t) : 0.0);
       }
       __syncthreads();
       for (int rr = 0; rr < rows; ++rr) {
-        const double a = s_a[rr * LDA_S + c];
-        const double* vr = s_v + rr * LDV_S + tg;
+        const TC a = s_a[rr * LDA_S + c];
+        const TC* vr = s_v + rr * LDV_S + tg;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-          if (q < NQ - 1 || tg + q * TG < l) acc[q] = fma(vr[q * TG], a, acc[q]);
+          if (q < NQ - 1 || tg + q * TG < l) acc[q] = fmat(vr[q * TG], a, acc[q]);
         }
       }
     }
@@ -1002,7 +1060,7 @@ __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int 
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
         const int t = tg + q * TG;
-        if (t < l) out[(int64_t)t * P.n + cbase + c] = acc[q];
+        if (t < l) out[(int64_t)t * P.n + cbase + c] = (double)acc[q];
       }
     }
   }
@@ -1010,7 +1068,8 @@ __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int 
 
 constexpr int TRAIL_W_SMEM = (TW_SUB * (GEMM_THREADS + 1) + TW_SUB * (KMAX + 1)) * (int)sizeof(double);
 
-__global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P, int j) {
+template <typename TC>
+__device__ __forceinline__ void trail_w_kernel(Params& P, int j) {
   DevState* st = P.st;
   if (st->done) return;
   const SubGeom sg = sub_geom(st, j);
@@ -1025,34 +1084,36 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P, int j) {
   const int tg = w_tg(l);
   const int nq = (l + tg - 1) / tg;
   if (tg == 1) {
-    trail_w_body<1, 1>(P, smw, l, ns, j0, mr, g);
+    trail_w_body<1, 1, TC>(P, smw, l, ns, j0, mr, g);
   } else if (tg == 2) {
-    if (nq == 1) trail_w_body<2, 1>(P, smw, l, ns, j0, mr, g);
-    else trail_w_body<2, 2>(P, smw, l, ns, j0, mr, g);
+    if (nq == 1) trail_w_body<2, 1, TC>(P, smw, l, ns, j0, mr, g);
+    else trail_w_body<2, 2, TC>(P, smw, l, ns, j0, mr, g);
   } else if (tg == 4) {
-    if (nq == 1) trail_w_body<4, 1>(P, smw, l, ns, j0, mr, g);
-    else trail_w_body<4, 2>(P, smw, l, ns, j0, mr, g);
+    if (nq == 1) trail_w_body<4, 1, TC>(P, smw, l, ns, j0, mr, g);
+    else trail_w_body<4, 2, TC>(P, smw, l, ns, j0, mr, g);
   } else {
     switch (nq) {
-      case 1: trail_w_body<8, 1>(P, smw, l, ns, j0, mr, g); break;
-      case 2: trail_w_body<8, 2>(P, smw, l, ns, j0, mr, g); break;
-      case 3: trail_w_body<8, 3>(P, smw, l, ns, j0, mr, g); break;
-      case 4: trail_w_body<8, 4>(P, smw, l, ns, j0, mr, g); break;
-      case 5: trail_w_body<8, 5>(P, smw, l, ns, j0, mr, g); break;
-      case 6: trail_w_body<8, 6>(P, smw, l, ns, j0, mr, g); break;
-      case 7: trail_w_body<8, 7>(P, smw, l, ns, j0, mr, g); break;
-      case 8: trail_w_body<8, 8>(P, smw, l, ns, j0, mr, g); break;
-      case 9: trail_w_body<8, 9>(P, smw, l, ns, j0, mr, g); break;
-      case 10: trail_w_body<8, 10>(P, smw, l, ns, j0, mr, g); break;
-      case 11: trail_w_body<8, 11>(P, smw, l, ns, j0, mr, g); break;
-      case 12: trail_w_body<8, 12>(P, smw, l, ns, j0, mr, g); break;
-      case 13: trail_w_body<8, 13>(P, smw, l, ns, j0, mr, g); break;
-      case 14: trail_w_body<8, 14>(P, smw, l, ns, j0, mr, g); break;
-      case 15: trail_w_body<8, 15>(P, smw, l, ns, j0, mr, g); break;
-      default: trail_w_body<8, 16>(P, smw, l, ns, j0, mr, g); break;
+      case 1: trail_w_body<8, 1, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 2: trail_w_body<8, 2, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 3: trail_w_body<8, 3, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 4: trail_w_body<8, 4, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 5: trail_w_body<8, 5, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 6: trail_w_body<8, 6, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 7: trail_w_body<8, 7, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 8: trail_w_body<8, 8, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 9: trail_w_body<8, 9, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 10: trail_w_body<8, 10, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 11: trail_w_body<8, 11, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 12: trail_w_body<8, 12, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 13: trail_w_body<8, 13, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 14: trail_w_body<8, 14, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 15: trail_w_body<8, 15, TC>(P, smw, l, ns, j0, mr, g); break;
+      default: trail_w_body<8, 16, TC>(P, smw, l, ns, j0, mr, g); break;
     }
   }
 }
+
+__global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P, int j) { trail_w_kernel<double>(P, j); }
 
 __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j) {
   DevState* st = P.st;
@@ -1090,7 +1151,8 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j)
   }
 }
 
-__global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P, int j) {
+template <typename TC>
+__device__ __forceinline__ void trail_update_kernel(Params& P, int j) {
   DevState* st = P.st;
   if (st->done) return;
   const SubGeom sg = sub_geom(st, j);
@@ -1103,19 +1165,19 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P, int j) 
   const int64_t nrt = (mr + TU_ROWS - 1) / TU_ROWS;
   const int64_t nct = (n2 + TU_COLS - 1) / TU_COLS;
   const int64_t units = nrt * nct;
-  __shared__ double s_v[TU_KC][TU_ROWS];
-  __shared__ double s_w[TU_KC][TU_COLS];
+  __shared__ TC s_v[TU_KC][TU_ROWS];
+  __shared__ TC s_w[TU_KC][TU_COLS];
   const int tid = threadIdx.x;
   const int tr = tid % 16, tc = tid / 16;  // 16 x 16 threads, 4 x 4 outputs each
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t rt = u % nrt, ct = u / nrt;
     const int64_t rbase = rt * TU_ROWS;  // relative to ns
     const int64_t cbase = j0 + ct * TU_COLS;
-    double acc[4][4];
+    TC acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < 4; ++j) acc[i][j] = (TC)0;
     for (int t0 = 0; t0 < l; t0 += TU_KC) {
       const int kcnt = min(TU_KC, l - t0);
       __syncthreads();
@@ -1123,17 +1185,17 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P, int j) 
         int t = e / TU_ROWS, r = e % TU_ROWS;
         double v = 0.0;
         if (t < kcnt && rbase + r < mr) v = vget(P.A, lda, ns, rbase + r, t0 + t);
-        s_v[t][r] = v;
+        s_v[t][r] = (TC)v;
       }
       for (int e = tid; e < TU_KC * TU_COLS; e += GEMM_THREADS) {
         int t = e / TU_COLS, c = e % TU_COLS;
         double v = 0.0;
         if (t < kcnt && cbase + c < P.n) v = P.W[(int64_t)(t0 + t) * P.n + cbase + c];
-        s_w[t][c] = v;
+        s_w[t][c] = (TC)v;
       }
       __syncthreads();
       for (int t = 0; t < kcnt; ++t) {
-        double vv[4], ww[4];
+        TC vv[4], ww[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) vv[i] = s_v[t][tr + 16 * i];
 #pragma unroll
@@ -1141,7 +1203,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P, int j) 
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(vv[i], ww[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmat(vv[i], ww[j], acc[i][j]);
       }
     }
 #pragma unroll
@@ -1152,7 +1214,207 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P, int j) 
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int64_t r = rbase + tr + 16 * i;
-        if (r < mr) a[r] -= acc[i][j];
+        if (r < mr) a[r] -= (double)acc[i][j];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P, int j) { trail_update_kernel<double>(P, j); }
+
+// ---------------------------------------------------------------------------
+// a9, FP32-class form.  With l <= PB = 16 reflectors per pass the update moves
+// 8 (W) + 16 (update) bytes of FP64 per element for 4 l flops: HBM-bound on
+// FP32 CUDA cores, so the kernels are built for streaming, not for tensor
+// cores: one warp per column, lanes stride the rows (coalesced 8-byte loads,
+// several in flight per lane), V staged in shared memory as FP32 rows of PB,
+// products and sums in FP32, the result written back in FP64.
+// ---------------------------------------------------------------------------
+constexpr int S32_ROWS = 1024;  // rows of V staged per pass
+
+__device__ __forceinline__ int64_t w32_rows_per(const Params& P, int64_t mr) {
+  int64_t r = (mr + P.wchunks - 1) / P.wchunks;
+  r = (r + 31) / 32 * 32;
+  return r < S32_ROWS ? S32_ROWS : r;
+}
+constexpr int S32_COLS = 64;    // columns per work unit (8 warps x 8 columns)
+constexpr int S32_SMEM = S32_ROWS * PB * (int)sizeof(float);
+
+// V rows [rs, rs + rows) of the sub-panel as FP32, row-major with PB columns
+__device__ __forceinline__ void stage_v32(const Params& P, float* s_v, int64_t base, int64_t rs, int rows, int l) {
+  for (int e = threadIdx.x; e < rows * PB; e += GEMM_THREADS) {
+    const int rr = e % rows, t = e / rows;  // consecutive threads: consecutive rows of one column
+    float v = 0.f;
+    if (t < l) v = f64_to_f32_rn(vget(P.A, P.lda, base, rs + rr, t));
+    s_v[rr * PB + t] = v;
+  }
+}
+
+constexpr int W32_CPW = 4;                     // columns per warp in k_trail_w32
+constexpr int W32_COLS = 8 * W32_CPW;          // columns per work unit
+
+__global__ void __launch_bounds__(GEMM_THREADS, 2) k_trail_w32(Params P, int j) {
+  DevState* st = P.st;
+  if (st->done) return;
+  const SubGeom sg = sub_geom(st, j);
+  const int l = sg.l;
+  const int64_t base = sg.r0, j0 = sg.c0;
+  const int64_t n2 = P.n - j0, mr = P.m - base;
+  if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_W, 2.0 * (double)mr * (double)n2 * l);
+  extern __shared__ float s32[];
+  float* s_v = s32;  // [S32_ROWS][PB]
+  const WGeom g = w_geom(P, l, n2, mr);  // row chunks shared with k_trail_wreduce
+  const int64_t ncb = (n2 + W32_COLS - 1) / W32_COLS;
+  const int64_t units = g.nrc * ncb;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  // contiguous unit ranges per CTA: consecutive units share a row chunk
+  const int64_t ub = units * blockIdx.x / gridDim.x, ue = units * (blockIdx.x + 1) / gridDim.x;
+  int64_t staged_rs = -1;  // first row of the V block now in shared memory
+  for (int64_t u = ub; u < ue; ++u) {
+    const int64_t rc = u / ncb, cb = u % ncb;
+    const int64_t rbeg = rc * g.rows_per, rend = min(mr, rbeg + g.rows_per);
+    const int64_t col0 = j0 + cb * W32_COLS + wp * W32_CPW;
+    int ncol = (int)min((int64_t)W32_CPW, P.n - col0);
+    if (ncol < 0) ncol = 0;
+    const double* a[W32_CPW];
+#pragma unroll
+    for (int c = 0; c < W32_CPW; ++c) a[c] = P.A + (col0 + (c < ncol ? c : 0)) * P.lda + base;
+    float acc[W32_CPW][PB];
+#pragma unroll
+    for (int c = 0; c < W32_CPW; ++c)
+#pragma unroll
+      for (int t = 0; t < PB; ++t) acc[c][t] = 0.f;
+    for (int64_t rs = rbeg; rs < rend; rs += S32_ROWS) {
+      const int rows = (int)min((int64_t)S32_ROWS, rend - rs);
+      if (rs != staged_rs) {  // uniform across the CTA; consecutive units share a pass
+        __syncthreads();
+        stage_v32(P, s_v, base, rs, rows, l);
+        __syncthreads();
+        staged_rs = rs;
+      }
+      if (ncol > 0) {
+        // rows outer, two rows per lane per pass: W32_CPW x 2 loads in flight
+        for (int r = lane; r < rows; r += 64) {
+          const bool two = (r + 32 < rows);
+          double x0[W32_CPW], x1[W32_CPW];
+#pragma unroll
+          for (int c = 0; c < W32_CPW; ++c) {
+            x0[c] = a[c][rs + r];
+            x1[c] = two ? a[c][rs + r + 32] : 0.0;
+          }
+          float y0[W32_CPW], y1[W32_CPW];
+#pragma unroll
+          for (int c = 0; c < W32_CPW; ++c) {
+            y0[c] = f64_to_f32_rn(x0[c]);
+            y1[c] = f64_to_f32_rn(x1[c]);
+          }
+          const float4* v0 = reinterpret_cast<const float4*>(s_v + r * PB);
+          const float4* v1 = reinterpret_cast<const float4*>(s_v + (two ? r + 32 : r) * PB);
+#pragma unroll
+          for (int q = 0; q < PB / 4; ++q) {
+            const float4 p0 = v0[q];
+            const float4 p1 = two ? v1[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < W32_CPW; ++c) {
+              acc[c][4 * q + 0] = fmaf(p1.x, y1[c], fmaf(p0.x, y0[c], acc[c][4 * q + 0]));
+              acc[c][4 * q + 1] = fmaf(p1.y, y1[c], fmaf(p0.y, y0[c], acc[c][4 * q + 1]));
+              acc[c][4 * q + 2] = fmaf(p1.z, y1[c], fmaf(p0.z, y0[c], acc[c][4 * q + 2]));
+              acc[c][4 * q + 3] = fmaf(p1.w, y1[c], fmaf(p0.w, y0[c], acc[c][4 * q + 3]));
+            }
+          }
+        }
+      }
+    }
+    // reduce over lanes and store this row chunk's partial W (FP64)
+    double* out = P.Wp + rc * (int64_t)P.kmax * P.n;
+#pragma unroll
+    for (int c = 0; c < W32_CPW; ++c) {
+#pragma unroll
+      for (int t = 0; t < PB; ++t) {
+        float v = acc[c][t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && t < l && c < ncol) out[(int64_t)t * P.n + col0 + c] = (double)v;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS, 2) k_trail_update32(Params P, int j) {
+  DevState* st = P.st;
+  if (st->done) return;
+  const SubGeom sg = sub_geom(st, j);
+  const int l = sg.l;
+  const int64_t base = sg.r0, j0 = sg.c0;
+  const int64_t n2 = P.n - j0, mr = P.m - base;
+  if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_UPDATE, 2.0 * (double)mr * (double)n2 * l);
+  extern __shared__ float s32[];
+  float* s_v = s32;  // [S32_ROWS][PB]
+  const int64_t nrb = (mr + S32_ROWS - 1) / S32_ROWS;
+  const int64_t ncb = (n2 + W32_COLS - 1) / W32_COLS;
+  const int64_t units = nrb * ncb;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int64_t ub = units * blockIdx.x / gridDim.x, ue = units * (blockIdx.x + 1) / gridDim.x;
+  int64_t staged_rb = -1;
+  for (int64_t u = ub; u < ue; ++u) {
+    const int64_t rb = u / ncb, cb = u % ncb;
+    const int64_t rs = rb * S32_ROWS;
+    const int rows = (int)min((int64_t)S32_ROWS, mr - rs);
+    if (rb != staged_rb) {  // uniform across the CTA
+      __syncthreads();
+      stage_v32(P, s_v, base, rs, rows, l);
+      __syncthreads();
+      staged_rb = rb;
+    }
+    const int64_t col0 = j0 + cb * W32_COLS + wp * W32_CPW;
+    int ncol = (int)min((int64_t)W32_CPW, P.n - col0);
+    if (ncol <= 0) continue;
+    // this warp's W columns (FP32, in registers)
+    float wv[W32_CPW][PB];
+#pragma unroll
+    for (int c = 0; c < W32_CPW; ++c)
+#pragma unroll
+      for (int t = 0; t < PB; ++t)
+        wv[c][t] = (t < l && c < ncol) ? f64_to_f32_rn(P.W[(int64_t)t * P.n + col0 + c]) : 0.f;
+    double* a[W32_CPW];
+#pragma unroll
+    for (int c = 0; c < W32_CPW; ++c) a[c] = P.A + (col0 + (c < ncol ? c : 0)) * P.lda + base + rs;
+    for (int r = lane; r < rows; r += 64) {  // two rows per lane: 8 loads in flight
+      const bool two = (r + 32 < rows);
+      double x0[W32_CPW], x1[W32_CPW];
+#pragma unroll
+      for (int c = 0; c < W32_CPW; ++c) {
+        x0[c] = (c < ncol) ? a[c][r] : 0.0;
+        x1[c] = (two && c < ncol) ? a[c][r + 32] : 0.0;
+      }
+      float d0[W32_CPW], d1[W32_CPW];
+#pragma unroll
+      for (int c = 0; c < W32_CPW; ++c) d0[c] = d1[c] = 0.f;
+      const float4* v0 = reinterpret_cast<const float4*>(s_v + r * PB);
+      const float4* v1 = reinterpret_cast<const float4*>(s_v + (two ? r + 32 : r) * PB);
+#pragma unroll
+      for (int q = 0; q < PB / 4; ++q) {
+        const float4 p0 = v0[q], p1 = v1[q];
+#pragma unroll
+        for (int c = 0; c < W32_CPW; ++c) {
+          d0[c] = fmaf(p0.x, wv[c][4 * q + 0], d0[c]);
+          d0[c] = fmaf(p0.y, wv[c][4 * q + 1], d0[c]);
+          d0[c] = fmaf(p0.z, wv[c][4 * q + 2], d0[c]);
+          d0[c] = fmaf(p0.w, wv[c][4 * q + 3], d0[c]);
+          d1[c] = fmaf(p1.x, wv[c][4 * q + 0], d1[c]);
+          d1[c] = fmaf(p1.y, wv[c][4 * q + 1], d1[c]);
+          d1[c] = fmaf(p1.z, wv[c][4 * q + 2], d1[c]);
+          d1[c] = fmaf(p1.w, wv[c][4 * q + 3], d1[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < W32_CPW; ++c) {
+        if (c < ncol) {
+          a[c][r] = x0[c] - f32_to_f64(d0[c]);
+          if (two) a[c][r + 32] = x1[c] - f32_to_f64(d1[c]);
+        }
       }
     }
   }

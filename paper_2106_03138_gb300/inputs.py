@@ -61,6 +61,33 @@ def from_spectrum(m: int, n: int, sigma: np.ndarray, seed: int) -> np.ndarray:
     return np.asfortranarray((u * sigma[None, :]) @ v.T)
 
 
+def from_spectrum_gpu(m: int, n: int, sigma: np.ndarray, seed: int, device="cuda"):
+    """A = U diag(sigma) V^T built on the GPU (for sizes where the host QR is
+    too slow, e.g. 16384 x 16384): N(0,1) draws from a seeded torch CUDA
+    generator, Haar factors from the library QR with sign(diag R) fixed.
+    Returns a column-major float64 CUDA tensor.  Seeded and deterministic on
+    a given GPU; not bit-identical to from_spectrum's numpy draws."""
+    import torch
+
+    sig = torch.as_tensor(np.asarray(sigma, dtype=np.float64), device=device)
+    p = sig.shape[0]
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+
+    def haar_t(rows):
+        x = torch.randn((rows, p), generator=g, dtype=torch.float64, device=device)
+        q, r = torch.linalg.qr(x, mode="reduced")
+        d = torch.sign(torch.diagonal(r))
+        d[d == 0] = 1.0
+        return q * d[None, :]
+
+    u = haar_t(m)
+    v = haar_t(n)
+    a = (u * sig[None, :]) @ v.T
+    del u, v
+    return a.t().contiguous().t()
+
+
 def sigma_gap(p: int, r: int, hi: float = 1.0, lo: float = 1e-14) -> np.ndarray:
     """sigma_i = hi for i <= r, lo after (a numerically rank-r matrix)."""
     s = np.full(p, lo, dtype=np.float64)
@@ -156,6 +183,8 @@ _NAMED = {
     "kahan2048": MatrixSpec("kahan2048", 2048, 2048, "kahan"),
     # rank-8192 gap spectrum: geometric 1 -> 1e-3 then 1e-14.
     "gapgeo16384": MatrixSpec("gapgeo16384", 16384, 16384, "gap_geometric", seed=0, rank=8192),
+    # the same recipe at 4096 (rank 2048), a host-generated profiling case
+    "gapgeo4096": MatrixSpec("gapgeo4096", 4096, 4096, "gap_geometric", seed=0, rank=2048),
 }
 
 

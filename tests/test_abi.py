@@ -82,5 +82,9 @@ def test_workspace_size_and_argument_checks(lib):
     o.eps1_mode = 7
     rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 4, fake, fake, o, fake, 1 << 30, 0)
     assert rc == -11
+    o = b.qrdm_opts()
+    o.precision = 2
+    rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 4, fake, fake, o, fake, 1 << 30, 0)
+    assert rc == -11
     assert b.qrdm_strerror(2).startswith("the matrix")
     assert lib.qrdm_version() >= 100
