@@ -222,6 +222,42 @@ def run_profile_case(name: str, max_steps: int, precision: int = 0) -> int:
     return 0
 
 
+def measure_c3(q, inputs, torch, stream) -> dict:
+    """The mixed-precision workload: 16384 x 16384 with sigma geometric
+    1 -> 1e-3 over 8192 values then 1e-14 (numerical rank 8192), generated on
+    the GPU; FP64 and FP32-class forms, both stopping at the rank (the
+    rank-revealing use), each timed once after one untimed run."""
+    n = 16384
+    r = n // 2
+    sig = inputs.sigma_gap_geometric(n, r)
+    A0 = inputs.from_spectrum_gpu(n, n, sig, 0)
+    ws = torch.empty(q.qrdm_workspace_size(n, n, KMAX), dtype=torch.uint8, device=A0.device)
+    out = {"workload": "16384x16384, sigma geometric 1->1e-3 over 8192 values then 1e-14; stop at the rank",
+           "tau": TAU, "delta": DELTA, "k_max": KMAX}
+    flops = metric_flops(n, n)
+    for prec, key in ((0, "fp64"), (1, "mixed_fp32")):
+        for rep in range(2):
+            dA = A0.clone()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f = q.factor(dA, TAU, DELTA, KMAX, workspace=ws, stream=stream, precision=prec, stop_at_rank=True)
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        # rank quality as in the paper (Sec. 5): d_i / sigma_i, d_i the sorted |R_ii|, i < r
+        d = torch.sort(torch.diagonal(dA)[:r].abs(), descending=True).values.cpu().numpy()
+        ratio = d / sig[:r]
+        out[key] = {"ms": ms, "GFLOP/s": flops / ms / 1e6, "rank": f.rank, "rank_colmax": f.rank_colmax,
+                    "steps": f.nsteps, "d_over_sigma_min": float(ratio.min()), "d_over_sigma_max": float(ratio.max())}
+        del dA
+    out["speedup"] = out["fp64"]["ms"] / out["mixed_fp32"]["ms"]
+    del A0, ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def config_dict(world: int) -> dict:
     return {"workload": WORKLOAD_DESC, "matrices": list(WORKLOAD), "tau": TAU, "delta": DELTA, "k_max": KMAX,
             "global_batch": 3 * world, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -236,6 +272,7 @@ def main() -> int:
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 16384^2 mixed-precision measurement")
     ap.add_argument("--profile-case", default=None,
                     help="factor one named matrix once at the benchmark's parameters and exit (profiler target)")
     ap.add_argument("--max-steps", type=int, default=0, help="with --profile-case: stop after this many block steps")
@@ -391,6 +428,10 @@ def main() -> int:
                                   "steps": f.nsteps, "rank": f.rank}
             del wk
 
+    c3 = None
+    if rank == 0 and not args.no_c3:
+        c3 = measure_c3(q, inputs, torch, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         secs, fl = time_oracle_sample(cpu_sample_matrices())
@@ -407,7 +448,7 @@ def main() -> int:
             "config": config_dict(world), "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": csum, "gpu_launches": launches, "wall_s": t_wall, "per_matrix": per,
-            "comparators": comparators,
+            "comparators": comparators, "mixed_precision_c3": c3,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
