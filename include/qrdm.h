@@ -198,6 +198,92 @@ int qrdm_factor_noalloc(double* dA, int64_t m, int64_t n, int64_t lda, double ta
                         double* d_htau, int32_t* d_perm, qrdm_info* info, const qrdm_opts* opts, void* stream,
                         qrdm_step_record* d_trace, int32_t* d_trace_J, int64_t trace_cap);
 
+/*
+ * Batched QRDM: many independent matrices factored by one persistent kernel.
+ * Each CTA factors whole matrices taken from a work queue, largest first
+ * (geqrf flop count), so no CTA ever waits on another.  Every matrix gets the
+ * QRDM2 of qrdm_factor (Algorithm 4 with the DM selection of Algorithm 1 and
+ * Sec. 4, the Sec. 3.4 stopping criterion), in FP64, with the same readings;
+ * only the summation order inside a CTA differs.  The paper factors one
+ * matrix at a time; the batched form, its plan object, the CUDA-graph launch
+ * and the autotuner have no counterpart in it.
+ *
+ * Use:
+ *   qrdm_batch_plan_create     validates the matrix list (host array, copied),
+ *                              orders it, picks a default tuning;
+ *   qrdm_batch_workspace_size  device bytes the plan needs;
+ *   qrdm_batch_bind            attaches a workspace and uploads the matrix
+ *                              descriptors (synchronizes `stream`);
+ *   qrdm_batch_autotune        optional: times every feasible tuning on the
+ *                              plan's own matrices, restores them, keeps the
+ *                              fastest (allocates a device backup of all
+ *                              matrices for its duration);
+ *   qrdm_factor_batched        enqueues the factorization on `stream` (a
+ *                              counter reset and one kernel launch; no host
+ *                              synchronization, so it may be captured);
+ *   qrdm_factor_batched_graph  the same through a CUDA graph that the plan
+ *                              captures on first use and replays afterwards
+ *                              (recaptured when tau, delta, opts, the tuning
+ *                              or the workspace change);
+ *   qrdm_batch_results         rank, rank_colmax, status (0 ok, 1 non-finite
+ *                              input: that matrix is left unmodified and its
+ *                              ranks are -1) and block steps per matrix, in
+ *                              the caller's order, copied to host arrays
+ *                              (NULL: skipped; synchronizes `stream`);
+ *   qrdm_batch_plan_destroy.
+ * Each matrix is factored in place like qrdm_factor: R and the reflectors in
+ * dA, htau in d_htau (min(m, n)), the 0-based int32 permutation in d_perm
+ * (n).  Matrices must not overlap.  An optional per-matrix step trace
+ * (d_trace, d_trace_J, trace_cap) is written as in qrdm_factor.  opts may be
+ * NULL; eps1_mode, stop_at_rank, check_last, no_break and sdd are honoured,
+ * max_steps is ignored, precision must be 0 (QRDM_ERR_UNSUPPORTED
+ * otherwise).  A profile (qrdm_factor_batched only; it then times the launch
+ * with events and synchronizes `stream`) receives, added to its contents:
+ * ms[0..7] the kernel time split by the CTAs' clock shares of the phases
+ * norms, argmax and candidates, Gram, DM pick, swaps, panel, block
+ * reflector, norm downdate; ms[8] the kernel time; flops[0] the load balance
+ * (mean over CTAs of their active time divided by the largest); launches[0]
+ * one per call.  One plan serves one device and one host
+ * thread at a time.
+ * Errors: -i for an invalid i-th argument (-2 from qrdm_batch_plan_create
+ * for any invalid matrix entry), QRDM_ERR_WORKSPACE for a missing, small or
+ * misaligned workspace, QRDM_ERR_UNSUPPORTED for a tuning whose CTAs do not
+ * fit on an SM, QRDM_ERR_CUDA.
+ */
+#define QRDM_BATCH_MAX_CTAS_PER_SM 2
+
+typedef struct qrdm_batch_plan qrdm_batch_plan; /* opaque host object */
+
+typedef struct qrdm_batch_matrix {
+  double* dA;      /* device, m x n column-major, leading dimension lda >= max(1, m) */
+  int64_t m, n, lda;
+  double* d_htau;  /* device, min(m, n) doubles */
+  int32_t* d_perm; /* device, n int32 */
+  qrdm_step_record* d_trace; /* optional device trace, trace_cap records (NULL/0: none) */
+  int32_t* d_trace_J;        /* optional, trace_cap * k_max int32 */
+  int64_t trace_cap;
+} qrdm_batch_matrix;
+
+typedef struct qrdm_batch_tuning {
+  int32_t ctas_per_sm;   /* resident CTAs per SM, 1..QRDM_BATCH_MAX_CTAS_PER_SM */
+  int32_t rows_per_pass; /* rows of V staged in shared memory per pass, 64..1024, multiple of 64 */
+  int32_t lanes_per_col; /* lanes sharing one column in the block reflector phases: 4 or 8 */
+  int32_t reserved;
+} qrdm_batch_tuning;
+
+int qrdm_batch_plan_create(int64_t count, const qrdm_batch_matrix* h_mats, int32_t k_max, qrdm_batch_plan** plan);
+void qrdm_batch_plan_destroy(qrdm_batch_plan* plan);
+int qrdm_batch_workspace_size(const qrdm_batch_plan* plan, size_t* bytes);
+int qrdm_batch_bind(qrdm_batch_plan* plan, void* d_work, size_t work_bytes, void* stream);
+int qrdm_batch_get_tuning(const qrdm_batch_plan* plan, qrdm_batch_tuning* tuning);
+int qrdm_batch_set_tuning(qrdm_batch_plan* plan, const qrdm_batch_tuning* tuning);
+int qrdm_batch_autotune(qrdm_batch_plan* plan, double tau, double delta, const qrdm_opts* opts, void* stream,
+                        qrdm_batch_tuning* best, double* best_ms);
+int qrdm_factor_batched(qrdm_batch_plan* plan, double tau, double delta, const qrdm_opts* opts, void* stream);
+int qrdm_factor_batched_graph(qrdm_batch_plan* plan, double tau, double delta, const qrdm_opts* opts, void* stream);
+int qrdm_batch_results(const qrdm_batch_plan* plan, int64_t* h_rank, int64_t* h_rank_colmax, int32_t* h_status,
+                       int64_t* h_steps, void* stream);
+
 /* Static description of an error code. */
 const char* qrdm_strerror(int code);
 

@@ -32,6 +32,7 @@ from ._binding import (  # noqa: F401
     qrdm_strerror,
     qrdm_workspace_size,
 )
+from .batched import BatchPlan, BatchResult  # noqa: F401,E402
 
 TRACE_DTYPE = np.dtype([("ns", np.int64), ("jstar", np.int64), ("ncand_all", np.int64), ("ncand", np.int64),
                         ("k", np.int64), ("l", np.int64), ("dm_on", np.int64), ("nrecomp", np.int64),

@@ -47,9 +47,26 @@ class qrdm_step_record(ctypes.Structure):
                 ("dm_on", c_i64), ("nrecomp", c_i64), ("mu", c_f64), ("eps_s", c_f64)]
 
 
+class qrdm_batch_matrix(ctypes.Structure):
+    _fields_ = [("dA", c_p), ("m", c_i64), ("n", c_i64), ("lda", c_i64), ("d_htau", c_p), ("d_perm", c_p),
+                ("d_trace", c_p), ("d_trace_J", c_p), ("trace_cap", c_i64)]
+
+
+class qrdm_batch_tuning(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", c_i32), ("rows_per_pass", c_i32), ("lanes_per_col", c_i32), ("reserved", c_i32)]
+
+    def as_dict(self) -> dict:
+        return {"ctas_per_sm": int(self.ctas_per_sm), "rows_per_pass": int(self.rows_per_pass),
+                "lanes_per_col": int(self.lanes_per_col)}
+
+
+QRDM_BATCH_MAX_CTAS_PER_SM = 2
+
 # every symbol declared in include/qrdm.h
 EXPORTS = ("qrdm_workspace_size", "qrdm_factor", "qrdm_factor_noalloc", "qrdm_strerror", "qrdm_last_cuda_error",
-           "qrdm_version")
+           "qrdm_version", "qrdm_batch_plan_create", "qrdm_batch_plan_destroy", "qrdm_batch_workspace_size",
+           "qrdm_batch_bind", "qrdm_batch_get_tuning", "qrdm_batch_set_tuning", "qrdm_batch_autotune",
+           "qrdm_factor_batched", "qrdm_factor_batched_graph", "qrdm_batch_results")
 QRDM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 _lock = threading.Lock()
@@ -86,6 +103,28 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.qrdm_last_cuda_error.argtypes = []
         lib.qrdm_version.restype = ctypes.c_int
         lib.qrdm_version.argtypes = []
+        P = ctypes.POINTER
+        lib.qrdm_batch_plan_create.restype = ctypes.c_int
+        lib.qrdm_batch_plan_create.argtypes = [c_i64, P(qrdm_batch_matrix), c_i32, P(c_p)]
+        lib.qrdm_batch_plan_destroy.restype = None
+        lib.qrdm_batch_plan_destroy.argtypes = [c_p]
+        lib.qrdm_batch_workspace_size.restype = ctypes.c_int
+        lib.qrdm_batch_workspace_size.argtypes = [c_p, P(c_sz)]
+        lib.qrdm_batch_bind.restype = ctypes.c_int
+        lib.qrdm_batch_bind.argtypes = [c_p, c_p, c_sz, c_p]
+        lib.qrdm_batch_get_tuning.restype = ctypes.c_int
+        lib.qrdm_batch_get_tuning.argtypes = [c_p, P(qrdm_batch_tuning)]
+        lib.qrdm_batch_set_tuning.restype = ctypes.c_int
+        lib.qrdm_batch_set_tuning.argtypes = [c_p, P(qrdm_batch_tuning)]
+        lib.qrdm_batch_autotune.restype = ctypes.c_int
+        lib.qrdm_batch_autotune.argtypes = [c_p, c_f64, c_f64, P(qrdm_opts), c_p, P(qrdm_batch_tuning),
+                                            P(c_f64)]
+        lib.qrdm_factor_batched.restype = ctypes.c_int
+        lib.qrdm_factor_batched.argtypes = [c_p, c_f64, c_f64, P(qrdm_opts), c_p]
+        lib.qrdm_factor_batched_graph.restype = ctypes.c_int
+        lib.qrdm_factor_batched_graph.argtypes = [c_p, c_f64, c_f64, P(qrdm_opts), c_p]
+        lib.qrdm_batch_results.restype = ctypes.c_int
+        lib.qrdm_batch_results.argtypes = [c_p, c_p, c_p, c_p, c_p, c_p]
         _lib = lib
         return lib
 
@@ -122,3 +161,60 @@ def qrdm_factor_noalloc(dA: int, m: int, n: int, lda: int, tau: float, delta: fl
                                     ctypes.byref(opts) if opts is not None else None, stream, d_trace or None,
                                     d_trace_J or None, trace_cap)
     return rc, info
+
+
+def _opts_ref(opts):
+    return ctypes.byref(opts) if opts is not None else None
+
+
+def qrdm_batch_plan_create(mats, k_max: int) -> tuple[int, int]:
+    """mats: sequence of qrdm_batch_matrix.  Returns (rc, plan handle or 0)."""
+    arr = (qrdm_batch_matrix * max(len(mats), 1))(*mats)
+    h = c_p(0)
+    rc = load().qrdm_batch_plan_create(len(mats), arr, k_max, ctypes.byref(h))
+    return rc, int(h.value or 0)
+
+
+def qrdm_batch_plan_destroy(plan: int) -> None:
+    load().qrdm_batch_plan_destroy(plan or None)
+
+
+def qrdm_batch_workspace_size(plan: int) -> tuple[int, int]:
+    out = c_sz(0)
+    rc = load().qrdm_batch_workspace_size(plan or None, ctypes.byref(out))
+    return rc, int(out.value)
+
+
+def qrdm_batch_bind(plan: int, d_work: int, work_bytes: int, stream: int) -> int:
+    return load().qrdm_batch_bind(plan or None, d_work or None, work_bytes, stream or None)
+
+
+def qrdm_batch_get_tuning(plan: int) -> tuple[int, qrdm_batch_tuning]:
+    t = qrdm_batch_tuning()
+    rc = load().qrdm_batch_get_tuning(plan or None, ctypes.byref(t))
+    return rc, t
+
+
+def qrdm_batch_set_tuning(plan: int, tuning: qrdm_batch_tuning) -> int:
+    return load().qrdm_batch_set_tuning(plan or None, ctypes.byref(tuning))
+
+
+def qrdm_batch_autotune(plan: int, tau: float, delta: float, opts, stream: int) -> tuple[int, qrdm_batch_tuning, float]:
+    t = qrdm_batch_tuning()
+    ms = c_f64(0.0)
+    rc = load().qrdm_batch_autotune(plan or None, tau, delta, _opts_ref(opts), stream or None, ctypes.byref(t),
+                                    ctypes.byref(ms))
+    return rc, t, float(ms.value)
+
+
+def qrdm_factor_batched(plan: int, tau: float, delta: float, opts, stream: int) -> int:
+    return load().qrdm_factor_batched(plan or None, tau, delta, _opts_ref(opts), stream or None)
+
+
+def qrdm_factor_batched_graph(plan: int, tau: float, delta: float, opts, stream: int) -> int:
+    return load().qrdm_factor_batched_graph(plan or None, tau, delta, _opts_ref(opts), stream or None)
+
+
+def qrdm_batch_results(plan: int, h_rank: int, h_rank_colmax: int, h_status: int, h_steps: int, stream: int) -> int:
+    return load().qrdm_batch_results(plan or None, h_rank or None, h_rank_colmax or None, h_status or None,
+                                     h_steps or None, stream or None)

@@ -7,9 +7,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "../../include/qrdm.h"
+#include "qrdm_batched.cuh"
 #include "qrdm_kernels.cuh"
 
 using namespace qrdm;
@@ -505,6 +508,485 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   info->rank_colmax = hs.rank_colmax >= 0 ? hs.rank_colmax : (hs.ns >= kmin ? kmin : hs.ns);
   info->nsteps = hs.step;
   return QRDM_OK;
+}
+
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched form: one persistent launch over many matrices (k_batched)
+// ---------------------------------------------------------------------------
+struct qrdm_batch_plan {
+  int64_t count = 0, nmax = 1;
+  int kmax = 1;
+  int device = 0, sms = 0;
+  std::vector<BatchDesc> desc;
+  std::vector<int32_t> order;
+  qrdm_batch_tuning tuning{};
+  // workspace
+  size_t off_next = 0, off_prof = 0, off_desc = 0, off_order = 0, off_rank = 0, off_rank_cm = 0, off_status = 0,
+         off_steps = 0, off_scratch = 0, total = 0;
+  char* work = nullptr;
+  size_t work_bytes = 0;
+  // graph of the last qrdm_factor_batched_graph parameters
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  double g_tau = -1.0, g_delta = -1.0;
+  qrdm_opts g_opts{};
+  qrdm_batch_tuning g_tuning{};
+};
+
+namespace {
+
+int g_batch_static_smem[2] = {-1, -1};  // static shared memory of k_batched<4>, k_batched<8>
+int g_batch_optin = 0;
+
+int lpc_index(int lpc) { return lpc == 4 ? 0 : 1; }
+
+cudaError_t batch_configure() {
+  if (g_batch_static_smem[0] >= 0) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_batch_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa4, fa8;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa4, k_batched<4>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa8, k_batched<8>);
+  if (e != cudaSuccess) return e;
+  const int mx4 = g_batch_optin - (int)fa4.sharedSizeBytes, mx8 = g_batch_optin - (int)fa8.sharedSizeBytes;
+  e = cudaFuncSetAttribute(k_batched<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx4);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batched<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx8);
+  if (e != cudaSuccess) return e;
+  g_batch_static_smem[0] = (int)fa4.sharedSizeBytes;
+  g_batch_static_smem[1] = (int)fa8.sharedSizeBytes;
+  return cudaSuccess;
+}
+
+// 0: feasible; QRDM_ERR_UNSUPPORTED: the CTAs do not fit on an SM; -1: bad values
+int tuning_check(const qrdm_batch_plan* P, const qrdm_batch_tuning& t) {
+  if (t.ctas_per_sm < 1 || t.ctas_per_sm > QRDM_BATCH_MAX_CTAS_PER_SM) return -1;
+  if (t.rows_per_pass < 64 || t.rows_per_pass > 1024 || t.rows_per_pass % 64) return -1;
+  if (t.lanes_per_col != 4 && t.lanes_per_col != 8) return -1;
+  const int64_t smem = batched_smem_bytes(P->kmax, t.rows_per_pass);
+  const int li = lpc_index(t.lanes_per_col);
+  if (smem + g_batch_static_smem[li] > g_batch_optin) return QRDM_ERR_UNSUPPORTED;
+  int nb = 0;
+  cudaError_t e = (t.lanes_per_col == 4)
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched<4>, BT, (size_t)smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched<8>, BT, (size_t)smem);
+  if (e != cudaSuccess) {
+    g_last_cuda = (int)e;
+    return QRDM_ERR_CUDA;
+  }
+  return nb >= t.ctas_per_sm ? 0 : QRDM_ERR_UNSUPPORTED;
+}
+
+// geqrf flop count of an m x n matrix (largest-first ordering key)
+double qr_cost(int64_t m, int64_t n) {
+  const double p = (double)(m < n ? m : n), mm = (double)m, nn = (double)n;
+  return 2.0 * mm * nn * p - (mm + nn) * p * p + 2.0 / 3.0 * p * p * p + mm * nn;
+}
+
+BatchParams batch_params(const qrdm_batch_plan* P, double tau, double delta, const qrdm_opts& o) {
+  BatchParams B;
+  memset(&B, 0, sizeof(B));
+  B.desc = (const BatchDesc*)(P->work + P->off_desc);
+  B.order = (const int32_t*)(P->work + P->off_order);
+  B.count = P->count;
+  B.tau = tau;
+  B.delta = delta;
+  B.kmax = P->kmax;
+  B.eps1_mode = o.eps1_mode;
+  B.stop_at_rank = o.stop_at_rank;
+  B.check_last = o.check_last;
+  B.no_break = o.no_break;
+  B.sdd = o.sdd;
+  B.rows_pp = P->tuning.rows_per_pass;
+  B.next = (int32_t*)(P->work + P->off_next);
+  B.scratch = (double*)(P->work + P->off_scratch);
+  B.nmax = P->nmax;
+  B.rank = (int64_t*)(P->work + P->off_rank);
+  B.rank_colmax = (int64_t*)(P->work + P->off_rank_cm);
+  B.status = (int32_t*)(P->work + P->off_status);
+  B.steps = (int64_t*)(P->work + P->off_steps);
+  return B;
+}
+
+int batch_opts(const qrdm_opts* opts, qrdm_opts* o) {
+  memset(o, 0, sizeof(*o));
+  if (opts) *o = *opts;
+  o->profile = nullptr;
+  o->max_steps = 0;
+  if (o->eps1_mode != 0 && o->eps1_mode != 1) return -1;
+  if (o->precision != 0) return QRDM_ERR_UNSUPPORTED;
+  return 0;
+}
+
+cudaError_t launch_batched(const qrdm_batch_plan* P, const BatchParams& B, int grid, cudaStream_t s) {
+  const size_t smem = (size_t)batched_smem_bytes(P->kmax, P->tuning.rows_per_pass);
+  if (P->tuning.lanes_per_col == 4)
+    k_batched<4><<<grid, BT, smem, s>>>(B);
+  else
+    k_batched<8><<<grid, BT, smem, s>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_enqueue(const qrdm_batch_plan* P, double tau, double delta, const qrdm_opts& o, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(P->work + P->off_next, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess || P->count == 0) return e;
+  return launch_batched(P, batch_params(P, tau, delta, o), P->sms * P->tuning.ctas_per_sm, s);
+}
+
+int batch_common(const qrdm_batch_plan* P, double tau, double delta, const qrdm_opts* opts, qrdm_opts* o) {
+  if (!P) return -1;
+  if (!(tau > 0.0 && tau <= 1.0)) return -2;
+  if (!(delta >= 0.0 && delta <= 1.0)) return -3;
+  const int r = batch_opts(opts, o);
+  if (r == -1) return -4;
+  if (r) return r;
+  if (!P->work) return QRDM_ERR_WORKSPACE;
+  return 0;
+}
+
+#define BCK(call)                \
+  do {                           \
+    cudaError_t e_ = (call);     \
+    if (e_ != cudaSuccess) {     \
+      g_last_cuda = (int)e_;     \
+      return QRDM_ERR_CUDA;      \
+    }                            \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int qrdm_batch_plan_create(int64_t count, const qrdm_batch_matrix* h_mats, int32_t k_max, qrdm_batch_plan** plan) {
+  if (count < 0 || count > INT32_MAX) return -1;
+  if (count > 0 && !h_mats) return -2;
+  if (k_max < 1 || k_max > QRDM_KMAX_LIMIT) return -3;
+  if (!plan) return -4;
+  *plan = nullptr;
+  std::vector<BatchDesc> desc((size_t)count);
+  std::vector<std::pair<double, int32_t>> cost((size_t)count);
+  int64_t nmax = 1;
+  for (int64_t i = 0; i < count; ++i) {
+    const qrdm_batch_matrix& q = h_mats[i];
+    if (q.m < 0 || q.n < 0 || q.n > INT32_MAX || q.lda < (q.m > 1 ? q.m : 1)) return -2;
+    if (q.m > 0 && q.n > 0 && (!q.dA || !q.d_htau)) return -2;
+    if (q.n > 0 && !q.d_perm) return -2;
+    if (q.trace_cap < 0 || (q.trace_cap > 0 && !q.d_trace)) return -2;
+    BatchDesc d;
+    d.A = q.dA;
+    d.htau = q.d_htau;
+    d.perm = q.d_perm;
+    d.m = q.m;
+    d.n = q.n;
+    d.lda = q.lda;
+    d.trace = q.trace_cap > 0 ? (StepRecord*)q.d_trace : nullptr;
+    d.traceJ = q.trace_cap > 0 ? q.d_trace_J : nullptr;
+    d.trace_cap = q.trace_cap > 0 ? q.trace_cap : 0;
+    desc[(size_t)i] = d;
+    if (q.n > nmax) nmax = q.n;
+    cost[(size_t)i] = {qr_cost(q.m, q.n), (int32_t)i};
+  }
+  cudaError_t ce = batch_configure();
+  int dev = 0, sms = 0;
+  if (ce == cudaSuccess) ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (ce != cudaSuccess) {
+    g_last_cuda = (int)ce;
+    return QRDM_ERR_CUDA;
+  }
+  // largest first (longest-processing-time order of the work queue); equal
+  // costs keep the caller's order
+  std::stable_sort(cost.begin(), cost.end(),
+                   [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& b) {
+                     return a.first > b.first;
+                   });
+  qrdm_batch_plan* P = new qrdm_batch_plan();
+  P->count = count;
+  P->nmax = nmax;
+  P->kmax = k_max;
+  P->device = dev;
+  P->sms = sms;
+  P->desc = std::move(desc);
+  P->order.resize((size_t)count);
+  for (int64_t i = 0; i < count; ++i) P->order[(size_t)i] = cost[(size_t)i].second;
+  // default tuning: the largest feasible tile, one CTA per SM, 8 lanes per column
+  const int rows_try[3] = {1024, 512, 256};
+  int ok = -1;
+  for (int r : rows_try) {
+    qrdm_batch_tuning t{1, r, 8, 0};
+    ok = tuning_check(P, t);
+    if (ok == 0) {
+      P->tuning = t;
+      break;
+    }
+  }
+  if (ok != 0) {
+    delete P;
+    return ok == QRDM_ERR_CUDA ? QRDM_ERR_CUDA : QRDM_ERR_UNSUPPORTED;
+  }
+  size_t off = 0;
+  P->off_next = off;
+  off = up(off + sizeof(int32_t));
+  P->off_prof = off;
+  off = up(off + (BP_N + 2) * sizeof(unsigned long long));
+  P->off_desc = off;
+  off = up(off + (size_t)count * sizeof(BatchDesc));
+  P->off_order = off;
+  off = up(off + (size_t)count * sizeof(int32_t));
+  P->off_rank = off;
+  off = up(off + (size_t)count * sizeof(int64_t));
+  P->off_rank_cm = off;
+  off = up(off + (size_t)count * sizeof(int64_t));
+  P->off_status = off;
+  off = up(off + (size_t)count * sizeof(int32_t));
+  P->off_steps = off;
+  off = up(off + (size_t)count * sizeof(int64_t));
+  P->off_scratch = off;
+  off = up(off + (size_t)sms * QRDM_BATCH_MAX_CTAS_PER_SM * (size_t)batched_scratch_doubles(nmax) * sizeof(double));
+  P->total = off;
+  *plan = P;
+  return 0;
+}
+
+void qrdm_batch_plan_destroy(qrdm_batch_plan* plan) {
+  if (!plan) return;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+  delete plan;
+}
+
+int qrdm_batch_workspace_size(const qrdm_batch_plan* plan, size_t* bytes) {
+  if (!plan) return -1;
+  if (!bytes) return -2;
+  *bytes = plan->total;
+  return 0;
+}
+
+int qrdm_batch_bind(qrdm_batch_plan* plan, void* d_work, size_t work_bytes, void* stream_) {
+  if (!plan) return -1;
+  if (!d_work || work_bytes < plan->total || ((uintptr_t)d_work % ALIGN) != 0) return QRDM_ERR_WORKSPACE;
+  int dev = 0;
+  BCK(cudaGetDevice(&dev));
+  if (dev != plan->device) return QRDM_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream_;
+  char* w = (char*)d_work;
+  if (plan->count > 0) {
+    BCK(cudaMemcpyAsync(w + plan->off_desc, plan->desc.data(), sizeof(BatchDesc) * (size_t)plan->count,
+                        cudaMemcpyHostToDevice, s));
+    BCK(cudaMemcpyAsync(w + plan->off_order, plan->order.data(), sizeof(int32_t) * (size_t)plan->count,
+                        cudaMemcpyHostToDevice, s));
+  }
+  BCK(cudaStreamSynchronize(s));
+  if (plan->work != w && plan->exec) {
+    cudaGraphExecDestroy(plan->exec);
+    plan->exec = nullptr;
+  }
+  plan->work = w;
+  plan->work_bytes = work_bytes;
+  return 0;
+}
+
+int qrdm_batch_get_tuning(const qrdm_batch_plan* plan, qrdm_batch_tuning* tuning) {
+  if (!plan) return -1;
+  if (!tuning) return -2;
+  *tuning = plan->tuning;
+  return 0;
+}
+
+int qrdm_batch_set_tuning(qrdm_batch_plan* plan, const qrdm_batch_tuning* tuning) {
+  if (!plan) return -1;
+  if (!tuning) return -2;
+  const int r = tuning_check(plan, *tuning);
+  if (r == -1) return -2;
+  if (r) return r;
+  plan->tuning = *tuning;
+  plan->tuning.reserved = 0;
+  return 0;
+}
+
+int qrdm_factor_batched(qrdm_batch_plan* plan, double tau, double delta, const qrdm_opts* opts, void* stream) {
+  qrdm_opts o;
+  const int r = batch_common(plan, tau, delta, opts, &o);
+  if (r) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  qrdm_profile* prof = opts ? opts->profile : nullptr;
+  if (!prof || plan->count == 0) {
+    BCK(batch_enqueue(plan, tau, delta, o, s));
+    return 0;
+  }
+  // profiled run: event-timed launch with per-phase SM clock accounting
+  unsigned long long* d_clk = (unsigned long long*)(plan->work + plan->off_prof);
+  unsigned long long h_clk[BP_N + 2];
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BCK(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d_clk, 0, sizeof(h_clk), s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(plan->work + plan->off_next, 0, sizeof(int32_t), s);
+  if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+  if (ce == cudaSuccess) {
+    BatchParams B = batch_params(plan, tau, delta, o);
+    B.phase_clk = d_clk;
+    ce = launch_batched(plan, B, plan->sms * plan->tuning.ctas_per_sm, s);
+  }
+  if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_clk, d_clk, sizeof(h_clk), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ce != cudaSuccess) {
+    g_last_cuda = (int)ce;
+    return QRDM_ERR_CUDA;
+  }
+  double tot = 0.0;
+  for (int q = 0; q < BP_N; ++q) tot += (double)h_clk[q];
+  for (int q = 0; q < BP_N; ++q) prof->ms[q] += tot > 0.0 ? (double)ms * (double)h_clk[q] / tot : 0.0;
+  prof->ms[BP_N] += (double)ms;
+  const int grid = plan->sms * plan->tuning.ctas_per_sm;
+  prof->flops[0] = h_clk[BP_N + 1] ? (double)h_clk[BP_N] / grid / (double)h_clk[BP_N + 1] : 0.0;
+  prof->launches[0] += 1;
+  return 0;
+}
+
+int qrdm_factor_batched_graph(qrdm_batch_plan* plan, double tau, double delta, const qrdm_opts* opts, void* stream) {
+  qrdm_opts o;
+  const int r = batch_common(plan, tau, delta, opts, &o);
+  if (r) return r;
+  const bool same = plan->exec && plan->g_tau == tau && plan->g_delta == delta &&
+                    memcmp(&plan->g_opts, &o, sizeof(o)) == 0 &&
+                    memcmp(&plan->g_tuning, &plan->tuning, sizeof(plan->tuning)) == 0;
+  if (!same) {
+    if (plan->exec) {
+      cudaGraphExecDestroy(plan->exec);
+      plan->exec = nullptr;
+    }
+    if (!plan->cap_stream) BCK(cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t e1 = batch_enqueue(plan, tau, delta, o, plan->cap_stream);
+    const cudaError_t e2 = cudaStreamEndCapture(plan->cap_stream, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      g_last_cuda = (int)(e1 != cudaSuccess ? e1 : e2);
+      return QRDM_ERR_CUDA;
+    }
+    const cudaError_t e3 = cudaGraphInstantiate(&plan->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+      plan->exec = nullptr;
+      g_last_cuda = (int)e3;
+      return QRDM_ERR_CUDA;
+    }
+    plan->g_tau = tau;
+    plan->g_delta = delta;
+    plan->g_opts = o;
+    plan->g_tuning = plan->tuning;
+  }
+  BCK(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+  return 0;
+}
+
+int qrdm_batch_results(const qrdm_batch_plan* plan, int64_t* h_rank, int64_t* h_rank_colmax, int32_t* h_status,
+                       int64_t* h_steps, void* stream_) {
+  if (!plan) return -1;
+  if (!plan->work) return QRDM_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream_;
+  const size_t c = (size_t)plan->count;
+  if (c) {
+    if (h_rank) BCK(cudaMemcpyAsync(h_rank, plan->work + plan->off_rank, c * 8, cudaMemcpyDeviceToHost, s));
+    if (h_rank_colmax)
+      BCK(cudaMemcpyAsync(h_rank_colmax, plan->work + plan->off_rank_cm, c * 8, cudaMemcpyDeviceToHost, s));
+    if (h_status) BCK(cudaMemcpyAsync(h_status, plan->work + plan->off_status, c * 4, cudaMemcpyDeviceToHost, s));
+    if (h_steps) BCK(cudaMemcpyAsync(h_steps, plan->work + plan->off_steps, c * 8, cudaMemcpyDeviceToHost, s));
+  }
+  BCK(cudaStreamSynchronize(s));
+  return 0;
+}
+
+int qrdm_batch_autotune(qrdm_batch_plan* plan, double tau, double delta, const qrdm_opts* opts, void* stream_,
+                        qrdm_batch_tuning* best, double* best_ms) {
+  qrdm_opts o;
+  const int r = batch_common(plan, tau, delta, opts, &o);
+  if (r) return r;
+  cudaStream_t s = (cudaStream_t)stream_;
+  // back up every matrix (packed m x n), so each trial starts from the input
+  size_t total = 0;
+  for (const BatchDesc& d : plan->desc) total += (size_t)d.m * (size_t)d.n;
+  double* backup = nullptr;
+  if (total) BCK(cudaMalloc(&backup, total * sizeof(double)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto copy_all = [&](bool save) -> cudaError_t {
+    size_t off = 0;
+    for (const BatchDesc& d : plan->desc) {
+      if (d.m > 0 && d.n > 0) {
+        const size_t w = (size_t)d.m * sizeof(double);
+        cudaError_t e = save ? cudaMemcpy2DAsync(backup + off, w, d.A, (size_t)d.lda * sizeof(double), w,
+                                                 (size_t)d.n, cudaMemcpyDeviceToDevice, s)
+                             : cudaMemcpy2DAsync(d.A, (size_t)d.lda * sizeof(double), backup + off, w, w,
+                                                 (size_t)d.n, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+      }
+      off += (size_t)d.m * (size_t)d.n;
+    }
+    return cudaSuccess;
+  };
+  const qrdm_batch_tuning keep = plan->tuning;
+  qrdm_batch_tuning win = keep;
+  double win_ms = 1e300;
+  cudaError_t ce = copy_all(true);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  const int lanes[2] = {8, 4};
+  const int rows[3] = {1024, 512, 256};
+  bool warmed[2] = {false, false};
+  for (int li = 0; li < 2 && ce == cudaSuccess; ++li)
+    for (int ri = 0; ri < 3 && ce == cudaSuccess; ++ri)
+      for (int c = 1; c <= QRDM_BATCH_MAX_CTAS_PER_SM && ce == cudaSuccess; ++c) {
+        const qrdm_batch_tuning t{c, rows[ri], lanes[li], 0};
+        const int ck = tuning_check(plan, t);
+        if (ck == QRDM_ERR_CUDA) {
+          ce = (cudaError_t)g_last_cuda;
+          break;
+        }
+        if (ck) continue;
+        plan->tuning = t;
+        if (!warmed[li]) {  // first launch of this instantiation (module load): an empty batch
+          BatchParams B0 = batch_params(plan, tau, delta, o);
+          B0.count = 0;
+          ce = launch_batched(plan, B0, 1, s);
+          warmed[li] = true;
+          if (ce != cudaSuccess) break;
+        }
+        ce = copy_all(false);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+        if (ce == cudaSuccess) ce = batch_enqueue(plan, tau, delta, o, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce == cudaSuccess && ms < win_ms) {
+          win_ms = ms;
+          win = t;
+        }
+      }
+  if (ce == cudaSuccess) ce = copy_all(false);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (backup) cudaFree(backup);
+  if (ce != cudaSuccess) {
+    plan->tuning = keep;
+    g_last_cuda = (int)ce;
+    return QRDM_ERR_CUDA;
+  }
+  plan->tuning = win;
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
+  return 0;
 }
 
 }  // extern "C"

@@ -30,6 +30,9 @@ __all__ = [
     "random_dense",
     "MatrixSpec",
     "named",
+    "sigma_rank_geometric",
+    "BatchEntry",
+    "batch_entries",
 ]
 
 
@@ -114,6 +117,11 @@ def sigma_gap_geometric(p: int, r: int, lo_top: float = 1e-3, tail: float = 1e-1
     return s
 
 
+def sigma_rank_geometric(p: int, r: int, lo_top: float = 1e-12, below: float = 1e-15) -> np.ndarray:
+    """Geometric 1 -> lo_top over the first r values, then `below` (rank r)."""
+    return sigma_gap_geometric(p, r, lo_top=lo_top, tail=below)
+
+
 def kahan(n: int, c: float = 0.285, pert: float = 1e-10) -> np.ndarray:
     """Kahan matrix K = diag(s^(i-1)) (I - c * strict-upper ones), s = sqrt(1 - c^2).
 
@@ -190,3 +198,36 @@ _NAMED = {
 
 def named(name: str) -> MatrixSpec:
     return _NAMED[name]
+
+
+@dataclass(frozen=True)
+class BatchEntry:
+    """One matrix of a batched workload: shape, numerical rank and seed."""
+
+    m: int
+    n: int
+    rank: int
+    seed: int
+
+    def sigma(self) -> np.ndarray:
+        return sigma_rank_geometric(min(self.m, self.n), self.rank)
+
+    def build(self) -> np.ndarray:
+        return from_spectrum(self.m, self.n, self.sigma(), self.seed)
+
+    def build_gpu(self, device="cuda"):
+        return from_spectrum_gpu(self.m, self.n, self.sigma(), self.seed, device=device)
+
+
+def batch_entries(count: int = 2000, seed: int = 0, m_lo: int = 64, m_hi: int = 1024, n_lo: int = 32) -> list:
+    """The uneven batch: m ~ U[m_lo, m_hi], n ~ U[min(n_lo, m), m],
+    rank ~ U[ceil(n/4), n], sigma geometric 1 -> 1e-12 over the rank and
+    1e-15 below it; matrix i is seeded with seed * 1_000_003 + i."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        m = int(rng.integers(m_lo, m_hi + 1))
+        n = int(rng.integers(min(n_lo, m), m + 1))
+        r = int(rng.integers(max(1, -(-n // 4)), n + 1))
+        out.append(BatchEntry(m, n, r, seed * 1_000_003 + i))
+    return out

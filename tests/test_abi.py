@@ -88,3 +88,45 @@ def test_workspace_size_and_argument_checks(lib):
     assert rc == -11
     assert b.qrdm_strerror(2).startswith("the matrix")
     assert lib.qrdm_version() >= 100
+
+
+def test_batched_struct_layouts():
+    from paper_2106_03138_gb300 import _binding
+
+    assert ctypes.sizeof(_binding.qrdm_batch_matrix) == 72
+    assert ctypes.sizeof(_binding.qrdm_batch_tuning) == 16
+
+
+def test_batched_argument_checks(lib):
+    from paper_2106_03138_gb300 import _binding as b
+
+    fake = 1 << 20  # never dereferenced
+    good = b.qrdm_batch_matrix(fake, 8, 4, 8, fake, fake, None, None, 0)
+    # invalid arguments are rejected before any CUDA call
+    h = ctypes.c_void_p(0)
+    arr = (b.qrdm_batch_matrix * 1)(good)
+    assert lib.qrdm_batch_plan_create(-1, arr, 4, ctypes.byref(h)) == -1
+    assert lib.qrdm_batch_plan_create(1, None, 4, ctypes.byref(h)) == -2
+    assert lib.qrdm_batch_plan_create(1, arr, 0, ctypes.byref(h)) == -3
+    assert lib.qrdm_batch_plan_create(1, arr, 129, ctypes.byref(h)) == -3
+    assert lib.qrdm_batch_plan_create(1, arr, 4, None) == -4
+    for bad in (b.qrdm_batch_matrix(fake, -1, 4, 8, fake, fake, None, None, 0),       # m < 0
+                b.qrdm_batch_matrix(fake, 8, 4, 7, fake, fake, None, None, 0),        # lda < m
+                b.qrdm_batch_matrix(None, 8, 4, 8, fake, fake, None, None, 0),        # no A
+                b.qrdm_batch_matrix(fake, 8, 4, 8, None, fake, None, None, 0),        # no htau
+                b.qrdm_batch_matrix(fake, 8, 4, 8, fake, None, None, None, 0),        # no perm
+                b.qrdm_batch_matrix(fake, 8, 4, 8, fake, fake, None, None, 3)):       # trace_cap, no trace
+        arr2 = (b.qrdm_batch_matrix * 2)(good, bad)
+        assert lib.qrdm_batch_plan_create(2, arr2, 4, ctypes.byref(h)) == -2
+    # a NULL plan is refused by every call; destroying it is a no-op
+    out = ctypes.c_size_t(0)
+    assert lib.qrdm_batch_workspace_size(None, ctypes.byref(out)) == -1
+    assert lib.qrdm_batch_bind(None, fake, 1 << 20, None) == -1
+    assert lib.qrdm_factor_batched(None, 0.5, 0.5, None, None) == -1
+    assert lib.qrdm_factor_batched_graph(None, 0.5, 0.5, None, None) == -1
+    assert lib.qrdm_batch_results(None, None, None, None, None, None) == -1
+    t = b.qrdm_batch_tuning()
+    assert lib.qrdm_batch_get_tuning(None, ctypes.byref(t)) == -1
+    assert lib.qrdm_batch_set_tuning(None, ctypes.byref(t)) == -1
+    assert lib.qrdm_batch_autotune(None, 0.5, 0.5, None, None, None, None) == -1
+    lib.qrdm_batch_plan_destroy(None)
