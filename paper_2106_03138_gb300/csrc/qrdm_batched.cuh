@@ -462,36 +462,41 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
       }
       __syncthreads();
       QRDM_BPHASE(BP_PICK);
-      // ---- a6: pairwise swaps n_s + t <-> current position of J_t (Sec. 4, R14)
-      if (tid == 0)
+      // ---- a6: pairwise swaps n_s + t <-> current position of J_t (Sec. 4, R14).
+      // Thread 0 resolves the swap partners first (index work only); then every
+      // thread performs the whole swap sequence on the rows it owns, so the
+      // sequence needs no barrier between swaps.
+      if (tid == 0) {
         for (int t = 0; t < k; ++t) s_sel[t] = s_cols[s_J[t]];
+        for (int t = 0; t < k; ++t) {
+          const int64_t q = ns + t, p = s_sel[t];
+          if (p == q) continue;
+          for (int t2 = t + 1; t2 < k; ++t2)
+            if (s_sel[t2] == q) s_sel[t2] = p;
+          double x = u[q];
+          u[q] = u[p];
+          u[p] = x;
+          x = uref[q];
+          uref[q] = uref[p];
+          uref[p] = x;
+          const int32_t pt = D.perm[q];
+          D.perm[q] = D.perm[p];
+          D.perm[p] = pt;
+        }
+      }
       __syncthreads();
       for (int t = 0; t < k; ++t) {
         const int64_t q = ns + t, p = s_sel[t];
-        if (p != q) {  // uniform
-          double* cq = A + q * lda;
-          double* cp = A + p * lda;
-          for (int64_t i = tid; i < m; i += BT) {
-            const double a = cq[i];
-            cq[i] = cp[i];
-            cp[i] = a;
-          }
-          if (tid == 0) {
-            double x = u[q];
-            u[q] = u[p];
-            u[p] = x;
-            x = uref[q];
-            uref[q] = uref[p];
-            uref[p] = x;
-            const int32_t pt = D.perm[q];
-            D.perm[q] = D.perm[p];
-            D.perm[p] = pt;
-            for (int t2 = t + 1; t2 < k; ++t2)
-              if (s_sel[t2] == q) s_sel[t2] = p;
-          }
+        if (p == q) continue;
+        double* cq = A + q * lda;
+        double* cp = A + p * lda;
+        for (int64_t i = tid; i < m; i += BT) {
+          const double a = cq[i];
+          cq[i] = cp[i];
+          cp[i] = a;
         }
-        __syncthreads();
       }
+      __syncthreads();
       if (D.trace && step < D.trace_cap) {
         if (tid == 0) {
           StepRecord* r = D.trace + step;
@@ -524,8 +529,14 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
           // x^T [sub-panel column] over rows > p, and the pivot-row values
           for (int t = wp; t < w; t += BW) {
             const double* ct = A + (r0 + t) * lda;
-            double acc = 0.0;
-            for (int64_t i = p + 1 + lane; i < m; i += 32) acc = fma(x[i], ct[i], acc);
+            double acc = 0.0, acc1 = 0.0;
+            int64_t i = p + 1 + lane;
+            for (; i + 32 < m; i += 64) {
+              acc = fma(x[i], ct[i], acc);
+              acc1 = fma(x[i + 32], ct[i + 32], acc1);
+            }
+            if (i < m) acc = fma(x[i], ct[i], acc);
+            acc += acc1;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) {
@@ -596,46 +607,65 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
         QRDM_BPHASE(BP_REFLECT);
       }
       if (D.trace && step < D.trace_cap && tid == 0) D.trace[step].l = lacc;
-      // ---- a10: partial norm update (Sec. 3.2 block form; R8, R9, R16)
+      // ---- a10: partial norm update (Sec. 3.2 block form; R8, R9, R16).
+      // 8 lanes per column, 4 columns per warp: every FP64 warp instruction
+      // costs the FP64 pipe the same whatever its active lanes.
       const int64_t nsn = ns + lacc;
       int nrec = 0;
-      for (int64_t j = ns + wp; j < n; j += BW) {
-        const double* a = A + j * lda;
-        if (j < nsn) {
-          if (lane == 0) u[j] = 0.0;
-          continue;
-        }
-        bool recompute = (j < ns + k);
-        const double uj = u[j];
-        double t = 0.0;
-        if (!recompute) {
-          if (uj == 0.0) continue;
+      {
+        const int sub = lane >> 3, l8 = lane & 7;
+        for (int64_t jg = ns + (int64_t)wp * 4; jg < n; jg += (int64_t)BW * 4) {
+          const int64_t j = jg + sub;
+          int mode = 0;  // 0: nothing, 1: factored (u = 0), 2: downdate, 3: recompute
+          double uj = 0.0;
+          if (j < n) {
+            if (j < nsn) {
+              mode = 1;
+            } else if (j < ns + k) {
+              mode = 3;
+            } else {
+              uj = u[j];
+              mode = (uj == 0.0) ? 0 : 2;
+            }
+          }
+          const double* a = A + (j < n ? j : 0) * lda;
           double q = 0.0;
-          for (int64_t r = ns + lane; r < nsn; r += 32) {
-            const double xv = a[r] / uj;
-            q = fma(xv, xv, q);
+          if (mode == 2)
+            for (int64_t r = ns + l8; r < nsn; r += 8) {
+              const double xv = a[r] / uj;
+              q = fma(xv, xv, q);
+            }
+          q += __shfl_xor_sync(0xffffffffu, q, 4);
+          q += __shfl_xor_sync(0xffffffffu, q, 2);
+          q += __shfl_xor_sync(0xffffffffu, q, 1);
+          double t = 0.0;
+          if (mode == 2) {
+            t = 1.0 - q;
+            if (t < 0.0) t = 0.0;
+            const double ratio = uj / uref[j];
+            if (t * ratio * ratio <= sqeps) mode = 3;
           }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-          t = 1.0 - q;
-          if (t < 0.0) t = 0.0;
-          const double ratio = uj / uref[j];
-          recompute = (t * ratio * ratio <= sqeps);
-        }
-        if (recompute) {
-          double s = 0.0;
-          for (int64_t r = nsn + lane; r < m; r += 32) s = fma(a[r], a[r], s);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-          if (lane == 0) {
-            u[j] = sqrt(s);
-            uref[j] = u[j];
-            ++nrec;
+          double sq = 0.0;
+          if (mode == 3)
+            for (int64_t r = nsn + l8; r < m; r += 8) sq = fma(a[r], a[r], sq);
+          sq += __shfl_xor_sync(0xffffffffu, sq, 4);
+          sq += __shfl_xor_sync(0xffffffffu, sq, 2);
+          sq += __shfl_xor_sync(0xffffffffu, sq, 1);
+          if (l8 == 0) {
+            if (mode == 1) {
+              u[j] = 0.0;
+            } else if (mode == 3) {
+              const double nr = sqrt(sq);
+              u[j] = nr;
+              uref[j] = nr;
+              ++nrec;
+            } else if (mode == 2) {
+              u[j] = uj * sqrt(t);
+            }
           }
-        } else if (lane == 0) {
-          u[j] = uj * sqrt(t);
         }
       }
+      nrec = __reduce_add_sync(0xffffffffu, nrec);
       if (D.trace && step < D.trace_cap && lane == 0 && nrec)
         atomicAdd((unsigned long long*)&D.trace[step].nrecomp, (unsigned long long)nrec);
       __syncthreads();
