@@ -213,6 +213,20 @@ def run_profile_case(name: str, max_steps: int, precision: int = 0) -> int:
     import paper_2106_03138_gb300 as q
     from paper_2106_03138_gb300 import inputs
 
+    if name.startswith("batch"):
+        # the first N matrices of the 2000-matrix batch, one batched launch at
+        # the tuning the autotuner picks on the full batch
+        count = int(name[len("batch"):])
+        ents = inputs.batch_entries(2000, seed=0)[:count]
+        mats = [e.build_gpu() for e in ents]
+        plan = q.BatchPlan(mats, KMAX)
+        plan.set_tuning(2, 512, 4)
+        plan.run(TAU, DELTA)
+        res = plan.results()
+        print(json.dumps({"profile_case": name, "matrices": count, "status_ok": int((res.status == 0).sum()),
+                          "block_steps": int(res.steps.sum()), "tuning": plan.tuning}), flush=True)
+        plan.close()
+        return 0
     A = inputs.named(name).build()
     dA = q.colmajor(A)
     f = q.factor(dA, TAU, DELTA, KMAX, max_steps=max_steps, precision=precision)
