@@ -100,7 +100,48 @@ typedef struct qrdm_opts {
   int32_t reserved1;
   /* host, optional: per-kernel event timing (see qrdm_profile). */
   qrdm_profile* profile;
+  /* host, optional: learned per-step (tau, delta) and feature logging (see
+     qrdm_policy); NULL: tau and delta fixed for the whole factorization. */
+  const struct qrdm_policy* policy;
 } qrdm_opts;
+
+/*
+ * Learned per-step (tau, delta).  The paper fixes tau and delta for a whole
+ * factorization and studies their choice empirically (Sec. 5); this library
+ * can instead pick them per DM step with a small MLP over features of the
+ * step.  Features (QRDM_POLICY_NFEAT = 16 floats, at the start of a DM step,
+ * after mu = max u):
+ *   0..7  min(#{j >= n_s, j != j*: u_j >= t mu}, 128) / 128 for
+ *         t = 0.95, 0.9, 0.75, 0.6, 0.45, 0.3, 0.15, 0.05;
+ *   8     (n - n_s) / n;   9  log2(n - n_s) / 16;
+ *   10    log10(mu / max_j ||a_j||) / 16;
+ *   11    l of the previous step / 64 (at most 1);   12  its l / k;
+ *   13,14 mean and max |theta(j*, i)| over the previous step's candidates;
+ *   15    tau of the previous step (0, 1, 0, 0, 0 for the first step).
+ * MLP 16 -> 64 -> 64 -> 2 with ReLU, BF16 weights, FP32 accumulation;
+ * tau_s = tau_lo + (tau_hi - tau_lo) sigmoid(o_0), delta_s likewise from o_1.
+ * Weights: QRDM_POLICY_NPARAM bf16 values, row-major W1[16][64], b1[64],
+ * W2[64][64], b2[64], W3[64][2], b3[2] (qrdm_mlp_* train them).
+ * Guard: when a step that used the MLP accepts a pivot with
+ * |R_ii| < rho_min * mu, the policy is switched off and the fixed (tau, delta)
+ * of the call finish the factorization.  Single-column steps (after the
+ * stopping criterion) ignore the policy.
+ * With d_weights == NULL nothing is predicted: tau and delta stay fixed and
+ * only the logs are written (training data from plain runs).
+ */
+#define QRDM_POLICY_NFEAT 16
+#define QRDM_POLICY_HIDDEN 64
+#define QRDM_POLICY_NPARAM 5378
+
+typedef struct qrdm_policy {
+  const void* d_weights; /* device bf16 weights, or NULL */
+  float* d_feat_log;     /* device, optional: log_cap x 16 features per block step (qrdm_factor only) */
+  double* d_act_log;     /* device, optional: log_cap x 2 (tau_s, delta_s) per block step (qrdm_factor only) */
+  int64_t log_cap;
+  double tau_lo, tau_hi;     /* 0 < tau_lo <= tau_hi <= 1 */
+  double delta_lo, delta_hi; /* 0 <= delta_lo <= delta_hi <= 1 */
+  double rho_min;            /* >= 0 */
+} qrdm_policy;
 
 /* Host-side results of one factorization. */
 typedef struct qrdm_info {
@@ -237,7 +278,9 @@ int qrdm_factor_noalloc(double* dA, int64_t m, int64_t n, int64_t lda, double ta
  * (d_trace, d_trace_J, trace_cap) is written as in qrdm_factor.  opts may be
  * NULL; eps1_mode, stop_at_rank, check_last, no_break and sdd are honoured,
  * max_steps is ignored, precision must be 0 (QRDM_ERR_UNSUPPORTED
- * otherwise).  A profile (qrdm_factor_batched only; it then times the launch
+ * otherwise).  opts->policy applies to every matrix (its d_weights, ranges and
+ * rho_min; the per-matrix logs come from qrdm_batch_matrix).  A profile
+ * (qrdm_factor_batched only; it then times the launch
  * with events and synchronizes `stream`) receives, added to its contents:
  * ms[0..7] the kernel time split by the CTAs' clock shares of the phases
  * norms, argmax and candidates, Gram, DM pick, swaps, panel, block
@@ -262,6 +305,9 @@ typedef struct qrdm_batch_matrix {
   qrdm_step_record* d_trace; /* optional device trace, trace_cap records (NULL/0: none) */
   int32_t* d_trace_J;        /* optional, trace_cap * k_max int32 */
   int64_t trace_cap;
+  float* d_feat_log;         /* optional, log_cap x 16 policy features per block step */
+  double* d_act_log;         /* optional, log_cap x 2 (tau_s, delta_s) per block step */
+  int64_t log_cap;
 } qrdm_batch_matrix;
 
 typedef struct qrdm_batch_tuning {
@@ -283,6 +329,47 @@ int qrdm_factor_batched(qrdm_batch_plan* plan, double tau, double delta, const q
 int qrdm_factor_batched_graph(qrdm_batch_plan* plan, double tau, double delta, const qrdm_opts* opts, void* stream);
 int qrdm_batch_results(const qrdm_batch_plan* plan, int64_t* h_rank, int64_t* h_rank_colmax, int32_t* h_status,
                        int64_t* h_steps, void* stream);
+
+/*
+ * Training of the learned (tau, delta) policy (qrdm_policy): the MLP's
+ * forward pass, its loss gradient, Adam, and a minibatch training loop, all
+ * on the device.  FP32 master weights d_w32 (QRDM_POLICY_NPARAM floats) and
+ * BF16 working weights d_w16 (QRDM_POLICY_NPARAM bf16, what the forward pass
+ * and the factorization read).  Inputs x: batch x 16 features (row-major),
+ * targets t: batch x 2 in [0, 1] (the normalized tau and delta), outputs
+ * y = sigmoid(o): batch x 2.  Loss L = (1/B) sum_b sum_o (y_bo - t_bo)^2 / 2.
+ * The gradient is taken with respect to the BF16 weights (the master weights
+ * receive it unchanged).  Every kernel is deterministic (fixed summation
+ * order, no atomics); minibatch row b of step s is sample
+ * splitmix64(seed, s, b) mod nsamples.  The paper has no learned component.
+ *   qrdm_mlp_workspace_size  float workspace bytes for a batch;
+ *   qrdm_mlp_init            He-uniform weights from the seed, zero biases,
+ *                            and the BF16 copy;
+ *   qrdm_mlp_to_bf16         refresh the BF16 copy from the master weights;
+ *   qrdm_mlp_forward         y for a batch;
+ *   qrdm_mlp_loss_grad       L (1 float) and dL/dw (QRDM_POLICY_NPARAM floats);
+ *   qrdm_mlp_adam_step       one Adam step (Kingma & Ba; decoupled weight
+ *                            decay, none on biases), step counter t >= 1;
+ *   qrdm_mlp_train           `steps` minibatches of `batch` samples from
+ *                            (d_x, d_t) with Adam (beta1 0.9, beta2 0.999,
+ *                            eps 1e-8); d_adam holds 2 x QRDM_POLICY_NPARAM
+ *                            floats (zero them before the first call);
+ *                            d_loss_log (optional) receives each step's loss.
+ * All pointers are device memory; calls enqueue on `stream` and return.
+ * Errors: -i for an invalid i-th argument, QRDM_ERR_WORKSPACE, QRDM_ERR_CUDA.
+ */
+int qrdm_mlp_workspace_size(int64_t batch, size_t* bytes);
+int qrdm_mlp_init(float* d_w32, void* d_w16, uint64_t seed, void* stream);
+int qrdm_mlp_to_bf16(const float* d_w32, void* d_w16, void* stream);
+int qrdm_mlp_forward(const void* d_w16, const float* d_x, int64_t batch, float* d_y, float* d_work,
+                     size_t work_bytes, void* stream);
+int qrdm_mlp_loss_grad(const void* d_w16, const float* d_x, const float* d_t, int64_t batch, float* d_grad,
+                       float* d_loss, float* d_work, size_t work_bytes, void* stream);
+int qrdm_mlp_adam_step(float* d_w32, void* d_w16, const float* d_grad, float* d_m, float* d_v, int64_t t, float lr,
+                       float beta1, float beta2, float eps, float weight_decay, void* stream);
+int qrdm_mlp_train(float* d_w32, void* d_w16, float* d_adam, const float* d_x, const float* d_t, int64_t nsamples,
+                   int64_t batch, int64_t steps, float lr, float weight_decay, uint64_t seed, float* d_loss_log,
+                   float* d_work, size_t work_bytes, void* stream);
 
 /* Static description of an error code. */
 const char* qrdm_strerror(int code);

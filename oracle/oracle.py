@@ -76,6 +76,9 @@ def _load():
             lib.oq_qrdm.restype = ctypes.c_int
             lib.oq_qrdm.argtypes = [i64, i64, p, i64, f64, f64, i64, i64, i64, i64, i64, i64, i64, p, p, p, p, p, p,
                                     p, i64, p, p]
+            lib.oq_qrdm_sched.restype = ctypes.c_int
+            lib.oq_qrdm_sched.argtypes = [i64, i64, p, i64, f64, f64, i64, i64, i64, i64, i64, i64, i64, p, p, p, p, p,
+                                          p, p, i64, p, p, p, p, i64]
             lib.oq_house.restype = None
             lib.oq_house.argtypes = [i64, p, p, p]
             lib.oq_larft.restype = None
@@ -130,7 +133,7 @@ def cosine(A: np.ndarray, cols, r0: int = 0):
 
 def qrdm(A: np.ndarray, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mode: int = 0,
          stop_at_rank: bool = False, check_last: bool = False, no_break: bool = False, sdd: bool = False,
-         max_steps: int = 0, trace_cap: int | None = None) -> dict:
+         max_steps: int = 0, trace_cap: int | None = None, schedule=None) -> dict:
     """Factor A Pi = Q R by QRDM2.  Returns a dict:
 
     ``A`` (R above the diagonal, reflector tails below), ``htau``, ``perm``,
@@ -152,10 +155,20 @@ def qrdm(A: np.ndarray, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *
     trace = np.zeros(cap, dtype=STEP_DTYPE)
     J = np.full((cap, k_max), -1, dtype=np.int64)
     nsteps = np.zeros(1, dtype=np.int64)
-    st = lib.oq_qrdm(m, n, _ptr(A), max(m, 1), float(tau), float(delta), int(k_max), int(eps1_mode),
-                     int(stop_at_rank), int(check_last), int(no_break), int(sdd), int(max_steps), _ptr(htau),
-                     _ptr(perm), _ptr(rank), _ptr(rank_cm), _ptr(u), _ptr(uref), _ptr(trace), cap, _ptr(J),
-                     _ptr(nsteps))
+    if schedule is None:
+        st = lib.oq_qrdm(m, n, _ptr(A), max(m, 1), float(tau), float(delta), int(k_max), int(eps1_mode),
+                         int(stop_at_rank), int(check_last), int(no_break), int(sdd), int(max_steps), _ptr(htau),
+                         _ptr(perm), _ptr(rank), _ptr(rank_cm), _ptr(u), _ptr(uref), _ptr(trace), cap, _ptr(J),
+                         _ptr(nsteps))
+    else:
+        # per-step (tau, delta): schedule is an (S, 2) array
+        sch = np.ascontiguousarray(np.asarray(schedule, dtype=np.float64).reshape(-1, 2))
+        ts = np.ascontiguousarray(sch[:, 0])
+        ds = np.ascontiguousarray(sch[:, 1])
+        st = lib.oq_qrdm_sched(m, n, _ptr(A), max(m, 1), float(tau), float(delta), int(k_max), int(eps1_mode),
+                               int(stop_at_rank), int(check_last), int(no_break), int(sdd), int(max_steps),
+                               _ptr(htau), _ptr(perm), _ptr(rank), _ptr(rank_cm), _ptr(u), _ptr(uref), _ptr(trace),
+                               cap, _ptr(J), _ptr(nsteps), _ptr(ts), _ptr(ds), int(sch.shape[0]))
     ns = int(nsteps[0])
     return {
         "status": int(st),

@@ -183,16 +183,20 @@ static int cmp_desc(double ua, int64_t pa, double ub, int64_t pb) {
  *   no_break: Algorithm 3 (no break test)
  *   sdd: per-step delta_s = min(delta, tau^2 / max(1, |I|)) (eq. delta_max)
  *   max_steps: stop after this many block steps (<= 0: no limit)
+ *   tau_sched, delta_sched, sched_len (oq_qrdm_sched only): the (tau, delta)
+ *   of block step s is (tau_sched[s], delta_sched[s]) for s < sched_len,
+ *   else (tau, delta) (a per-step schedule, e.g. one a learned policy chose)
  * Outputs: rank (criterion eq. practical stopping criterion), rank_colmax
  *   (the same test without the sqrt(n - n_s) factor), u_out/uref_out (n, may
  *   be NULL), trace (trace_cap records, may be NULL), Jout (trace_cap*k_max
  *   original column indices of J per step), nsteps.
  * Returns 0, or -i for an invalid i-th argument, or 1 for non-finite input.
  */
-int oq_qrdm(int64_t m, int64_t n, double* A, int64_t lda, double tau, double delta, int64_t kmax, int64_t eps1_mode,
-            int64_t stop_at_rank, int64_t check_last, int64_t no_break, int64_t sdd, int64_t max_steps, double* htau,
-            int64_t* perm, int64_t* rank_out, int64_t* rank_colmax_out, double* u_out, double* uref_out,
-            oq_step* trace, int64_t trace_cap, int64_t* Jout, int64_t* nsteps_out) {
+int oq_qrdm_sched(int64_t m, int64_t n, double* A, int64_t lda, double tau, double delta, int64_t kmax,
+                  int64_t eps1_mode, int64_t stop_at_rank, int64_t check_last, int64_t no_break, int64_t sdd,
+                  int64_t max_steps, double* htau, int64_t* perm, int64_t* rank_out, int64_t* rank_colmax_out,
+                  double* u_out, double* uref_out, oq_step* trace, int64_t trace_cap, int64_t* Jout,
+                  int64_t* nsteps_out, const double* tau_sched, const double* delta_sched, int64_t sched_len) {
   if (m < 0) return -1;
   if (n < 0) return -2;
   if (lda < (m > 1 ? m : 1)) return -4;
@@ -239,6 +243,9 @@ int oq_qrdm(int64_t m, int64_t n, double* A, int64_t lda, double tau, double del
   int64_t ns = 0, step = 0;
   while (ns < kmin) {
     if (max_steps > 0 && step >= max_steps) break;
+    const int in_sched = (tau_sched && delta_sched && step < sched_len);
+    const double tau_s = in_sched ? tau_sched[step] : tau;
+    const double delta_s = in_sched ? delta_sched[step] : delta;
     oq_step rec;
     memset(&rec, 0, sizeof(rec));
     rec.ns = ns;
@@ -297,7 +304,7 @@ int oq_qrdm(int64_t m, int64_t n, double* A, int64_t lda, double tau, double del
     /* ---- a3: candidate set I (eq. def_candidate_set), sorted, capped ---- */
     int64_t nc = 0;
     if (kcap > 1) {
-      const double thr = tau * mu;
+      const double thr = tau_s * mu;
       for (int64_t j = ns; j < n; ++j) {
         if (j == jstar) continue;
         if (mu > 0.0) {
@@ -341,9 +348,9 @@ int oq_qrdm(int64_t m, int64_t n, double* A, int64_t lda, double tau, double del
     const int64_t kc = nc + 1;
     if (nc > 0) {
       oq_cosine(m, ns, A, lda, kc, cols, G, Th);
-      double dlt = delta;
+      double dlt = delta_s;
       if (sdd) {
-        double dm = tau * tau / (double)(nc > 1 ? nc : 1);
+        double dm = tau_s * tau_s / (double)(nc > 1 ? nc : 1);
         if (dm < dlt) dlt = dm;
       }
       for (int64_t a = 1; a < kc; ++a) {
@@ -397,7 +404,7 @@ int oq_qrdm(int64_t m, int64_t n, double* A, int64_t lda, double tau, double del
     }
 
     /* ---- a7: panel with break check (Alg. 4 inner loop) ---- */
-    const double eps_s = tau * mu;
+    const double eps_s = tau_s * mu;
     rec.eps_s = eps_s;
     int64_t lacc = k;
     for (int64_t l = 0; l < k; ++l) {
@@ -530,3 +537,12 @@ int oq_qrdm(int64_t m, int64_t n, double* A, int64_t lda, double tau, double del
 }
 
 int64_t oq_step_size(void) { return (int64_t)sizeof(oq_step); }
+
+int oq_qrdm(int64_t m, int64_t n, double* A, int64_t lda, double tau, double delta, int64_t kmax, int64_t eps1_mode,
+            int64_t stop_at_rank, int64_t check_last, int64_t no_break, int64_t sdd, int64_t max_steps, double* htau,
+            int64_t* perm, int64_t* rank_out, int64_t* rank_colmax_out, double* u_out, double* uref_out,
+            oq_step* trace, int64_t trace_cap, int64_t* Jout, int64_t* nsteps_out) {
+  return oq_qrdm_sched(m, n, A, lda, tau, delta, kmax, eps1_mode, stop_at_rank, check_last, no_break, sdd, max_steps,
+                       htau, perm, rank_out, rank_colmax_out, u_out, uref_out, trace, trace_cap, Jout, nsteps_out,
+                       NULL, NULL, 0);
+}

@@ -27,6 +27,7 @@ from ._binding import (  # noqa: F401
     qrdm_info,
     KERNEL_NAMES,
     qrdm_opts,
+    qrdm_policy,
     qrdm_profile,
     qrdm_step_record,
     qrdm_strerror,
@@ -60,12 +61,15 @@ class Factorization:
 
 
 def make_opts(eps1_mode=0, stop_at_rank=False, check_last=False, no_break=False, sdd=False, max_steps=0,
-              profile: qrdm_profile | None = None, precision: int = 0) -> qrdm_opts:
+              profile: qrdm_profile | None = None, precision: int = 0,
+              policy: qrdm_policy | None = None) -> qrdm_opts:
     import ctypes
 
     o = qrdm_opts()
     if profile is not None:
         o.profile = ctypes.pointer(profile)
+    if policy is not None:
+        o.policy = ctypes.pointer(policy)
     o.eps1_mode = int(eps1_mode)
     o.stop_at_rank = int(bool(stop_at_rank))
     o.check_last = int(bool(check_last))
@@ -96,7 +100,8 @@ def colmajor(A, device="cuda"):
 def factor(A, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mode: int = 0,
            stop_at_rank: bool = False, check_last: bool = False, no_break: bool = False, sdd: bool = False,
            max_steps: int = 0, trace: bool = False, workspace=None, out_htau=None, out_perm=None,
-           stream=None, profile: qrdm_profile | None = None, precision: int = 0) -> Factorization:
+           stream=None, profile: qrdm_profile | None = None, precision: int = 0,
+           policy: qrdm_policy | None = None) -> Factorization:
     """Factor A Pi = Q R in place.  ``A`` is a CUDA float64 tensor with
     stride(0) == 1 (column-major, lda = stride(1)).  ``precision=1`` selects
     the FP32-class mixed-precision form (see include/qrdm.h)."""
@@ -124,7 +129,7 @@ def factor(A, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mod
         tr = torch.zeros(cap * TRACE_DTYPE.itemsize, dtype=torch.uint8, device=dev)
         trJ = torch.empty(cap * k_max, dtype=torch.int32, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
-    opts = make_opts(eps1_mode, stop_at_rank, check_last, no_break, sdd, max_steps, profile, precision)
+    opts = make_opts(eps1_mode, stop_at_rank, check_last, no_break, sdd, max_steps, profile, precision, policy)
     rc, info = qrdm_factor(A.data_ptr() if m * n else 0, m, n, lda, float(tau), float(delta), int(k_max),
                            htau.data_ptr(), perm.data_ptr(), opts, workspace.data_ptr(), workspace.numel(),
                            s.cuda_stream, tr.data_ptr() if tr is not None else 0,

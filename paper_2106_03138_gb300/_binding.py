@@ -31,10 +31,20 @@ class qrdm_profile(ctypes.Structure):
     _fields_ = [("ms", c_f64 * 16), ("flops", c_f64 * 16), ("launches", c_i64 * 16)]
 
 
+class qrdm_policy(ctypes.Structure):
+    _fields_ = [("d_weights", c_p), ("d_feat_log", c_p), ("d_act_log", c_p), ("log_cap", c_i64),
+                ("tau_lo", c_f64), ("tau_hi", c_f64), ("delta_lo", c_f64), ("delta_hi", c_f64), ("rho_min", c_f64)]
+
+
+QRDM_POLICY_NFEAT = 16
+QRDM_POLICY_HIDDEN = 64
+QRDM_POLICY_NPARAM = 5378
+
+
 class qrdm_opts(ctypes.Structure):
     _fields_ = [("eps1_mode", c_i32), ("stop_at_rank", c_i32), ("check_last", c_i32), ("no_break", c_i32),
                 ("sdd", c_i32), ("max_steps", c_i32), ("precision", c_i32), ("reserved1", c_i32),
-                ("profile", ctypes.POINTER(qrdm_profile))]
+                ("profile", ctypes.POINTER(qrdm_profile)), ("policy", ctypes.POINTER(qrdm_policy))]
 
 
 class qrdm_info(ctypes.Structure):
@@ -49,7 +59,8 @@ class qrdm_step_record(ctypes.Structure):
 
 class qrdm_batch_matrix(ctypes.Structure):
     _fields_ = [("dA", c_p), ("m", c_i64), ("n", c_i64), ("lda", c_i64), ("d_htau", c_p), ("d_perm", c_p),
-                ("d_trace", c_p), ("d_trace_J", c_p), ("trace_cap", c_i64)]
+                ("d_trace", c_p), ("d_trace_J", c_p), ("trace_cap", c_i64), ("d_feat_log", c_p), ("d_act_log", c_p),
+                ("log_cap", c_i64)]
 
 
 class qrdm_batch_tuning(ctypes.Structure):
@@ -66,7 +77,9 @@ QRDM_BATCH_MAX_CTAS_PER_SM = 2
 EXPORTS = ("qrdm_workspace_size", "qrdm_factor", "qrdm_factor_noalloc", "qrdm_strerror", "qrdm_last_cuda_error",
            "qrdm_version", "qrdm_batch_plan_create", "qrdm_batch_plan_destroy", "qrdm_batch_workspace_size",
            "qrdm_batch_bind", "qrdm_batch_get_tuning", "qrdm_batch_set_tuning", "qrdm_batch_autotune",
-           "qrdm_factor_batched", "qrdm_factor_batched_graph", "qrdm_batch_results")
+           "qrdm_factor_batched", "qrdm_factor_batched_graph", "qrdm_batch_results", "qrdm_mlp_workspace_size",
+           "qrdm_mlp_init", "qrdm_mlp_to_bf16", "qrdm_mlp_forward", "qrdm_mlp_loss_grad", "qrdm_mlp_adam_step",
+           "qrdm_mlp_train")
 QRDM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 _lock = threading.Lock()
@@ -125,6 +138,18 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.qrdm_factor_batched_graph.argtypes = [c_p, c_f64, c_f64, P(qrdm_opts), c_p]
         lib.qrdm_batch_results.restype = ctypes.c_int
         lib.qrdm_batch_results.argtypes = [c_p, c_p, c_p, c_p, c_p, c_p]
+        f32, u64 = ctypes.c_float, ctypes.c_uint64
+        for name, args in (("qrdm_mlp_workspace_size", [c_i64, P(c_sz)]),
+                           ("qrdm_mlp_init", [c_p, c_p, u64, c_p]),
+                           ("qrdm_mlp_to_bf16", [c_p, c_p, c_p]),
+                           ("qrdm_mlp_forward", [c_p, c_p, c_i64, c_p, c_p, c_sz, c_p]),
+                           ("qrdm_mlp_loss_grad", [c_p, c_p, c_p, c_i64, c_p, c_p, c_p, c_sz, c_p]),
+                           ("qrdm_mlp_adam_step", [c_p, c_p, c_p, c_p, c_p, c_i64, f32, f32, f32, f32, f32, c_p]),
+                           ("qrdm_mlp_train", [c_p, c_p, c_p, c_p, c_p, c_i64, c_i64, c_i64, f32, f32, u64, c_p,
+                                               c_p, c_sz, c_p])):
+            fn = getattr(lib, name)
+            fn.restype = ctypes.c_int
+            fn.argtypes = args
         _lib = lib
         return lib
 
@@ -218,3 +243,11 @@ def qrdm_factor_batched_graph(plan: int, tau: float, delta: float, opts, stream:
 def qrdm_batch_results(plan: int, h_rank: int, h_rank_colmax: int, h_status: int, h_steps: int, stream: int) -> int:
     return load().qrdm_batch_results(plan or None, h_rank or None, h_rank_colmax or None, h_status or None,
                                      h_steps or None, stream or None)
+
+
+def qrdm_mlp_workspace_size(batch: int) -> int:
+    out = c_sz(0)
+    rc = load().qrdm_mlp_workspace_size(batch, ctypes.byref(out))
+    if rc != 0:
+        raise ValueError(f"qrdm_mlp_workspace_size: invalid argument {-rc}")
+    return int(out.value)

@@ -31,7 +31,7 @@ class BatchPlan:
     (as ``factor(trace=True)`` does).  The plan may be run many times; each
     run factors the tensors as they are at that moment."""
 
-    def __init__(self, mats, k_max: int, *, trace: bool = False, stream=None):
+    def __init__(self, mats, k_max: int, *, trace: bool = False, policy_logs: bool = False, stream=None):
         import torch
 
         from . import QRDMError
@@ -42,6 +42,7 @@ class BatchPlan:
         dev = self.mats[0].device if self.mats else torch.device("cuda", torch.cuda.current_device())
         self.device = dev
         self.htau, self.perm, self._trace, self._traceJ, self._cap = [], [], [], [], []
+        self._flog, self._alog = [], []
         descs = []
         for A in self.mats:
             if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2):
@@ -58,7 +59,7 @@ class BatchPlan:
             self.htau.append(h)
             self.perm.append(p)
             d = _b.qrdm_batch_matrix(A.data_ptr() if m * n else None, m, n, lda, h.data_ptr(), p.data_ptr(),
-                                     None, None, 0)
+                                     None, None, 0, None, None, 0)
             if trace:
                 from . import TRACE_DTYPE
 
@@ -69,6 +70,13 @@ class BatchPlan:
                 self._trace.append(tr)
                 self._traceJ.append(tj)
                 self._cap.append(cap)
+            if policy_logs:
+                lcap = max(kmin, 1) + 1
+                fl = torch.zeros((lcap, _b.QRDM_POLICY_NFEAT), dtype=torch.float32, device=dev)
+                al = torch.zeros((lcap, 2), dtype=torch.float64, device=dev)
+                d.d_feat_log, d.d_act_log, d.log_cap = fl.data_ptr(), al.data_ptr(), lcap
+                self._flog.append(fl)
+                self._alog.append(al)
             descs.append(d)
         rc, self._h = _b.qrdm_batch_plan_create(descs, self.k_max)
         if rc != 0:
@@ -147,6 +155,13 @@ class BatchPlan:
         tr = np.frombuffer(self._trace[i].cpu().numpy().tobytes(), dtype=TRACE_DTYPE)[:ns].copy()
         J = self._traceJ[i].cpu().numpy().reshape(cap, self.k_max)[:ns].copy()
         return tr, J
+
+    def policy_logs(self, i: int, nsteps: int):
+        """(features [nsteps x 16], (tau_s, delta_s) [nsteps x 2]) of matrix i
+        (rows of single-column steps after the stopping criterion are zero in
+        the features)."""
+        ns = min(int(nsteps), self._flog[i].shape[0])
+        return self._flog[i][:ns].cpu().numpy(), self._alog[i][:ns].cpu().numpy()
 
     def outputs(self, i: int):
         """(htau, perm) views of matrix i."""

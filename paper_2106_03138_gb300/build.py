@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqrdm.so")
-SOURCES = [os.path.join(CSRC, "qrdm.cu"), os.path.join(CSRC, "qrdm_noalloc.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("qrdm.cu", "qrdm_noalloc.cu", "qrdm_mlp.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(os.path.dirname(HERE), "include", "qrdm.h")
 ]
@@ -28,15 +28,28 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every translation unit in parallel, then link the library."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, *SOURCES,
-           "-lcudart"]
+    flags = [*ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+        flags.insert(0, "-Xptxas=-v")
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + f".{os.getpid()}.o")
+        objs.append(obj)
+        procs.append(subprocess.Popen([nvcc(), *flags, "-c", src, "-o", obj]))
+    rcs = [p.wait() for p in procs]
+    if any(rcs):
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
+        raise subprocess.CalledProcessError(max(rcs), "nvcc")
+    tmp = LIB + f".tmp{os.getpid()}"
+    subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

@@ -154,6 +154,31 @@ int configure(DeviceConfig* cfg) {
   return 0;
 }
 
+bool policy_valid(const qrdm_policy* p) {
+  if (!p) return true;
+  if (!(p->tau_lo > 0.0 && p->tau_lo <= p->tau_hi && p->tau_hi <= 1.0)) return false;
+  if (!(p->delta_lo >= 0.0 && p->delta_lo <= p->delta_hi && p->delta_hi <= 1.0)) return false;
+  if (!(p->rho_min >= 0.0) || p->log_cap < 0) return false;
+  return true;
+}
+
+PolicyParams policy_params(const qrdm_policy* p) {
+  PolicyParams pp;
+  memset(&pp, 0, sizeof(pp));
+  if (!p) return pp;
+  pp.active = 1;
+  pp.w = (const __nv_bfloat16*)p->d_weights;
+  pp.feat_log = p->log_cap > 0 ? p->d_feat_log : nullptr;
+  pp.act_log = p->log_cap > 0 ? p->d_act_log : nullptr;
+  pp.log_cap = p->log_cap;
+  pp.tau_lo = p->tau_lo;
+  pp.tau_hi = p->tau_hi;
+  pp.delta_lo = p->delta_lo;
+  pp.delta_hi = p->delta_hi;
+  pp.rho_min = p->rho_min;
+  return pp;
+}
+
 #define CK(call)                                  \
   do {                                            \
     cudaError_t e_ = (call);                      \
@@ -165,6 +190,11 @@ int configure(DeviceConfig* cfg) {
   } while (0)
 
 }  // namespace
+
+namespace qrdm {
+// the other translation units record their CUDA errors here
+void set_last_cuda_error(int e) { g_last_cuda = e; }
+}  // namespace qrdm
 
 extern "C" {
 
@@ -220,6 +250,7 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   if (opts) o = *opts;
   if (o.eps1_mode != 0 && o.eps1_mode != 1) return -11;
   if (o.precision != 0 && o.precision != 1) return -11;
+  if (!policy_valid(o.policy)) return -11;
   cudaStream_t stream = (cudaStream_t)stream_;
 
   if (n == 0 || m == 0) {
@@ -303,6 +334,7 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   P.trace = (StepRecord*)d_trace;
   P.traceJ = d_trace_J;
   P.trace_cap = d_trace ? trace_cap : 0;
+  P.pol = policy_params(o.policy);
 
   CK(cudaMemsetAsync(d_htau, 0, sizeof(double) * (size_t)kmin, stream));
   if (d_trace && trace_cap > 0) CK(cudaMemsetAsync(d_trace, 0, sizeof(qrdm_step_record) * (size_t)trace_cap, stream));
@@ -533,6 +565,7 @@ struct qrdm_batch_plan {
   cudaStream_t cap_stream = nullptr;
   double g_tau = -1.0, g_delta = -1.0;
   qrdm_opts g_opts{};
+  qrdm_policy g_pol{};
   qrdm_batch_tuning g_tuning{};
 };
 
@@ -608,6 +641,10 @@ BatchParams batch_params(const qrdm_batch_plan* P, double tau, double delta, con
   B.rank_colmax = (int64_t*)(P->work + P->off_rank_cm);
   B.status = (int32_t*)(P->work + P->off_status);
   B.steps = (int64_t*)(P->work + P->off_steps);
+  B.pol = policy_params(o.policy);
+  B.pol.feat_log = nullptr;  // per matrix, from the descriptors
+  B.pol.act_log = nullptr;
+  B.pol.log_cap = 0;
   return B;
 }
 
@@ -617,6 +654,7 @@ int batch_opts(const qrdm_opts* opts, qrdm_opts* o) {
   o->profile = nullptr;
   o->max_steps = 0;
   if (o->eps1_mode != 0 && o->eps1_mode != 1) return -1;
+  if (!policy_valid(o->policy)) return -1;
   if (o->precision != 0) return QRDM_ERR_UNSUPPORTED;
   return 0;
 }
@@ -675,6 +713,7 @@ int qrdm_batch_plan_create(int64_t count, const qrdm_batch_matrix* h_mats, int32
     if (q.m > 0 && q.n > 0 && (!q.dA || !q.d_htau)) return -2;
     if (q.n > 0 && !q.d_perm) return -2;
     if (q.trace_cap < 0 || (q.trace_cap > 0 && !q.d_trace)) return -2;
+    if (q.log_cap < 0) return -2;
     BatchDesc d;
     d.A = q.dA;
     d.htau = q.d_htau;
@@ -685,6 +724,9 @@ int qrdm_batch_plan_create(int64_t count, const qrdm_batch_matrix* h_mats, int32
     d.trace = q.trace_cap > 0 ? (StepRecord*)q.d_trace : nullptr;
     d.traceJ = q.trace_cap > 0 ? q.d_trace_J : nullptr;
     d.trace_cap = q.trace_cap > 0 ? q.trace_cap : 0;
+    d.feat_log = q.log_cap > 0 ? q.d_feat_log : nullptr;
+    d.act_log = q.log_cap > 0 ? q.d_act_log : nullptr;
+    d.log_cap = q.log_cap > 0 ? q.log_cap : 0;
     desc[(size_t)i] = d;
     if (q.n > nmax) nmax = q.n;
     cost[(size_t)i] = {qr_cost(q.m, q.n), (int32_t)i};
@@ -856,8 +898,11 @@ int qrdm_factor_batched_graph(qrdm_batch_plan* plan, double tau, double delta, c
   qrdm_opts o;
   const int r = batch_common(plan, tau, delta, opts, &o);
   if (r) return r;
+  qrdm_policy pol_now;
+  memset(&pol_now, 0, sizeof(pol_now));
+  if (o.policy) pol_now = *o.policy;
   const bool same = plan->exec && plan->g_tau == tau && plan->g_delta == delta &&
-                    memcmp(&plan->g_opts, &o, sizeof(o)) == 0 &&
+                    memcmp(&plan->g_opts, &o, sizeof(o)) == 0 && memcmp(&plan->g_pol, &pol_now, sizeof(pol_now)) == 0 &&
                     memcmp(&plan->g_tuning, &plan->tuning, sizeof(plan->tuning)) == 0;
   if (!same) {
     if (plan->exec) {
@@ -884,6 +929,7 @@ int qrdm_factor_batched_graph(qrdm_batch_plan* plan, double tau, double delta, c
     plan->g_tau = tau;
     plan->g_delta = delta;
     plan->g_opts = o;
+    plan->g_pol = pol_now;
     plan->g_tuning = plan->tuning;
   }
   BCK(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));

@@ -43,6 +43,9 @@ struct BatchDesc {
   StepRecord* trace;  // optional step trace (nullptr: none)
   int32_t* traceJ;    // trace_cap x kmax original column indices of J
   int64_t trace_cap;
+  float* feat_log;    // optional [log_cap][POL_NFEAT] policy features per step
+  double* act_log;    // optional [log_cap][2] (tau_s, delta_s) per step
+  int64_t log_cap;
 };
 
 struct BatchParams {
@@ -61,6 +64,7 @@ struct BatchParams {
   int32_t* status;        // [count] 0 ok, 1 non-finite input
   int64_t* steps;         // [count]
   unsigned long long* phase_clk;  // optional: SM cycles per phase, then the sum and max of CTA active cycles
+  PolicyParams pol;               // learned (tau, delta) (pol.active = 0: fixed)
 };
 
 // Non-negative doubles order like their bit patterns read as int64, so the
@@ -264,6 +268,12 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
   __shared__ double s_y[PB];
   __shared__ double s_sc[8];
   __shared__ int s_i[2];
+  __shared__ PolicyCarry s_pc;
+  __shared__ float s_feat[POL_NFEAT];
+  __shared__ int s_pcnt[8 * BW];
+  __shared__ float s_h[2 * POL_HIDDEN];
+  __shared__ double s_pout[2];
+  __shared__ double s_minb;
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   double* u = B.scratch + (int64_t)blockIdx.x * batched_scratch_doubles(B.nmax);
   double* uref = u + B.nmax;
@@ -293,6 +303,14 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
     if (qi >= B.count) break;
     const int32_t mi = B.order[qi];
     const BatchDesc D = B.desc[mi];
+    if (tid == 0) {
+      s_pc.prev_l = 0.0f;
+      s_pc.prev_k = 0.0f;
+      s_pc.cos_mean = 0.0f;
+      s_pc.cos_max = 0.0f;
+      s_pc.prev_tau = 0.0f;
+      s_pc.off = 0;
+    }
     double* A = D.A;
     const int64_t m = D.m, n = D.n, lda = D.lda, kmin = m < n ? m : n;
     // ---- a1: column norms, identity permutation, zero htau
@@ -354,9 +372,27 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
       }
       int kcap = dm_on ? B.kmax : 1;
       if (kcap > kmin - ns) kcap = (int)(kmin - ns);
+      // (tau_s, delta_s) of this step: fixed, or from the learned policy
+      double tau_s = B.tau, delta_s = B.delta;
+      bool learned = false;
+      if (B.pol.active && dm_on) {
+        pol_features<BT>(u, ns, n, jstar, mu, anorm, s_pc, s_feat, s_pcnt);
+        if (D.feat_log && step < D.log_cap && tid < POL_NFEAT) D.feat_log[step * POL_NFEAT + tid] = s_feat[tid];
+        if (B.pol.w && !s_pc.off) {
+          pol_mlp<BT>(B.pol, s_feat, s_h, s_pout);
+          tau_s = s_pout[0];
+          delta_s = s_pout[1];
+          learned = true;
+        }
+      }
+      if (D.act_log && step < D.log_cap && tid == 0) {
+        D.act_log[2 * step] = tau_s;
+        D.act_log[2 * step + 1] = delta_s;
+      }
+      if (tid == 0) s_minb = INFINITY;
       // candidate set (eq. def_candidate_set): the kcap-1 largest u_j >= tau mu,
       // j != j*, by (u desc, position asc) (readings R1, R2, R4)
-      const double thr = B.tau * mu;
+      const double thr = tau_s * mu;
       const long long thr_key = okey(thr);
       if (tid == 0) s_cols[0] = (int32_t)jstar;
       int nc = 0;
@@ -431,10 +467,29 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
         __syncthreads();
         // ---- a5: greedy DM pick (Alg. 1 loop), strict |theta| < delta (R5, R6)
         if (wp == 0) {
-          double dlt = B.delta;
+          double dlt = delta_s;
           if (B.sdd) {
-            const double dm = B.tau * B.tau / (double)((kc - 1) > 1 ? (kc - 1) : 1);
+            const double dm = tau_s * tau_s / (double)((kc - 1) > 1 ? (kc - 1) : 1);
             if (dm < dlt) dlt = dm;
+          }
+          if (B.pol.active) {
+            // |theta(j*, i)| statistics over the candidates (a feature of the next step)
+            double cs = 0.0, cm = 0.0;
+            for (int a = 1 + lane; a < kc; a += 32) {
+              const double rr = s_rd[0] * s_rd[a];
+              const double th = (rr > 0.0) ? fabs(s_g[tri(0, a)]) * rr : 1.0;
+              cs += th;
+              cm = fmax(cm, th);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              cs += __shfl_xor_sync(0xffffffffu, cs, o);
+              cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+            }
+            if (lane == 0) {
+              s_pc.cos_mean = (float)(cs / (double)(kc - 1));
+              s_pc.cos_max = (float)cm;
+            }
           }
           int kk = 1;
           if (lane == 0) s_J[0] = 0;
@@ -507,7 +562,7 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
           r->k = k;
           r->dm_on = dm_on;
           r->mu = mu;
-          r->eps_s = B.tau * mu;
+          r->eps_s = tau_s * mu;
           r->nrecomp = 0;
         }
         if (D.traceJ)
@@ -516,7 +571,11 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
       QRDM_BPHASE(BP_SWAP);
       // ---- a7/a8/a9: sub-panels of PB columns (Alg. 4 panel with its break
       //      test, R10, R11), each followed by its block reflector
-      const double eps_s = B.tau * mu;
+      const double eps_s = tau_s * mu;
+      if (B.pol.active && kc == 1 && tid == 0) {
+        s_pc.cos_mean = 0.0f;
+        s_pc.cos_max = 0.0f;
+      }
       int lacc = 0;
       bool broke = false;
       for (int jb = 0; jb < k && !broke; jb += PB) {
@@ -569,6 +628,7 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
             break;
           }
           const double beta = s_sc[0], ht = s_sc[1], rden = s_sc[2];
+          if (tid == 0) s_minb = fmin(s_minb, fabs(beta));
           // column l of T (forward columnwise compact WY): y_r = v_r^T v_l
           if (tid < l) s_y[tid] = s_tot[PB + tid] + s_tot[tid] * rden;
           __syncthreads();
@@ -668,6 +728,14 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
       nrec = __reduce_add_sync(0xffffffffu, nrec);
       if (D.trace && step < D.trace_cap && lane == 0 && nrec)
         atomicAdd((unsigned long long*)&D.trace[step].nrecomp, (unsigned long long)nrec);
+      if (B.pol.active && dm_on && tid == 0) {
+        // guard of the learned (tau, delta): a pivot below rho_min * mu turns
+        // the policy off for the rest of this matrix
+        if (learned && lacc > 0 && s_minb < B.pol.rho_min * mu) s_pc.off = 1;
+        s_pc.prev_l = (float)lacc;
+        s_pc.prev_k = (float)k;
+        s_pc.prev_tau = (float)tau_s;
+      }
       __syncthreads();
       QRDM_BPHASE(BP_DOWNDATE);
       ns = nsn;

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "qrdm_policy.cuh"
+
 namespace cg = cooperative_groups;
 
 namespace qrdm {
@@ -57,6 +59,11 @@ struct alignas(128) DevState {
   int64_t diag_step;
   int64_t diag_ns;
   int64_t diag_value;
+  // learned (tau, delta): the values of the current step and the carry
+  double tau_s, delta_s;
+  double pol_minb;     // smallest accepted |R_ii| of the current step
+  PolicyCarry pc;
+  int32_t pol_learned; // 1: the current step used the MLP's (tau, delta)
 };
 
 struct StepRecord {  // layout of qrdm_step_record
@@ -91,6 +98,7 @@ struct Params {
   StepRecord* trace;
   int32_t* traceJ;
   int64_t trace_cap;
+  PolicyParams pol;  // learned (tau, delta) and feature logging (pol.active = 0: off)
 };
 
 // kernel ids (same numbering as QRDM_K_* in the C header)
@@ -342,12 +350,12 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
       } else {
         st->mu = mu;
         st->jstar = jstar;
-        st->eps_s = P.tau * mu;
         int64_t kcap = st->dm_on ? P.kmax : 1;
         if (kcap > P.kmin - ns) kcap = P.kmin - ns;
         s_ctl[2] = (int)kcap;
-        s_ctld[0] = P.tau * mu;
+        s_ctl[3] = st->dm_on;
         s_ctld[1] = mu;
+        s_ctld[2] = anorm;
         const int64_t rec = st->step;
         if (P.trace && rec < P.trace_cap) {
           StepRecord* r = P.trace + rec;
@@ -355,7 +363,6 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
           r->jstar = jstar;
           r->dm_on = st->dm_on;
           r->mu = mu;
-          r->eps_s = P.tau * mu;
           r->nrecomp = 0;
         }
         P.cols[0] = (int32_t)jstar;
@@ -368,6 +375,46 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
   if (s_ctl[1]) return;
   const int64_t jstar = s_p[0];
   const int K = s_ctl[2] - 1;  // candidates to keep
+  {
+    // (tau_s, delta_s) of this step: fixed, or from the learned policy
+    __shared__ float s_feat[POL_NFEAT];
+    __shared__ int s_pcnt[8 * (SEL_THREADS / 32)];
+    __shared__ float s_h[2 * POL_HIDDEN];
+    __shared__ double s_pout[2];
+    const double mu = s_ctld[1];
+    if (tid == 0) {
+      s_pout[0] = P.tau;
+      s_pout[1] = P.delta;
+    }
+    int learned = 0;
+    if (P.pol.active && s_ctl[3]) {
+      const PolicyCarry pc = st->pc;
+      pol_features<SEL_THREADS>(P.u, ns, n, jstar, mu, s_ctld[2], pc, s_feat, s_pcnt);
+      const int64_t rec = st->step;
+      if (P.pol.feat_log && rec < P.pol.log_cap && tid < POL_NFEAT) P.pol.feat_log[rec * POL_NFEAT + tid] = s_feat[tid];
+      if (P.pol.w && !pc.off) {
+        pol_mlp<SEL_THREADS>(P.pol, s_feat, s_h, s_pout);
+        learned = 1;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double tau_s = s_pout[0], delta_s = s_pout[1];
+      st->tau_s = tau_s;
+      st->delta_s = delta_s;
+      st->pol_learned = learned;
+      st->pol_minb = INFINITY;
+      st->eps_s = tau_s * mu;
+      s_ctld[0] = tau_s * mu;
+      const int64_t rec = st->step;
+      if (P.trace && rec < P.trace_cap) P.trace[rec].eps_s = tau_s * mu;
+      if (P.pol.act_log && rec < P.pol.log_cap) {
+        P.pol.act_log[2 * rec] = tau_s;
+        P.pol.act_log[2 * rec + 1] = delta_s;
+      }
+    }
+    __syncthreads();
+  }
   const double thr = s_ctld[0];
 
   // count candidates
@@ -597,10 +644,30 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
   }
   __syncthreads();
   if (tid < 32) {
-    double dlt = P.delta;
+    const double tau_s = st->tau_s;
+    double dlt = st->delta_s;
     if (P.sdd && kc > 1) {
-      double dm = P.tau * P.tau / (double)((kc - 1) > 1 ? (kc - 1) : 1);
+      double dm = tau_s * tau_s / (double)((kc - 1) > 1 ? (kc - 1) : 1);
       if (dm < dlt) dlt = dm;
+    }
+    if (P.pol.active) {
+      // |theta(j*, i)| statistics over the candidates (a feature of the next step)
+      double cs = 0.0, cm = 0.0;
+      for (int a = 1 + lane; a < kc; a += 32) {
+        const double rr = s_d[0] * s_d[a];
+        const double th = (rr > 0.0) ? fabs(s_g[tri(0, a)]) * rr : 1.0;
+        cs += th;
+        cm = fmax(cm, th);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+      }
+      if (lane == 0) {
+        st->pc.cos_mean = (kc > 1) ? (float)(cs / (double)(kc - 1)) : 0.0f;
+        st->pc.cos_max = (float)cm;
+      }
     }
     // greedy DM pick (Alg. 1 loop): candidates in order, accept when
     // |theta(a, b)| = |G_ab| / (||c_a|| ||c_b||) < delta for every accepted b
@@ -816,6 +883,7 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
   int lacc = w;
   bool broke = false;
   double flops = 0.0;
+  double minb = INFINITY;  // smallest accepted |R_ii| (the learned policy's guard)
   for (int l = 0; l < w; ++l) {
     const int64_t p = r0 + l;  // pivot row and column
     double* slot = s_slot[l & 1];
@@ -879,6 +947,7 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
       break;
     }
     const double beta = s_sc[0], ht = s_sc[1], rden = s_sc[2];
+    minb = fmin(minb, fabs(beta));
     // compact-WY T_j column l (rank-0 CTA): y_t = v_t^T v_l for t < l
     if (crank == 0) {
       if (tid < l) s_y[tid] = s_tot[PB + tid] + s_tot[tid] * rden;
@@ -925,6 +994,7 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
     if (tid == 0) {
       st->cur_lj = lacc;
       st->l += lacc;
+      if (lacc > 0) st->pol_minb = fmin(st->pol_minb, minb);
       if (broke) st->pbreak = 1;
       if (P.trace && st->step < P.trace_cap) P.trace[st->step].l = st->l;
       add_flops(st, KID_PANEL, flops);
@@ -1770,6 +1840,14 @@ out:
 __global__ void k_step_end(Params P) {
   DevState* st = P.st;
   if (st->done) return;
+  if (P.pol.active && st->dm_on) {
+    // guard of the learned (tau, delta): a pivot below rho_min * mu turns the
+    // policy off for the rest of the factorization
+    if (st->pol_learned && st->l > 0 && st->pol_minb < P.pol.rho_min * st->mu) st->pc.off = 1;
+    st->pc.prev_l = (float)st->l;
+    st->pc.prev_k = (float)st->k;
+    st->pc.prev_tau = (float)st->tau_s;
+  }
   st->ns += st->l;
   st->step += 1;
 }
@@ -1798,6 +1876,16 @@ __global__ void k_state_init(Params P) {
   st->diag_step = -1;
   st->diag_ns = -1;
   st->diag_value = 0;
+  st->tau_s = P.tau;
+  st->delta_s = P.delta;
+  st->pol_minb = INFINITY;
+  st->pc.prev_l = 0.0f;
+  st->pc.prev_k = 0.0f;
+  st->pc.cos_mean = 0.0f;
+  st->pc.cos_max = 0.0f;
+  st->pc.prev_tau = 0.0f;
+  st->pc.off = 0;
+  st->pol_learned = 0;
 }
 
 }  // namespace qrdm

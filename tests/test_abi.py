@@ -16,7 +16,7 @@ HEADER = os.path.join(ROOT, "include", "qrdm.h")
 def declared_functions() -> list[str]:
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(qrdm_[a-z_]+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(qrdm_[a-z_0-9]+)\s*\(", src, flags=re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -46,7 +46,8 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layouts():
     from paper_2106_03138_gb300 import _binding
 
-    assert ctypes.sizeof(_binding.qrdm_opts) == 40
+    assert ctypes.sizeof(_binding.qrdm_opts) == 48
+    assert ctypes.sizeof(_binding.qrdm_policy) == 72
     assert ctypes.sizeof(_binding.qrdm_info) == 40
     assert ctypes.sizeof(_binding.qrdm_profile) == 16 * 8 * 3
     assert ctypes.sizeof(_binding.qrdm_step_record) == 80
@@ -93,7 +94,7 @@ def test_workspace_size_and_argument_checks(lib):
 def test_batched_struct_layouts():
     from paper_2106_03138_gb300 import _binding
 
-    assert ctypes.sizeof(_binding.qrdm_batch_matrix) == 72
+    assert ctypes.sizeof(_binding.qrdm_batch_matrix) == 96
     assert ctypes.sizeof(_binding.qrdm_batch_tuning) == 16
 
 
@@ -101,7 +102,7 @@ def test_batched_argument_checks(lib):
     from paper_2106_03138_gb300 import _binding as b
 
     fake = 1 << 20  # never dereferenced
-    good = b.qrdm_batch_matrix(fake, 8, 4, 8, fake, fake, None, None, 0)
+    good = b.qrdm_batch_matrix(fake, 8, 4, 8, fake, fake, None, None, 0, None, None, 0)
     # invalid arguments are rejected before any CUDA call
     h = ctypes.c_void_p(0)
     arr = (b.qrdm_batch_matrix * 1)(good)
@@ -115,7 +116,8 @@ def test_batched_argument_checks(lib):
                 b.qrdm_batch_matrix(None, 8, 4, 8, fake, fake, None, None, 0),        # no A
                 b.qrdm_batch_matrix(fake, 8, 4, 8, None, fake, None, None, 0),        # no htau
                 b.qrdm_batch_matrix(fake, 8, 4, 8, fake, None, None, None, 0),        # no perm
-                b.qrdm_batch_matrix(fake, 8, 4, 8, fake, fake, None, None, 3)):       # trace_cap, no trace
+                b.qrdm_batch_matrix(fake, 8, 4, 8, fake, fake, None, None, 3, None, None, 0),  # trace_cap, no trace
+                b.qrdm_batch_matrix(fake, 8, 4, 8, fake, fake, None, None, 0, None, None, -1)):  # log_cap < 0
         arr2 = (b.qrdm_batch_matrix * 2)(good, bad)
         assert lib.qrdm_batch_plan_create(2, arr2, 4, ctypes.byref(h)) == -2
     # a NULL plan is refused by every call; destroying it is a no-op
@@ -130,3 +132,29 @@ def test_batched_argument_checks(lib):
     assert lib.qrdm_batch_set_tuning(None, ctypes.byref(t)) == -1
     assert lib.qrdm_batch_autotune(None, 0.5, 0.5, None, None, None, None) == -1
     lib.qrdm_batch_plan_destroy(None)
+
+
+def test_policy_and_mlp_argument_checks(lib):
+    from paper_2106_03138_gb300 import _binding as b
+
+    fake = 1 << 20  # never dereferenced
+    pol = b.qrdm_policy(None, None, None, 0, 0.1, 1.0, 0.5, 1.0, 0.05)
+    for field, bad in (("tau_lo", 0.0), ("tau_hi", 1.5), ("delta_lo", -0.1), ("rho_min", -1.0), ("log_cap", -3)):
+        p = b.qrdm_policy.from_buffer_copy(pol)
+        setattr(p, field, bad)
+        o = b.qrdm_opts()
+        o.policy = ctypes.pointer(p)
+        rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 4, fake, fake, o, fake, 1 << 30, 0)
+        assert rc == -11, field
+    assert b.qrdm_mlp_workspace_size(64) > 0
+    with pytest.raises(ValueError):
+        b.qrdm_mlp_workspace_size(0)
+    assert lib.qrdm_mlp_init(None, fake, 1, None) == -1
+    assert lib.qrdm_mlp_init(fake, None, 1, None) == -2
+    assert lib.qrdm_mlp_forward(fake, fake, 0, fake, fake, 1 << 30, None) == -3
+    assert lib.qrdm_mlp_forward(fake, fake, 4, fake, fake, 16, None) == b.QRDM_ERR_WORKSPACE
+    assert lib.qrdm_mlp_loss_grad(fake, fake, None, 4, fake, fake, fake, 1 << 30, None) == -3
+    assert lib.qrdm_mlp_adam_step(fake, fake, fake, fake, fake, 0, 1e-3, 0.9, 0.999, 1e-8, 0.0, None) == -6
+    assert lib.qrdm_mlp_adam_step(fake, fake, fake, fake, fake, 1, 1e-3, 1.0, 0.999, 1e-8, 0.0, None) == -8
+    assert lib.qrdm_mlp_train(fake, fake, fake, fake, fake, 0, 4, 1, 1e-3, 0.0, 1, None, fake, 1 << 30, None) == -6
+    assert lib.qrdm_mlp_train(fake, fake, fake, fake, fake, 10, 4, 1, -1.0, 0.0, 1, None, fake, 1 << 30, None) == -9
