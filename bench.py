@@ -218,7 +218,7 @@ def run_profile_case(name: str, max_steps: int, precision: int = 0) -> int:
         # the tuning the autotuner picks on the full batch
         count = int(name[len("batch"):])
         ents = inputs.batch_entries(2000, seed=0)[:count]
-        mats = [e.build_gpu() for e in ents]
+        mats = [q.colmajor(e.build()) for e in ents]  # host-built: no library linear algebra under a profiler
         plan = q.BatchPlan(mats, KMAX)
         plan.set_tuning(2, 512, 4)
         plan.run(TAU, DELTA)
@@ -377,6 +377,85 @@ def measure_c4(q, inputs, torch, stream, fp64_peak_tflops: float, count: int = 2
     return out
 
 
+def measure_c5(q, torch, stream, n_train: int = 150, n_held: int = 60, big: int = 4096) -> dict:
+    """The learned per-step (tau, delta): plain-QRDM (tau, delta) sweeps of
+    generated training matrices label the steps, the MLP is trained by the
+    library's kernels, then held-out matrices are factored with the policy
+    and with fixed (0.9, 0.9) (and the paper's (0.15, 0.9) for context):
+    block steps, time and rank quality."""
+    import numpy as np
+
+    from paper_2106_03138_gb300 import inputs
+    from paper_2106_03138_gb300 import policy as P
+
+    out = {"grid_tau": list(P.GRID_TAU), "grid_delta": list(P.GRID_DELTA), "rho_min": P.RHO_MIN,
+           "tau_range": list(P.TAU_RANGE), "delta_range": list(P.DELTA_RANGE)}
+    t0 = time.perf_counter()
+    train = P.training_entries(n_train, seed=21, n_lo=64, n_hi=512)
+    pristine = [e.build_gpu() for e in train]
+    X, T, info = P.collect(train, pristine)
+    t1 = time.perf_counter()
+    pol = P.Policy(seed=2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    loss = pol.train(X, T, steps=2000, batch=1024, lr=2e-3)
+    e1.record()
+    e1.synchronize()
+    out["training"] = {"matrices": n_train, "n_range": [64, 512], "samples": int(X.shape[0]),
+                       "label_counts": info["label_counts"], "sweep_and_label_s": t1 - t0,
+                       "train_steps": 2000, "batch": 1024, "train_ms": e0.elapsed_time(e1),
+                       "loss_first50": float(loss[:50].mean()), "loss_last50": float(loss[-50:].mean())}
+    del pristine
+    held = P.training_entries(n_held, seed=99, n_lo=64, n_hi=512)
+    hp = [e.build_gpu() for e in held]
+    runs = {"fixed_0.9_0.9": P.run_batch(hp, held, 0.9, 0.9), "fixed_0.15_0.9": P.run_batch(hp, held, 0.15, 0.9),
+            "learned": P.run_batch(hp, held, 0.9, 0.9, policy=pol)}
+    ref = runs["fixed_0.9_0.9"]
+    flops = sum(metric_flops(e.n, e.n) for e in held)
+    bat = {}
+    for k, r in runs.items():
+        ratio = r.quality / np.maximum(ref.quality, 1e-300)
+        bat[k] = {"block_steps": int(r.steps.sum()), "kernel_ms": r.ms, "GFLOP/s": flops / r.ms / 1e6,
+                  "quality_ratio_vs_fixed_0.9_min": float(ratio.min()),
+                  "quality_ratio_vs_fixed_0.9_median": float(np.median(ratio)),
+                  "within_2x": float(np.mean(ratio >= 0.5))}
+    out["held_out_batch"] = {"matrices": n_held, "n_range": [64, 512], "batched_kernel": bat}
+    del hp
+    # one held-out large matrix through the single-matrix path
+    n = big
+    r = 3 * n // 4
+    sig = inputs.sigma_rank_geometric(n, r)
+    A0 = inputs.from_spectrum_gpu(n, n, sig, 1000)
+    ws = torch.empty(q.qrdm_workspace_size(n, n, KMAX), dtype=torch.uint8, device=A0.device)
+    single = {}
+    for key, kw in (("fixed_0.9_0.9", {}), ("learned", {"policy": pol.struct()})):
+        for rep in range(2):
+            dA = A0.clone()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            f = q.factor(dA, 0.9, 0.9, KMAX, workspace=ws, stream=stream, **kw)
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        R11 = torch.triu(dA[:r, :r])
+        smin = float(torch.linalg.svdvals(R11)[-1].item())
+        d = torch.diagonal(dA)[:r].abs().cpu().numpy()
+        single[key] = {"ms": ms, "GFLOP/s": metric_flops(n, n) / ms / 1e6, "block_steps": f.nsteps,
+                       "rank": f.rank, "rank_colmax": f.rank_colmax, "sigma_min_R11_over_sigma_r": smin / sig[r - 1],
+                       "min_Rii_over_sigma_i": float(np.min(d / sig[:r]))}
+        del dA, R11
+    single["speedup"] = single["fixed_0.9_0.9"]["ms"] / single["learned"]["ms"]
+    single["quality_ratio"] = (single["learned"]["sigma_min_R11_over_sigma_r"] /
+                               single["fixed_0.9_0.9"]["sigma_min_R11_over_sigma_r"])
+    out["held_out_single"] = {"matrix": f"{n}x{n}, sigma geometric 1->1e-12 over {r} values then 1e-15, seed 1000",
+                              "k_max": KMAX, **single}
+    del A0, ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def config_dict(world: int) -> dict:
     return {"workload": WORKLOAD_DESC, "matrices": list(WORKLOAD), "tau": TAU, "delta": DELTA, "k_max": KMAX,
             "global_batch": 3 * world, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -393,6 +472,7 @@ def main() -> int:
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-c3", action="store_true", help="skip the 16384^2 mixed-precision measurement")
     ap.add_argument("--no-c4", action="store_true", help="skip the 2000-matrix batched measurement")
+    ap.add_argument("--no-c5", action="store_true", help="skip the learned (tau, delta) training and evaluation")
     ap.add_argument("--profile-case", default=None,
                     help="factor one named matrix once at the benchmark's parameters and exit (profiler target)")
     ap.add_argument("--max-steps", type=int, default=0, help="with --profile-case: stop after this many block steps")
@@ -556,6 +636,10 @@ def main() -> int:
     if rank == 0 and not args.no_c4:
         c4 = measure_c4(q, inputs, torch, stream, peak)
 
+    c5 = None
+    if rank == 0 and not args.no_c5:
+        c5 = measure_c5(q, torch, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         secs, fl = time_oracle_sample(cpu_sample_matrices())
@@ -572,7 +656,7 @@ def main() -> int:
             "config": config_dict(world), "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": csum, "gpu_launches": launches, "wall_s": t_wall, "per_matrix": per,
-            "comparators": comparators, "mixed_precision_c3": c3, "batched_c4": c4,
+            "comparators": comparators, "mixed_precision_c3": c3, "batched_c4": c4, "learned_c5": c5,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

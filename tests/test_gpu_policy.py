@@ -142,10 +142,14 @@ def test_logged_features_match_the_oracles_partial_norms():
     for s in range(min(len(tr), 8)):
         if tr["dm_on"][s] != 1:
             break
-        o = O.qrdm(A, 0.9, 0.9, 32, schedule=acts, max_steps=s)
-        if o["nsteps"] != s or int(o["trace"]["ns"][-1] + o["trace"]["l"][-1] if s else 0) != int(tr["ns"][s]):
-            break  # the two sides diverged (a tie); stop comparing
-        u = o["u"]
+        if s == 0:
+            u = np.linalg.norm(A, axis=0)
+        else:
+            # the oracle's partial norms at the start of step s
+            o = O.qrdm(A, 0.9, 0.9, 32, schedule=acts, max_steps=s)
+            if o["nsteps"] != s or int(o["trace"]["ns"][-1] + o["trace"]["l"][-1]) != int(tr["ns"][s]):
+                break  # the two sides diverged (a tie); stop comparing
+            u = o["u"]
         ns = int(tr["ns"][s])
         jstar = ns + int(np.argmax(u[ns:]))
         prev_l = float(tr["l"][s - 1]) if s else 0.0
@@ -181,8 +185,10 @@ def test_guard_turns_the_policy_off():
     compare(A, g, o)
     # with rho_min = 0 the policy is never switched off
     pol0 = _policy_with(w32, rho_min=0.0)
-    _, _, acts0 = _factor_with_policy(A, pol0, tau=0.9, delta=0.9)
-    assert np.all(np.abs(acts0[dm, 0] - P.TAU_RANGE[0]) < 1e-6)
+    g0, _, acts0 = _factor_with_policy(A, pol0, tau=0.9, delta=0.9)
+    dm0 = np.nonzero(g0["trace"]["dm_on"] == 1)[0]
+    assert np.all(np.abs(acts0[dm0, 0] - P.TAU_RANGE[0]) < 1e-6)
+    assert len(acts0) < len(acts)  # the smallest tau all along takes fewer, larger blocks
 
 
 def test_batched_learned_matches_oracle_replay():
