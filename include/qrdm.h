@@ -122,10 +122,12 @@ typedef struct qrdm_opts {
  * tau_s = tau_lo + (tau_hi - tau_lo) sigmoid(o_0), delta_s likewise from o_1.
  * Weights: QRDM_POLICY_NPARAM bf16 values, row-major W1[16][64], b1[64],
  * W2[64][64], b2[64], W3[64][2], b3[2] (qrdm_mlp_* train them).
- * Guard: when a step that used the MLP accepts a pivot with
- * |R_ii| < rho_min * mu, the policy is switched off and the fixed (tau, delta)
- * of the call finish the factorization.  Single-column steps (after the
- * stopping criterion) ignore the policy.
+ * Guard (a check of the column-pivoting order): at the start of each DM step,
+ * if the previous step used the MLP and accepted a pivot |R_ii| smaller than
+ * rho_min times the largest partial norm now left (mu of this step), the
+ * policy is switched off and the fixed (tau, delta) of the call finish the
+ * factorization.  Single-column steps (after the stopping criterion) ignore
+ * the policy.
  * With d_weights == NULL nothing is predicted: tau and delta stay fixed and
  * only the logs are written (training data from plain runs).
  */

@@ -310,6 +310,8 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
       s_pc.cos_max = 0.0f;
       s_pc.prev_tau = 0.0f;
       s_pc.off = 0;
+      s_pc.prev_learned = 0;
+      s_pc.prev_minb = INFINITY;
     }
     double* A = D.A;
     const int64_t m = D.m, n = D.n, lda = D.lda, kmin = m < n ? m : n;
@@ -376,6 +378,9 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
       double tau_s = B.tau, delta_s = B.delta;
       bool learned = false;
       if (B.pol.active && dm_on) {
+        // guard: every pivot the previous (learned) step accepted must be at
+        // least rho_min times the largest partial norm left after it
+        if (tid == 0 && s_pc.prev_learned && s_pc.prev_minb < B.pol.rho_min * mu) s_pc.off = 1;
         pol_features<BT>(u, ns, n, jstar, mu, anorm, s_pc, s_feat, s_pcnt);
         if (D.feat_log && step < D.log_cap && tid < POL_NFEAT) D.feat_log[step * POL_NFEAT + tid] = s_feat[tid];
         if (B.pol.w && !s_pc.off) {
@@ -729,9 +734,8 @@ __global__ void __launch_bounds__(BT, 2) k_batched(BatchParams B) {
       if (D.trace && step < D.trace_cap && lane == 0 && nrec)
         atomicAdd((unsigned long long*)&D.trace[step].nrecomp, (unsigned long long)nrec);
       if (B.pol.active && dm_on && tid == 0) {
-        // guard of the learned (tau, delta): a pivot below rho_min * mu turns
-        // the policy off for the rest of this matrix
-        if (learned && lacc > 0 && s_minb < B.pol.rho_min * mu) s_pc.off = 1;
+        s_pc.prev_learned = learned ? 1 : 0;
+        s_pc.prev_minb = s_minb;
         s_pc.prev_l = (float)lacc;
         s_pc.prev_k = (float)k;
         s_pc.prev_tau = (float)tau_s;

@@ -388,6 +388,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
     }
     int learned = 0;
     if (P.pol.active && s_ctl[3]) {
+      if (tid == 0 && st->pc.prev_learned && st->pc.prev_minb < P.pol.rho_min * mu) st->pc.off = 1;
+      __syncthreads();
       const PolicyCarry pc = st->pc;
       pol_features<SEL_THREADS>(P.u, ns, n, jstar, mu, s_ctld[2], pc, s_feat, s_pcnt);
       const int64_t rec = st->step;
@@ -1841,9 +1843,10 @@ __global__ void k_step_end(Params P) {
   DevState* st = P.st;
   if (st->done) return;
   if (P.pol.active && st->dm_on) {
-    // guard of the learned (tau, delta): a pivot below rho_min * mu turns the
-    // policy off for the rest of the factorization
-    if (st->pol_learned && st->l > 0 && st->pol_minb < P.pol.rho_min * st->mu) st->pc.off = 1;
+    // carry for the next step's features and for the guard of the learned
+    // (tau, delta), checked at the next step's start against its mu
+    st->pc.prev_learned = st->pol_learned;
+    st->pc.prev_minb = st->pol_minb;
     st->pc.prev_l = (float)st->l;
     st->pc.prev_k = (float)st->k;
     st->pc.prev_tau = (float)st->tau_s;
@@ -1885,6 +1888,8 @@ __global__ void k_state_init(Params P) {
   st->pc.cos_max = 0.0f;
   st->pc.prev_tau = 0.0f;
   st->pc.off = 0;
+  st->pc.prev_learned = 0;
+  st->pc.prev_minb = INFINITY;
   st->pol_learned = 0;
 }
 

@@ -44,7 +44,7 @@ struct PolicyParams {
   double* act_log;         // optional [cap][2] (tau_s, delta_s) used per step
   int64_t log_cap;
   double tau_lo, tau_hi, delta_lo, delta_hi;
-  double rho_min;          // guard: min |R_ii| / mu of a learned step
+  double rho_min;          // guard: accepted |R_ii| of a learned step >= rho_min * (largest partial norm after it)
   int32_t active;          // 1: a policy object was passed
   int32_t pad;
 };
@@ -52,7 +52,10 @@ struct PolicyParams {
 // Per-factorization memory of the previous step, carried between steps.
 struct PolicyCarry {
   float prev_l, prev_k, cos_mean, cos_max, prev_tau;
-  int32_t off;  // 1 once the guard fired: fixed (tau, delta) from then on
+  int32_t off;           // 1 once the guard fired: fixed (tau, delta) from then on
+  int32_t prev_learned;  // the previous step used the MLP's (tau, delta)
+  int32_t pad;
+  double prev_minb;      // smallest |R_ii| the previous step accepted
 };
 
 __device__ __forceinline__ long long pol_key(double x) { return __double_as_longlong(x); }

@@ -9,15 +9,16 @@ empirically (Sec. 5).  This module learns a per-step choice:
 * **Labels.** The factorization is split into four phases by n_s / min(m, n).
   For each matrix and phase the label is the grid point with the largest mean
   block size l in that phase among the points whose rank quality
-  q = min_{i<r} |R_ii| / sigma_i stays within a factor 2 of the fixed
-  (0.9, 0.9) run.  Every logged step of every run gets the label of its
-  matrix and phase.
+  sigma_min(R11) / sigma_r is at least QUALITY_FACTOR (0.9) times that of the
+  fixed (0.9, 0.9) run.  Every logged step of every run gets the label of its matrix and
+  phase.
 * **Training** runs the library's own kernels (qrdm_mlp_train: forward,
   backward and Adam on the GPU) on BF16 weights with FP32 accumulation.
 * **Use.** ``Policy.struct()`` is the qrdm_policy passed to ``factor`` or
   ``BatchPlan.run``.  The kernels predict (tau_s, delta_s) at every DM step,
   and a guard falls back to the fixed (tau, delta) for the rest of a
-  factorization when a step accepts a pivot below rho_min * mu.
+  factorization when a learned step accepted a pivot below rho_min times the
+  largest partial norm left after it (an approximate column-pivoting order).
 
 Argument marshalling and bookkeeping only; every numeric step runs in the
 library's kernels.
@@ -36,9 +37,10 @@ GRID_TAU = (0.1, 0.15, 0.25, 0.4, 0.6, 0.9)
 GRID_DELTA = (0.5, 0.7, 0.9)
 TAU_RANGE = (0.05, 1.0)
 DELTA_RANGE = (0.3, 1.0)
-RHO_MIN = 0.02
+RHO_MIN = 0.5
 REFERENCE = (0.9, 0.9)
 NPHASE = 4
+QUALITY_FACTOR = 0.9
 
 
 @dataclass(frozen=True)
@@ -174,6 +176,41 @@ class Policy:
         return loss[:steps].cpu().numpy()
 
 
+def smin_r11(mats, ranks, iters: int = 30, seed: int = 0) -> np.ndarray:
+    """sigma_min of each factored matrix's leading R11 (ranks[i] x ranks[i]),
+    by inverse power iteration on (R11^T R11)^{-1}: each iteration is two
+    triangular solves; the Rayleigh quotient after `iters` steps estimates
+    1 / sigma_min^2 from below.  The R11 are padded with identity blocks to
+    sizes that are multiples of 64 and solved in batches of equal size.
+    Evaluation of the training labels only (the factorization is done)."""
+    import torch
+
+    out = np.ones(len(mats))
+    groups = {}
+    for i, (A, r) in enumerate(zip(mats, ranks)):
+        if r > 0:
+            groups.setdefault(-(-int(r) // 64) * 64, []).append(i)
+    g = torch.Generator(device=mats[0].device if mats else "cpu")
+    g.manual_seed(seed)
+    for size, idx in groups.items():
+        R = torch.eye(size, dtype=torch.float64, device=mats[idx[0]].device).repeat(len(idx), 1, 1)
+        for b, i in enumerate(idx):
+            r = int(ranks[i])
+            R[b, :r, :r] = torch.triu(mats[i][:r, :r])
+        x = torch.randn((len(idx), size, 1), dtype=torch.float64, device=R.device, generator=g)
+        x = x / torch.linalg.vector_norm(x, dim=1, keepdim=True)
+        lam = None
+        for _ in range(iters):
+            y = torch.linalg.solve_triangular(R.transpose(1, 2), x, upper=False)
+            z = torch.linalg.solve_triangular(R, y, upper=True)
+            lam = (x * z).sum(dim=(1, 2))
+            x = z / torch.linalg.vector_norm(z, dim=1, keepdim=True)
+        sm = (1.0 / torch.sqrt(lam)).cpu().numpy()
+        for b, i in enumerate(idx):
+            out[i] = sm[b]
+    return out
+
+
 def _quality(A_fact, sigma: np.ndarray, r: int) -> float:
     """min_{i<r} |R_ii| / sigma_i of a factored matrix (device tensor)."""
     import torch
@@ -189,11 +226,12 @@ class SweepResult:
     tau: float
     delta: float
     steps: np.ndarray      # per matrix
-    quality: np.ndarray    # per matrix
+    quality: np.ndarray    # per matrix: min_{i<r} |R_ii| / sigma_i
     rank_colmax: np.ndarray
     ms: float
     traces: list = field(default_factory=list)  # per matrix: (ns, k, l, dm_on) arrays
     feats: list = field(default_factory=list)   # per matrix: (steps x 16) features
+    smin: np.ndarray | None = None              # per matrix: sigma_min(R11) / sigma_r
 
 
 def run_batch(pristine, entries, tau, delta, k_max=64, policy: Policy | None = None, logs=False, stream=None):
@@ -220,8 +258,11 @@ def run_batch(pristine, entries, tau, delta, k_max=64, policy: Policy | None = N
     e1.synchronize()
     res = plan.results()
     out = SweepResult(tau, delta, res.steps.copy(), np.zeros(len(work)), res.rank_colmax.copy(), e0.elapsed_time(e1))
+    qranks = [_quality_rank(e, int(res.rank_colmax[i])) for i, e in enumerate(entries)]
+    sm = smin_r11(work, qranks)
+    out.smin = np.array([sm[i] / e.sigma()[qranks[i] - 1] if qranks[i] > 0 else 1.0 for i, e in enumerate(entries)])
     for i, (A, e) in enumerate(zip(work, entries)):
-        out.quality[i] = _quality(A, e.sigma(), _quality_rank(e, int(res.rank_colmax[i])))
+        out.quality[i] = _quality(A, e.sigma(), qranks[i])
         if logs:
             tr, _ = plan.trace(i, res.steps[i])
             out.traces.append((tr["ns"].copy(), tr["k"].copy(), tr["l"].copy(), tr["dm_on"].copy()))
@@ -246,9 +287,12 @@ def _quality_rank(e, rank_colmax: int) -> int:
     return min(e.rank, rank_colmax) if e.kind != 1 else rank_colmax
 
 
-def collect(entries, pristine, k_max=64, stream=None) -> tuple[np.ndarray, np.ndarray, dict]:
-    """Sweep the (tau, delta) grid with plain QRDM and build (X, T).  Returns
-    (X, T, info) with T the normalized label (tau*, delta*)."""
+def collect(entries, pristine, k_max=64, stream=None, quality_factor: float = QUALITY_FACTOR
+            ) -> tuple[np.ndarray, np.ndarray, dict]:
+    """Sweep the (tau, delta) grid with plain QRDM and build (X, T).  A grid
+    point is admissible for a matrix when its sigma_min(R11) / sigma_r is at
+    least quality_factor times the fixed (0.9, 0.9) run's.  Returns (X, T,
+    info) with T the normalized label (tau*, delta*)."""
     sweeps = {}
     for tau in GRID_TAU:
         for delta in GRID_DELTA:
@@ -258,12 +302,12 @@ def collect(entries, pristine, k_max=64, stream=None) -> tuple[np.ndarray, np.nd
     label_hist = {}
     for i, e in enumerate(entries):
         kmin = e.n
-        qref = ref.quality[i]
+        qref = ref.smin[i]
         best = {}
         for q in range(NPHASE):
             cand = []
             for g, sw in sweeps.items():
-                if not (sw.quality[i] >= 0.5 * qref):
+                if not (sw.smin[i] >= quality_factor * qref):
                     continue
                 ns, k, l, dm = sw.traces[i]
                 ph = np.minimum((NPHASE * ns) // max(kmin, 1), NPHASE - 1)

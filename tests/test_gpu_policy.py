@@ -106,10 +106,11 @@ def _factor_with_policy(A, pol, tau=0.9, delta=0.9, kmax=32):
 
 
 def _random_policy(seed, tau_bias=0.0):
+    """Random weights, guard off (rho_min = 0): every DM step uses the MLP."""
     rng = np.random.default_rng(seed)
     w32 = (rng.standard_normal(M.NPARAM) * 0.15).astype(np.float32)
     w32[-2] += tau_bias
-    return _policy_with(w32), w32
+    return _policy_with(w32, rho_min=0.0), w32
 
 
 @pytest.mark.parametrize("seed,shape", [(1, (300, 220)), (2, (256, 256)), (3, (500, 130))])
@@ -165,22 +166,47 @@ def test_logged_features_match_the_oracles_partial_norms():
     assert checked >= 3
 
 
+def test_smin_estimate_matches_the_singular_values():
+    """The inverse power iteration used for label quality against the
+    library SVD of the same R11 blocks."""
+    rng = np.random.default_rng(8)
+    mats, ranks = [], []
+    for n, r in ((70, 50), (130, 128), (64, 1), (200, 150)):
+        A = inputs.from_spectrum(n, n, inputs.sigma_geometric(n, 1e-8), int(rng.integers(1000)))
+        Rq = np.linalg.qr(A, mode="r")
+        mats.append(torch.as_tensor(np.asfortranarray(Rq), device="cuda"))
+        ranks.append(r)
+    est = P.smin_r11(mats, ranks, iters=60)
+    for M_, r, e in zip(mats, ranks, est):
+        exact = np.linalg.svd(np.triu(M_[:r, :r].cpu().numpy()), compute_uv=False)[-1]
+        assert e == pytest.approx(exact, rel=0.05), (r, e, exact)
+
+
 def test_guard_turns_the_policy_off():
     A = inputs.from_spectrum(300, 300, inputs.sigma_geometric(300, 1e-15), 11)
     rng = np.random.default_rng(5)
     w32 = (rng.standard_normal(M.NPARAM) * 0.01).astype(np.float32)
     w32[-2] = -30.0  # tau_s -> tau_lo for every step
-    pol = _policy_with(w32, rho_min=0.5)
+    rho = 0.9
+    pol = _policy_with(w32, rho_min=rho)
     g, feats, acts = _factor_with_policy(A, pol, tau=0.9, delta=0.9)
-    dm = np.nonzero(g["trace"]["dm_on"] == 1)[0]
-    first = acts[dm[0]]
-    assert first[0] == pytest.approx(P.TAU_RANGE[0], abs=1e-6)
-    # some later DM step runs with the fixed (0.9, 0.9) again
+    tr = g["trace"]
+    dm = np.nonzero(tr["dm_on"] == 1)[0]
+    assert acts[dm[0], 0] == pytest.approx(P.TAU_RANGE[0], abs=1e-6)
+    # some later DM step runs with the fixed (0.9, 0.9) again, and all after it
     fixed = np.nonzero((acts[dm, 0] == 0.9) & (acts[dm, 1] == 0.9))[0]
     assert fixed.size > 0
-    k = fixed[0]
-    assert np.all(acts[dm[k:], 0] == 0.9)
-    # the step before the switch accepted a pivot below rho_min * mu
+    k = int(fixed[0])
+    assert k >= 1 and np.all(acts[dm[k:], 0] == 0.9)
+    # the switch follows the first learned step whose smallest accepted pivot
+    # |R_ii| is below rho times the largest partial norm left after it (the
+    # next step's mu); every earlier learned step stayed above that bound
+    d = np.abs(np.diag(g["A"]))
+    for j in range(k):
+        s = int(dm[j])
+        mb = d[int(tr["ns"][s]):int(tr["ns"][s] + tr["l"][s])].min()
+        bound = rho * float(tr["mu"][s + 1])
+        assert (mb < bound) if j == k - 1 else (mb >= bound), (j, k, mb, bound)
     o = O.qrdm(A, 0.9, 0.9, 32, schedule=acts)
     compare(A, g, o)
     # with rho_min = 0 the policy is never switched off
@@ -214,7 +240,7 @@ def test_batched_learned_matches_oracle_replay():
 def test_trained_policy_gains_over_fixed_tau_delta():
     """Train on plain-QRDM sweeps of small generated matrices, then factor
     held-out matrices: fewer block steps than fixed (0.9, 0.9) at rank quality
-    within a factor 2 (q = min_{i<r} |R_ii| / sigma_i)."""
+    sigma_min(R11) / sigma_r within a factor 2."""
     train = P.training_entries(150, seed=21, n_lo=64, n_hi=320)
     pristine = [e.build_gpu() for e in train]
     X, T, info = P.collect(train, pristine)
@@ -226,7 +252,7 @@ def test_trained_policy_gains_over_fixed_tau_delta():
     hp = [e.build_gpu() for e in held]
     fixed = P.run_batch(hp, held, 0.9, 0.9)
     learned = P.run_batch(hp, held, 0.9, 0.9, policy=pol)
-    ratio = learned.quality / np.maximum(fixed.quality, 1e-300)
+    ratio = learned.smin / np.maximum(fixed.smin, 1e-300)
     print(f"\n[policy] samples {X.shape[0]}, labels {info['label_counts']}; held-out steps: fixed "
           f"{fixed.steps.sum()}, learned {learned.steps.sum()}; quality ratio min {ratio.min():.3f} "
           f"median {np.median(ratio):.3f}; kernel ms fixed {fixed.ms:.1f} learned {learned.ms:.1f}")
