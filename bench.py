@@ -265,6 +265,23 @@ def measure_c3(q, inputs, torch, stream) -> dict:
         ratio = d / sig[:r]
         out[key] = {"ms": ms, "GFLOP/s": flops / ms / 1e6, "rank": f.rank, "rank_colmax": f.rank_colmax,
                     "steps": f.nsteps, "d_over_sigma_min": float(ratio.min()), "d_over_sigma_max": float(ratio.max())}
+        if prec == 1:
+            # least squares on the mixed factorization, refined in FP64 on the
+            # original matrix: a compatible right-hand side b = A x0
+            g = torch.Generator(device=A0.device)
+            g.manual_seed(7)
+            x0 = torch.randn(n, dtype=torch.float64, device=A0.device, generator=g)
+            b = A0 @ x0
+            torch.cuda.synchronize()
+            e0.record(stream)
+            x, res = q.ls_solve(A0, f, b, rank=r, refine=3, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            nb = float(torch.linalg.vector_norm(b))
+            out["ls_refinement"] = {"rank_used": r, "refine_iters": 3, "ms_incl_residual_norms": e0.elapsed_time(e1),
+                                    "residual_over_b": [float(v) / nb for v in res[:, 0]],
+                                    "rhs": "b = A x0, x0 ~ N(0,1) (seed 7, torch CUDA generator)"}
+            del x, b, x0
         del dA
     out["speedup"] = out["fp64"]["ms"] / out["mixed_fp32"]["ms"]
     del A0, ws

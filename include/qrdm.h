@@ -373,6 +373,34 @@ int qrdm_mlp_train(float* d_w32, void* d_w16, float* d_adam, const float* d_x, c
                    int64_t batch, int64_t steps, float lr, float weight_decay, uint64_t seed, float* d_loss_log,
                    float* d_work, size_t work_bytes, void* stream);
 
+/*
+ * Least squares with a QRDM factorization (the paper stops at the
+ * factorization; the solve is this library's).  With A Pi = Q R from
+ * qrdm_factor (dQR, d_htau, d_perm as it returned them) and a rank r (e.g.
+ * info.rank or rank_colmax), the basic solution of min ||A x - b|| is
+ *   x = Pi [R11^{-1} (Q^T b)_{1:r}; 0],
+ * Q^T b by the stored reflectors H_1..H_r, R11 the leading r x r block of R.
+ * refine > 0 iterations of FP64 refinement use the original matrix dA
+ * (unchanged copy, FP64): r_k = b - A x_k, x_{k+1} = x_k + basic(r_k).  This
+ * recovers FP64 accuracy from a factorization computed in reduced precision
+ * (opts.precision = 1) when the system is compatible (b in the range of A)
+ * or its residual is small; for other systems the fixed point satisfies
+ * Q1^T (b - A x) = 0 with the computed Q1.
+ * Arguments: dA/lda (may be NULL when refine = 0), dQR/ldqr, m, n, d_htau,
+ * d_perm, rank, dB/ldb (m x nrhs, read only), dX/ldx (n x nrhs, written),
+ * refine (0..100); h_resid (host, optional): (refine + 1) x nrhs residual
+ * 2-norms ||b - A x_k|| per column, before each correction and after the
+ * last (needs dA; synchronizes the stream per iteration).  Device workspace
+ * of qrdm_ls_workspace_size bytes, 16-byte aligned.  m <= 24576 (a column of
+ * b is kept in shared memory).
+ * Errors: -i for an invalid i-th argument, QRDM_ERR_WORKSPACE, QRDM_ERR_CUDA.
+ */
+int qrdm_ls_workspace_size(int64_t m, int64_t n, int64_t rank, int64_t nrhs, size_t* bytes);
+int qrdm_ls_solve(const double* dA, int64_t lda, const double* dQR, int64_t ldqr, int64_t m, int64_t n,
+                  const double* d_htau, const int32_t* d_perm, int64_t rank, const double* dB, int64_t ldb,
+                  int64_t nrhs, double* dX, int64_t ldx, int32_t refine, double* h_resid, void* d_work,
+                  size_t work_bytes, void* stream);
+
 /* Static description of an error code. */
 const char* qrdm_strerror(int code);
 

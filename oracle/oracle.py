@@ -184,3 +184,26 @@ def qrdm(A: np.ndarray, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *
         "nsteps": ns,
     }
 
+
+
+def ls_basic(A: np.ndarray, b: np.ndarray, rank: int | None = None, fact: dict | None = None, **qrdm_kwargs):
+    """Basic least-squares solution from the oracle's QRDM factorization:
+    x = Pi [R11^{-1} (Q^T b)_{1:r}; 0], Q^T b by the reflectors H_1..H_r
+    (H_j = I - htau_j v_j v_j^T, v_j(j) = 1, v_j below the diagonal of the
+    factored matrix), R11 the leading r x r block.  ``fact``: a result of
+    ``qrdm`` to reuse; ``rank`` defaults to its numerical rank."""
+    import scipy.linalg
+
+    A = np.asarray(A, dtype=np.float64)
+    f = fact if fact is not None else qrdm(A, **qrdm_kwargs)
+    F, htau, perm = f["A"], f["htau"], f["perm"]
+    m, n = A.shape
+    r = f["rank"] if rank is None else int(rank)
+    y = np.array(b, dtype=np.float64).reshape(m, -1).copy()
+    for j in range(r):
+        v = np.concatenate([[1.0], F[j + 1:, j]])
+        y[j:] -= htau[j] * np.outer(v, v @ y[j:])
+    z = scipy.linalg.solve_triangular(np.triu(F[:r, :r]), y[:r], lower=False)
+    x = np.zeros((n, y.shape[1]))
+    x[perm[:r]] = z
+    return x.reshape((n,) + np.shape(b)[1:])

@@ -143,3 +143,42 @@ def factor(A, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mod
         out.trace = np.frombuffer(tr.cpu().numpy().tobytes(), dtype=TRACE_DTYPE)[:ns].copy()
         out.J = trJ.cpu().numpy().reshape(cap, k_max)[:ns].copy()
     return out
+
+
+def ls_solve(A_orig, f: Factorization, b, rank: int | None = None, refine: int = 0, stream=None):
+    """Basic least-squares solution of min ||A x - b|| from a factorization
+    ``f`` of A (``factor``), with ``refine`` FP64 refinement iterations on the
+    original matrix ``A_orig`` (column-major float64 CUDA tensor, unchanged).
+    ``b``: CUDA float64 (m,) or (m, nrhs).  Returns (x, residual norms per
+    iteration as a numpy array (refine + 1, nrhs), or None without A_orig)."""
+    import ctypes
+
+    import torch
+
+    from . import _binding as _b
+
+    QR = f.A
+    m, n = QR.shape
+    r = f.rank if rank is None else int(rank)
+    vec = b.dim() == 1
+    B = (b[:, None] if vec else b).to(torch.float64)
+    B = B.t().contiguous().t() if B.shape[1] > 1 else B.contiguous()
+    nrhs = B.shape[1]
+    X = torch.zeros((nrhs, n), dtype=torch.float64, device=QR.device).t()
+    sz = ctypes.c_size_t(0)
+    rc = _b.load().qrdm_ls_workspace_size(m, n, r, nrhs, ctypes.byref(sz))
+    if rc != 0:
+        raise QRDMError(rc, "qrdm_ls_workspace_size")
+    ws = torch.empty(max(int(sz.value), 16), dtype=torch.uint8, device=QR.device)
+    resid = np.zeros((refine + 1, nrhs)) if A_orig is not None else None
+    s = stream if stream is not None else torch.cuda.current_stream(QR.device)
+    lda = A_orig.stride(1) if A_orig is not None and n > 1 else max(m, 1)
+    rc = _b.load().qrdm_ls_solve(A_orig.data_ptr() if A_orig is not None else None, lda, QR.data_ptr(),
+                                 QR.stride(1) if n > 1 else max(m, 1), m, n, f.htau.data_ptr(), f.perm.data_ptr(),
+                                 r, B.data_ptr(), B.stride(1) if nrhs > 1 else max(m, 1), nrhs, X.data_ptr(),
+                                 X.stride(1) if nrhs > 1 else max(n, 1), int(refine),
+                                 resid.ctypes.data if resid is not None else None, ws.data_ptr(), ws.numel(),
+                                 s.cuda_stream)
+    if rc != 0:
+        raise QRDMError(rc, "qrdm_ls_solve")
+    return (X[:, 0] if vec else X), resid

@@ -393,3 +393,31 @@ def test_no_break_mode_takes_whole_block():
     A = inputs.named("gap256").build()
     r = O.qrdm(A, 0.9, 0.9, 32, no_break=True)
     assert np.all(r["trace"]["l"] == r["trace"]["k"])
+
+
+def test_ls_basic_square_full_rank_is_the_linear_solve():
+    A = inputs.random_dense(60, 60, 3)
+    b = np.random.default_rng(4).standard_normal(60)
+    x = O.ls_basic(A, b, tau=0.5, delta=0.9, k_max=8)
+    ref = np.linalg.solve(A, b)
+    cond = np.linalg.cond(A)
+    assert np.linalg.norm(x - ref) <= 50 * cond * 2.0 ** -52 * np.linalg.norm(ref)
+
+
+def test_ls_basic_tall_full_rank_is_the_least_squares_solution():
+    A = inputs.random_dense(120, 40, 5)
+    B = np.random.default_rng(6).standard_normal((120, 3))
+    X = O.ls_basic(A, B, tau=0.15, delta=0.9, k_max=16)
+    ref = np.linalg.lstsq(A, B, rcond=None)[0]
+    np.testing.assert_allclose(X, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_ls_basic_rank_deficient_compatible_system_is_solved():
+    """A of rank 25 (sigma 1 then 1e-15), b = A x0: the basic solution with
+    r = 25 reproduces b to roundoff and has at most 25 nonzeros."""
+    A = inputs.from_spectrum(90, 70, inputs.sigma_gap(70, 25, lo=1e-15), 7)
+    x0 = np.random.default_rng(8).standard_normal(70)
+    b = A @ x0
+    x = O.ls_basic(A, b, rank=25, tau=0.9, delta=0.9, k_max=32)
+    assert np.count_nonzero(x) <= 25
+    assert np.linalg.norm(A @ x - b) <= 1e-12 * np.linalg.norm(b)
