@@ -647,6 +647,23 @@ def main() -> int:
             comparators[label] = {"matrix": WORKLOAD[0], "ms": msc, "GFLOP/s": metric_flops(m, n) / msc / 1e6,
                                   "steps": f.nsteps, "rank": f.rank}
             del wk
+        # blocked column pivoting with lazy updates (the xGEQP3 scheme), nb = 16
+        qws = None
+        for rep in range(2):
+            wk = pristine[0].clone()
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f = q.qp3_factor(wk, 16, workspace=qws, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+        msc = e0.elapsed_time(e1)
+        m, n = shapes[0]
+        comparators["qp3_lazy_nb16"] = {"matrix": WORKLOAD[0], "ms": msc, "GFLOP/s": metric_flops(m, n) / msc / 1e6,
+                                        "blocks": f.nsteps, "rank": f.rank}
+        del wk
 
     c3 = None
     if rank == 0 and not args.no_c3:

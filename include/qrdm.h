@@ -401,6 +401,29 @@ int qrdm_ls_solve(const double* dA, int64_t lda, const double* dQR, int64_t ldqr
                   int64_t nrhs, double* dX, int64_t ldx, int32_t refine, double* h_resid, void* d_work,
                   size_t work_bytes, void* stream);
 
+/*
+ * Comparator: blocked QR with column pivoting with lazy updates (the scheme
+ * of LAPACK's xGEQP3 / xLAQPS by Quintana-Orti, Sun and Bischof, which the
+ * paper measures QRDM against in Sec. 5), written for this GPU as one
+ * cooperative persistent kernel.  Pivots are the largest partial norm
+ * (ties to the lowest position), so the permutation is that of qrdm_factor
+ * with k_max = 1; the block size nb (1..32) only changes how the trailing
+ * update is applied (F accumulates nb columns, then one blocked update).
+ * A partial norm whose downdate cancels (t (vn1/vn2)^2 <= sqrt(eps)) ends
+ * the block early and is recomputed exactly after its update.
+ * Outputs as qrdm_factor (R and reflectors in dA, htau, 0-based int32
+ * permutation, info.rank / rank_colmax from the Sec. 3.4 criterion with
+ * eps1_mode, info.nsteps = blocks).  Workspace: qrdm_qp3_workspace_size
+ * bytes, 256-byte aligned.  Synchronizes the stream.
+ * Errors: -i for an invalid i-th argument, QRDM_ERR_WORKSPACE,
+ * QRDM_ERR_NONFINITE (A left unmodified), QRDM_ERR_UNSUPPORTED (no
+ * cooperative launch), QRDM_ERR_INTERNAL (a grid barrier wait gave up),
+ * QRDM_ERR_CUDA.
+ */
+int qrdm_qp3_workspace_size(int64_t m, int64_t n, int32_t nb, size_t* bytes);
+int qrdm_qp3_factor(double* dA, int64_t m, int64_t n, int64_t lda, int32_t nb, double* d_htau, int32_t* d_perm,
+                    qrdm_info* info, int32_t eps1_mode, void* d_work, size_t work_bytes, void* stream);
+
 /* Static description of an error code. */
 const char* qrdm_strerror(int code);
 

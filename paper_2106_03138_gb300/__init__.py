@@ -182,3 +182,39 @@ def ls_solve(A_orig, f: Factorization, b, rank: int | None = None, refine: int =
     if rc != 0:
         raise QRDMError(rc, "qrdm_ls_solve")
     return (X[:, 0] if vec else X), resid
+
+
+def qp3_factor(A, nb: int = 32, *, eps1_mode: int = 0, workspace=None, stream=None) -> Factorization:
+    """Comparator: blocked QR with column pivoting (lazy updates, block nb)
+    of the column-major float64 CUDA tensor A, in place (see
+    qrdm_qp3_factor in include/qrdm.h)."""
+    import ctypes
+
+    import torch
+
+    from . import _binding as _b
+
+    if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2):
+        raise ValueError("A must be a 2-D float64 CUDA tensor")
+    m, n = A.shape
+    if m * n and m > 1 and A.stride(0) != 1:
+        raise ValueError("A must be column-major (stride(0) == 1)")
+    lda = A.stride(1) if (n > 1 and m * n) else max(m, 1)
+    kmin = min(m, n)
+    htau = torch.empty(max(kmin, 1), dtype=torch.float64, device=A.device)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
+    sz = ctypes.c_size_t(0)
+    rc = _b.load().qrdm_qp3_workspace_size(m, n, nb, ctypes.byref(sz))
+    if rc != 0:
+        raise QRDMError(rc, "qrdm_qp3_workspace_size")
+    if workspace is None or workspace.numel() < sz.value:
+        workspace = torch.empty(max(int(sz.value), 256), dtype=torch.uint8, device=A.device)
+    info = qrdm_info()
+    s = stream if stream is not None else torch.cuda.current_stream(A.device)
+    rc = _b.load().qrdm_qp3_factor(A.data_ptr() if m * n else None, m, n, lda, nb, htau.data_ptr(), perm.data_ptr(),
+                                   ctypes.byref(info), int(eps1_mode), workspace.data_ptr(), workspace.numel(),
+                                   s.cuda_stream)
+    if rc != 0:
+        raise QRDMError(rc, "qrdm_qp3_factor")
+    return Factorization(A=A, htau=htau[:kmin], perm=perm[:n], rank=int(info.rank),
+                         rank_colmax=int(info.rank_colmax), nsteps=int(info.nsteps), launches=int(info.launches))

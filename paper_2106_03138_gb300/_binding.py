@@ -79,7 +79,8 @@ EXPORTS = ("qrdm_workspace_size", "qrdm_factor", "qrdm_factor_noalloc", "qrdm_st
            "qrdm_batch_bind", "qrdm_batch_get_tuning", "qrdm_batch_set_tuning", "qrdm_batch_autotune",
            "qrdm_factor_batched", "qrdm_factor_batched_graph", "qrdm_batch_results", "qrdm_mlp_workspace_size",
            "qrdm_mlp_init", "qrdm_mlp_to_bf16", "qrdm_mlp_forward", "qrdm_mlp_loss_grad", "qrdm_mlp_adam_step",
-           "qrdm_mlp_train", "qrdm_ls_workspace_size", "qrdm_ls_solve")
+           "qrdm_mlp_train", "qrdm_ls_workspace_size", "qrdm_ls_solve", "qrdm_qp3_workspace_size",
+           "qrdm_qp3_factor")
 QRDM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 _lock = threading.Lock()
@@ -150,6 +151,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             fn = getattr(lib, name)
             fn.restype = ctypes.c_int
             fn.argtypes = args
+        lib.qrdm_qp3_workspace_size.restype = ctypes.c_int
+        lib.qrdm_qp3_workspace_size.argtypes = [c_i64, c_i64, c_i32, P(c_sz)]
+        lib.qrdm_qp3_factor.restype = ctypes.c_int
+        lib.qrdm_qp3_factor.argtypes = [c_p, c_i64, c_i64, c_i64, c_i32, c_p, c_p, P(qrdm_info), c_i32, c_p, c_sz,
+                                        c_p]
         lib.qrdm_ls_workspace_size.restype = ctypes.c_int
         lib.qrdm_ls_workspace_size.argtypes = [c_i64, c_i64, c_i64, c_i64, P(c_sz)]
         lib.qrdm_ls_solve.restype = ctypes.c_int
