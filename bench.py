@@ -236,11 +236,17 @@ def run_profile_case(name: str, max_steps: int, precision: int = 0) -> int:
     return 0
 
 
-def measure_c3(q, inputs, torch, stream) -> dict:
+def measure_c3(q, inputs, torch, stream, hbm_gbs: float | None = None) -> dict:
     """The mixed-precision workload: 16384 x 16384 with sigma geometric
     1 -> 1e-3 over 8192 values then 1e-14 (numerical rank 8192), generated on
-    the GPU; FP64 and FP32-class forms, both stopping at the rank (the
-    rank-revealing use), each timed once after one untimed run."""
+    the GPU; the FP64 form, the FP32-class form on the CUDA cores and the two
+    tensor-core forms (3xTF32, split-BF16x3), all stopping at the rank (the
+    rank-revealing use), each timed once after one untimed run.  For the
+    tensor-core forms a third, profiled run gives the HBM rate of the merged
+    update's two passes over the trailing block (W = V^T A22 reads it once,
+    A22 -= V W reads and writes it: 8 and 16 bytes per element per step)."""
+    import numpy as np
+
     n = 16384
     r = n // 2
     sig = inputs.sigma_gap_geometric(n, r)
@@ -249,7 +255,8 @@ def measure_c3(q, inputs, torch, stream) -> dict:
     out = {"workload": "16384x16384, sigma geometric 1->1e-3 over 8192 values then 1e-14; stop at the rank",
            "tau": TAU, "delta": DELTA, "k_max": KMAX}
     flops = metric_flops(n, n)
-    for prec, key in ((0, "fp64"), (1, "mixed_fp32")):
+    forms = ((0, "fp64"), (1, "mixed_fp32"), (3, "tc_3xtf32"), (2, "tc_bf16x3"))
+    for prec, key in forms:
         for rep in range(2):
             dA = A0.clone()
             torch.cuda.synchronize()
@@ -265,6 +272,31 @@ def measure_c3(q, inputs, torch, stream) -> dict:
         ratio = d / sig[:r]
         out[key] = {"ms": ms, "GFLOP/s": flops / ms / 1e6, "rank": f.rank, "rank_colmax": f.rank_colmax,
                     "steps": f.nsteps, "d_over_sigma_min": float(ratio.min()), "d_over_sigma_max": float(ratio.max())}
+        if prec >= 2:
+            pr = q.qrdm_profile()
+            dA = A0.clone()
+            torch.cuda.synchronize()
+            f = q.factor(dA, TAU, DELTA, KMAX, workspace=ws, stream=stream, precision=prec, stop_at_rank=True,
+                         profile=pr, trace=True)
+            torch.cuda.synchronize()
+            t = f.trace
+            ns = np.asarray(t["ns"], dtype=np.float64)
+            kk = np.asarray(t["k"], dtype=np.float64)
+            elems = float(np.sum((n - ns) * np.maximum(n - ns - kk, 0.0)))
+            kms = {q.KERNEL_NAMES[i]: float(pr.ms[i]) for i in range(len(q.KERNEL_NAMES))}
+            w_gbs = 8.0 * elems / (kms["k_trail_w"] * 1e-3) / 1e9
+            u_gbs = 16.0 * elems / (kms["k_trail_update"] * 1e-3) / 1e9
+            out[key]["merged_update"] = {
+                "trailing_elements_over_steps": elems,
+                "w_pass_ms": kms["k_trail_w"], "w_pass_GBps": w_gbs,
+                "update_pass_ms": kms["k_trail_update"], "update_pass_GBps": u_gbs,
+                "t_build_and_w_sum_ms": kms["k_trail_wreduce"],
+                "hbm_frac_of_measured": {"w_pass": w_gbs / hbm_gbs if hbm_gbs else None,
+                                         "update_pass": u_gbs / hbm_gbs if hbm_gbs else None},
+                "note": "the k_trail_w / k_trail_update slots also hold the FP64 sub-panel updates of the panel "
+                        "columns (a small share); profiled run, events around every launch",
+                "kernel_ms": {k: round(v, 2) for k, v in kms.items() if v > 0},
+            }
         if prec == 1:
             # least squares on the mixed factorization, refined in FP64 on the
             # original matrix: a compatible right-hand side b = A x0
@@ -284,6 +316,7 @@ def measure_c3(q, inputs, torch, stream) -> dict:
             del x, b, x0
         del dA
     out["speedup"] = out["fp64"]["ms"] / out["mixed_fp32"]["ms"]
+    out["speedup_vs_fp64"] = {key: out["fp64"]["ms"] / out[key]["ms"] for _, key in forms[1:]}
     del A0, ws
     torch.cuda.empty_cache()
     return out
@@ -667,7 +700,13 @@ def main() -> int:
 
     c3 = None
     if rank == 0 and not args.no_c3:
-        c3 = measure_c3(q, inputs, torch, stream)
+        hbm = None
+        try:
+            with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fp:
+                hbm = float(json.load(fp)["hbm_gbs"])
+        except (OSError, KeyError, ValueError):
+            hbm = 6800.0  # fallback copy bandwidth of a GB300 (GB/s)
+        c3 = measure_c3(q, inputs, torch, stream, hbm)
 
     c4 = None
     if rank == 0 and not args.no_c4:

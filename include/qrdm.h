@@ -95,7 +95,25 @@ typedef struct qrdm_opts {
      updated in FP64); reflectors, panel, partial norms, recomputation and the
      rank decision stay FP64.  The stopping criterion then uses
      eps1 = max(eps1, 8 * 2^-24 * sqrt(n)), since FP32 updates leave roundoff
-     of about 2^-24 ||A|| in the trailing block. */
+     of about 2^-24 ||A|| in the trailing block.
+     2: split-BF16x3 on the tensor cores (tcgen05, FP32 accumulation in
+     TMEM): the panel's sub-panels update only the rest of the panel (FP64),
+     then the trailing block gets one merged update per step with all l
+     reflectors, W = T^T V^T A22 and A22 -= V W, operands converted on load
+     (FP64 -> FP32 -> hi + lo BF16; hi*hi + hi*lo + lo*hi).  Requires
+     k_max <= 64 (QRDM_ERR_UNSUPPORTED otherwise); eps1 = max(eps1,
+     2^-16 * sqrt(n)).  The candidate Gram matrix is FP32 as in 1.
+     3: as 2 with 3xTF32 (kind::tf32; hi, lo TF32, rounded to nearest): an
+     FP32-class form on the tensor cores, about 2^-21 relative per product;
+     eps1 = max(eps1, 8 * 2^-21 * sqrt(n)).
+     In 2 and 3 each chunk of 64 rows of the W product has its own TMEM
+     accumulator, summed in FP32 registers with round-to-nearest.
+     4: the merged structure of 2 and 3 entirely in FP64 on the CUDA cores
+     (the same results as 0 up to rounding order; k_max <= 64).
+     In 1, 2 and 3 the partial-norm downdate recomputes a norm once
+     t (u/uref)^2 <= sqrt(u_upd), with u_upd = 2^-24, 2^-16 and 2^-21, the
+     unit roundoff of that form's trailing update, instead of sqrt(eps).
+     Any other value: -11. */
   int32_t precision;
   int32_t reserved1;
   /* host, optional: per-kernel event timing (see qrdm_profile). */
@@ -383,7 +401,7 @@ int qrdm_mlp_train(float* d_w32, void* d_w16, float* d_adam, const float* d_x, c
  * refine > 0 iterations of FP64 refinement use the original matrix dA
  * (unchanged copy, FP64): r_k = b - A x_k, x_{k+1} = x_k + basic(r_k).  This
  * recovers FP64 accuracy from a factorization computed in reduced precision
- * (opts.precision = 1) when the system is compatible (b in the range of A)
+ * (opts.precision = 1, 2 or 3) when the system is compatible (b in the range of A)
  * or its residual is small; for other systems the fixed point satisfies
  * Q1^T (b - A x) = 0 with the computed Q1.
  * Arguments: dA/lda (may be NULL when refine = 0), dQR/ldqr, m, n, d_htau,

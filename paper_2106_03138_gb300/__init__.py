@@ -103,8 +103,10 @@ def factor(A, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mod
            stream=None, profile: qrdm_profile | None = None, precision: int = 0,
            policy: qrdm_policy | None = None) -> Factorization:
     """Factor A Pi = Q R in place.  ``A`` is a CUDA float64 tensor with
-    stride(0) == 1 (column-major, lda = stride(1)).  ``precision=1`` selects
-    the FP32-class mixed-precision form (see include/qrdm.h)."""
+    stride(0) == 1 (column-major, lda = stride(1)).  ``precision`` selects the
+    arithmetic of the trailing update: 0 FP64, 1 FP32 on the CUDA cores, 2
+    split-BF16x3 and 3 3xTF32 on the tensor cores, 4 the tensor-core forms'
+    merged update in FP64 (include/qrdm.h states each)."""
     import torch
 
     if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2):

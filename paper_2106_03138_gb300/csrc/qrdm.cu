@@ -14,6 +14,7 @@
 #include "../../include/qrdm.h"
 #include "qrdm_batched.cuh"
 #include "qrdm_kernels.cuh"
+#include "qrdm_tc_update.cuh"
 
 using namespace qrdm;
 
@@ -58,8 +59,8 @@ Layout make_layout(int64_t m, int64_t n, int kmax) {
   off = up(off + kk * sizeof(double));
   L.T = off;
   off = up(off + (size_t)KMAX * KMAX * sizeof(double));
-  L.Wp = off;
-  off = up(off + (size_t)WCHUNKS * kmax * nn * sizeof(double));
+  L.Wp = off;  // also holds the merged form's Wt (n x 64 floats)
+  off = up(off + std::max((size_t)WCHUNKS * kmax * nn * sizeof(double), nn * (size_t)TC_LMAX * sizeof(float)));
   L.W = off;
   off = up(off + (size_t)kmax * nn * sizeof(double));
   L.total = off;
@@ -96,6 +97,16 @@ int configure(DeviceConfig* cfg) {
   const int gram_smem = (int)(KMAX * (GRAM_ROWS + 1) * sizeof(double));
   if ((e = cudaFuncSetAttribute(k_trail_w, cudaFuncAttributeMaxDynamicSharedMemorySize, TRAIL_W_SMEM)) != cudaSuccess)
     return (int)e;
+  if ((e = cudaFuncSetAttribute(k_tc_w<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCW_SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_tc_w<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCW_SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_tc_update<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcu_smem<1>())) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_tc_update<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcu_smem<2>())) !=
+      cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(k_trail_w32, cudaFuncAttributeMaxDynamicSharedMemorySize, S32_SMEM)) != cudaSuccess)
     return (int)e;
   if ((e = cudaFuncSetAttribute(k_trail_update32, cudaFuncAttributeMaxDynamicSharedMemorySize, S32_SMEM)) !=
@@ -249,8 +260,9 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
   if (o.eps1_mode != 0 && o.eps1_mode != 1) return -11;
-  if (o.precision != 0 && o.precision != 1) return -11;
+  if (o.precision < 0 || o.precision > 4) return -11;
   if (!policy_valid(o.policy)) return -11;
+  if (o.precision >= 2 && k_max > TC_LMAX) return QRDM_ERR_UNSUPPORTED;
   cudaStream_t stream = (cudaStream_t)stream_;
 
   if (n == 0 || m == 0) {
@@ -304,9 +316,33 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     // block; the rank threshold must sit above it
     const double e32 = 8.0 * 5.9604644775390625e-8 * sqrt((double)n);
     if (e32 > P.eps1) P.eps1 = e32;
+  } else if (o.precision == 3) {
+    // 3xTF32 products carry about 2^-21 relative error
+    const double e21 = 8.0 * 4.76837158203125e-7 * sqrt((double)n);
+    if (e21 > P.eps1) P.eps1 = e21;
+  } else if (o.precision == 2) {
+    // split-BF16x3 products carry about 2^-17 relative error; threshold at 2^-16
+    // (the constant 1 calibrated on the gap spectra: the trailing noise after
+    // the gap stays about 50x below it)
+    const double e16 = 1.52587890625e-5 * sqrt((double)n);
+    if (e16 > P.eps1) P.eps1 = e16;
   }
+  // Norm downdating (Sec. 3.1) assumes the rows it subtracts come from an
+  // exact orthogonal transformation of the column; a reduced-precision update
+  // breaks that to its own unit roundoff u, so the downdated norm is trusted
+  // only while t (u_j / uref_j)^2 stays above sqrt(u) rather than sqrt(eps).
+  double u_upd = EPS;
+  if (o.precision == 1) u_upd = 5.9604644775390625e-8;       // 2^-24
+  else if (o.precision == 3) u_upd = 4.76837158203125e-7;    // 2^-21
+  else if (o.precision == 2) u_upd = 1.52587890625e-5;       // 2^-16
+  P.sqeps_dd = sqrt(u_upd);
   const bool mixed = (o.precision == 1);
+  const bool merged = (o.precision >= 2);
+  const bool tf32 = (o.precision == 3);
+  const bool merged64 = (o.precision == 4);
+  const bool gram32 = (o.precision != 0 && o.precision != 4);
   P.mixed = mixed ? 1 : 0;
+  P.merged = merged ? 1 : 0;
   P.kmax = k_max;
   P.stop_at_rank = o.stop_at_rank;
   P.check_last = o.check_last;
@@ -325,6 +361,14 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   P.G = (double*)(w + L.G);
   P.T = (double*)(w + L.T);
   P.Wp = (double*)(w + L.Wp);
+  P.Wt = (float*)(w + L.Wp);
+  {
+    // Wt and the W GEMM's segment partials share the W-partials buffer
+    const size_t wp_bytes = std::max((size_t)WCHUNKS * k_max * (size_t)n * sizeof(double),
+                                     (size_t)n * TC_LMAX * sizeof(float));
+    const int64_t fit = (int64_t)(wp_bytes / ((size_t)n * TC_LMAX * sizeof(float))) - 1;
+    P.tc_nseg = (int32_t)std::max<int64_t>(1, std::min<int64_t>(16, fit));
+  }
   P.W = (double*)(w + L.W);
   const int sms = cfg.sms;
   P.gram_chunks = sms < GRAM_CHUNKS_MAX ? sms : GRAM_CHUNKS_MAX;
@@ -395,7 +439,7 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   // events for profiling: two pools (the previous batch is read while the
   // next one runs), each with a start/end pair per launch
   constexpr int MAX_BATCH = 16;
-  const int per_step = 7 + 4 * nsub_full;
+  const int per_step = 11 + 4 * nsub_full;  // select..permute, 4 per sub-panel, 4 merged, downdate, step end
   const int pool = MAX_BATCH * per_step;
   if (prof && (int)g_events.size() < 2 * 2 * pool) {
     while ((int)g_events.size() < 2 * 2 * pool) {
@@ -438,11 +482,14 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     recs[which].clear();
     return cudaSuccess;
   };
+  const unsigned tcv_grid = (unsigned)std::min<int64_t>(TCV_CHUNKS, (m + TCV_ROWS_MIN - 1) / TCV_ROWS_MIN);
+  const dim3 tcw_grid((unsigned)((n + TCW_COLS - 1) / TCW_COLS), (unsigned)P.tc_nseg);
+  const dim3 tcu_grid((unsigned)((m + TCU_ROWS - 1) / TCU_ROWS), (unsigned)((n + TCU_COLS - 1) / TCU_COLS));
   auto enqueue_step = [&](int nsub) -> cudaError_t {
     cudaError_t e;
     if ((e = run(QRDM_K_SELECT, [&] { k_select<<<1, SEL_THREADS, 0, stream>>>(P); })) != cudaSuccess) return e;
     if ((e = run(QRDM_K_GRAM, [&] {
-           if (mixed)
+           if (gram32)
              k_gram32<<<P.gram_chunks, 256, gram_smem, stream>>>(P);
            else
              k_gram<<<P.gram_chunks, 256, gram_smem, stream>>>(P);
@@ -478,6 +525,45 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
                k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P, j);
            })) != cudaSuccess)
         return e;
+    }
+    if (merged) {
+      // one update of the trailing block with all of the step's reflectors
+      if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] {
+             k_tc_vtv<<<tcv_grid, TC_THREADS, 0, stream>>>(P);
+             k_tc_tbuild<<<1, TC_THREADS, 0, stream>>>(P);
+           })) != cudaSuccess)
+        return e;
+      if (merged64) {
+        // the same merged update in FP64 on the CUDA cores (exact form)
+        if ((e = run(QRDM_K_TRAIL_W, [&] {
+               k_trail_w<<<gemm_grid, GEMM_THREADS, TRAIL_W_SMEM, stream>>>(P, -1);
+             })) != cudaSuccess)
+          return e;
+        if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] { k_trail_wreduce<<<sms, GEMM_THREADS, 0, stream>>>(P, -1); })) !=
+            cudaSuccess)
+          return e;
+        if ((e = run(QRDM_K_TRAIL_UPDATE, [&] {
+               k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P, -1);
+             })) != cudaSuccess)
+          return e;
+      } else {
+        if ((e = run(QRDM_K_TRAIL_W, [&] {
+               if (tf32)
+                 k_tc_w<2><<<tcw_grid, TC_THREADS, TCW_SMEM, stream>>>(P);
+               else
+                 k_tc_w<1><<<tcw_grid, TC_THREADS, TCW_SMEM, stream>>>(P);
+             })) != cudaSuccess)
+          return e;
+        if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] { k_tc_wsum<<<2 * sms, TC_THREADS, 0, stream>>>(P); })) != cudaSuccess)
+          return e;
+        if ((e = run(QRDM_K_TRAIL_UPDATE, [&] {
+               if (tf32)
+                 k_tc_update<2><<<tcu_grid, TC_THREADS, tcu_smem<2>(), stream>>>(P);
+               else
+                 k_tc_update<1><<<tcu_grid, TC_THREADS, tcu_smem<1>(), stream>>>(P);
+             })) != cudaSuccess)
+          return e;
+      }
     }
     if ((e = run(QRDM_K_DOWNDATE, [&] { k_downdate<<<dd_grid, 256, 0, stream>>>(P); })) != cudaSuccess) return e;
     return run(QRDM_K_STEP_END, [&] { k_step_end<<<1, 1, 0, stream>>>(P); });

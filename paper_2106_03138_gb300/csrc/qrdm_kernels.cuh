@@ -75,6 +75,7 @@ struct Params {
   double* A;
   int64_t m, n, lda, kmin;
   double tau, delta, eps1;
+  double sqeps_dd;       // recompute threshold of the norm downdate: sqrt(unit roundoff of the trailing update)
   int32_t kmax, stop_at_rank, check_last, no_break, sdd, max_steps;
   double* htau;
   int32_t* perm;
@@ -94,6 +95,9 @@ struct Params {
   int32_t wchunks;      // most row chunks of the W phase
   int32_t w_units;      // target work units of the W phase (same in k_trail_w and k_trail_wreduce)
   int32_t mixed;        // 1: FP32-class trailing update and Gram (geometry of k_trail_w32)
+  int32_t merged;       // 1: sub-panel updates stop at the panel's end; one merged trailing update per step
+  float* Wt;            // merged form: [n][64] T^T V^T A22 per column, then tc_nseg segment partials (aliases Wp)
+  int32_t tc_nseg;      // merged form: most row segments of the W GEMM
   // optional trace
   StepRecord* trace;
   int32_t* traceJ;
@@ -1022,9 +1026,24 @@ struct SubGeom {
   int l;
 };
 
+// last column (exclusive) a sub-panel's block reflector reaches: the whole
+// trailing matrix, or only the rest of the panel when the trailing block gets
+// one merged update per step
+// (j < 0: the merged update itself, all of the step's reflectors on the
+// trailing block)
+__device__ __forceinline__ int64_t trail_end(const Params& P, const DevState* st, int j) {
+  return (P.merged && j >= 0) ? min(P.n, st->ns + (int64_t)st->k) : P.n;
+}
+
 __device__ __forceinline__ SubGeom sub_geom(const DevState* st, int j) {
   SubGeom g;
   const int k = st->k;
+  if (j < 0) {
+    g.r0 = st->ns;
+    g.c0 = st->ns + k;
+    g.l = st->l;
+    return g;
+  }
   g.r0 = st->ns + (int64_t)j * PB;
   g.c0 = st->ns + min((j + 1) * PB, k);
   g.l = st->cur_lj;
@@ -1086,7 +1105,7 @@ __device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int6
 
 template <int TG, int NQ, typename TC>
 __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int l, int64_t ns, int64_t j0,
-                                             int64_t mr, const WGeom& g) {
+                                             int64_t mr, const WGeom& g, int64_t cend) {
   constexpr int COLS = GEMM_THREADS / TG;
   constexpr int LDA_S = COLS + 1;
   constexpr int LDV_S = KMAX + 1;
@@ -1099,7 +1118,7 @@ __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int 
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t ct = u % g.nct, rc = u / g.nct;
     const int64_t cbase = j0 + ct * COLS;
-    const int ncols = (int)min((int64_t)COLS, P.n - cbase);
+    const int ncols = (int)min((int64_t)COLS, cend - cbase);
     const int64_t rbeg = rc * g.rows_per, rend = min(mr, rbeg + g.rows_per);
     TC acc[NQ];
 #pragma unroll
@@ -1148,7 +1167,8 @@ __device__ __forceinline__ void trail_w_kernel(Params& P, int j) {
   const int l = sg.l;
   const int64_t ns = sg.r0;  // base row/column of V
   const int64_t j0 = sg.c0;
-  const int64_t n2 = P.n - j0, mr = P.m - ns;
+  const int64_t cend = trail_end(P, st, j);
+  const int64_t n2 = cend - j0, mr = P.m - ns;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_W, 2.0 * (double)mr * (double)n2 * l);
   extern __shared__ double smw[];
@@ -1156,31 +1176,31 @@ __device__ __forceinline__ void trail_w_kernel(Params& P, int j) {
   const int tg = w_tg(l);
   const int nq = (l + tg - 1) / tg;
   if (tg == 1) {
-    trail_w_body<1, 1, TC>(P, smw, l, ns, j0, mr, g);
+    trail_w_body<1, 1, TC>(P, smw, l, ns, j0, mr, g, cend);
   } else if (tg == 2) {
-    if (nq == 1) trail_w_body<2, 1, TC>(P, smw, l, ns, j0, mr, g);
-    else trail_w_body<2, 2, TC>(P, smw, l, ns, j0, mr, g);
+    if (nq == 1) trail_w_body<2, 1, TC>(P, smw, l, ns, j0, mr, g, cend);
+    else trail_w_body<2, 2, TC>(P, smw, l, ns, j0, mr, g, cend);
   } else if (tg == 4) {
-    if (nq == 1) trail_w_body<4, 1, TC>(P, smw, l, ns, j0, mr, g);
-    else trail_w_body<4, 2, TC>(P, smw, l, ns, j0, mr, g);
+    if (nq == 1) trail_w_body<4, 1, TC>(P, smw, l, ns, j0, mr, g, cend);
+    else trail_w_body<4, 2, TC>(P, smw, l, ns, j0, mr, g, cend);
   } else {
     switch (nq) {
-      case 1: trail_w_body<8, 1, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 2: trail_w_body<8, 2, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 3: trail_w_body<8, 3, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 4: trail_w_body<8, 4, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 5: trail_w_body<8, 5, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 6: trail_w_body<8, 6, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 7: trail_w_body<8, 7, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 8: trail_w_body<8, 8, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 9: trail_w_body<8, 9, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 10: trail_w_body<8, 10, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 11: trail_w_body<8, 11, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 12: trail_w_body<8, 12, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 13: trail_w_body<8, 13, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 14: trail_w_body<8, 14, TC>(P, smw, l, ns, j0, mr, g); break;
-      case 15: trail_w_body<8, 15, TC>(P, smw, l, ns, j0, mr, g); break;
-      default: trail_w_body<8, 16, TC>(P, smw, l, ns, j0, mr, g); break;
+      case 1: trail_w_body<8, 1, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 2: trail_w_body<8, 2, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 3: trail_w_body<8, 3, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 4: trail_w_body<8, 4, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 5: trail_w_body<8, 5, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 6: trail_w_body<8, 6, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 7: trail_w_body<8, 7, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 8: trail_w_body<8, 8, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 9: trail_w_body<8, 9, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 10: trail_w_body<8, 10, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 11: trail_w_body<8, 11, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 12: trail_w_body<8, 12, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 13: trail_w_body<8, 13, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 14: trail_w_body<8, 14, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 15: trail_w_body<8, 15, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      default: trail_w_body<8, 16, TC>(P, smw, l, ns, j0, mr, g, cend); break;
     }
   }
 }
@@ -1193,7 +1213,8 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j)
   const SubGeom sg = sub_geom(st, j);
   const int l = sg.l;
   const int64_t j0 = sg.c0;
-  const int64_t n2 = P.n - j0, mr = P.m - sg.r0;
+  const int64_t cend = trail_end(P, st, j);
+  const int64_t n2 = cend - j0, mr = P.m - sg.r0;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
   const int64_t nct = (n2 + TW_COLS - 1) / TW_COLS;
   const int64_t nrc = w_geom(P, l, n2, mr).nrc;  // row chunks of k_trail_w
@@ -1204,7 +1225,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j)
   const int c = tid % TW_COLS, tg = tid / TW_COLS, TG = GEMM_THREADS / TW_COLS;
   for (int64_t ct = blockIdx.x; ct < nct; ct += gridDim.x) {
     const int64_t cbase = j0 + ct * TW_COLS;
-    const bool ok = (cbase + c) < P.n;
+    const bool ok = (cbase + c) < cend;
     __syncthreads();
     for (int t = tg; t < l; t += TG) {
       double s = 0.0;
@@ -1231,7 +1252,8 @@ __device__ __forceinline__ void trail_update_kernel(Params& P, int j) {
   const int l = sg.l;
   const int64_t ns = sg.r0, m = P.m, lda = P.lda;
   const int64_t j0 = sg.c0;
-  const int64_t n2 = P.n - j0, mr = m - ns;
+  const int64_t cend = trail_end(P, st, j);
+  const int64_t n2 = cend - j0, mr = m - ns;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_UPDATE, 2.0 * (double)mr * (double)n2 * l);
   const int64_t nrt = (mr + TU_ROWS - 1) / TU_ROWS;
@@ -1262,7 +1284,7 @@ __device__ __forceinline__ void trail_update_kernel(Params& P, int j) {
       for (int e = tid; e < TU_KC * TU_COLS; e += GEMM_THREADS) {
         int t = e / TU_COLS, c = e % TU_COLS;
         double v = 0.0;
-        if (t < kcnt && cbase + c < P.n) v = P.W[(int64_t)(t0 + t) * P.n + cbase + c];
+        if (t < kcnt && cbase + c < cend) v = P.W[(int64_t)(t0 + t) * P.n + cbase + c];
         s_w[t][c] = (TC)v;
       }
       __syncthreads();
@@ -1281,7 +1303,7 @@ __device__ __forceinline__ void trail_update_kernel(Params& P, int j) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int64_t col = cbase + tc + 16 * j;
-      if (col >= P.n) continue;
+      if (col >= cend) continue;
       double* a = P.A + col * lda + ns;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -1496,7 +1518,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 2) k_trail_update32(Params P, in
 // a10/a11: partial norm update.  One warp per column j >= ns + l:
 //   rejected panel columns (ns+l <= j < ns+k): recompute;
 //   trailing columns: block downdate over rows ns..ns+l-1, recompute when
-//   t (u/uref)^2 <= sqrt(eps).
+//   t (u/uref)^2 <= sqrt(u_upd), u_upd the unit roundoff of the trailing
+//   update (eps in the FP64 forms).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_downdate(Params P) {
   DevState* st = P.st;
@@ -1507,7 +1530,7 @@ __global__ void __launch_bounds__(256) k_downdate(Params P) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const double sqeps = sqrt(EPS);
+  const double sqeps = P.sqeps_dd;
   int nrec = 0;
   for (int64_t j = ns + gw; j < P.n; j += nwarps) {
     const double* a = P.A + j * lda;

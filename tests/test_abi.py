@@ -84,9 +84,13 @@ def test_workspace_size_and_argument_checks(lib):
     rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 4, fake, fake, o, fake, 1 << 30, 0)
     assert rc == -11
     o = b.qrdm_opts()
-    o.precision = 2
-    rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 4, fake, fake, o, fake, 1 << 30, 0)
-    assert rc == -11
+    for bad in (5, -1):
+        o.precision = bad
+        rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 4, fake, fake, o, fake, 1 << 30, 0)
+        assert rc == -11
+    o.precision = 3  # the tensor-core forms take blocks of at most 64
+    rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 65, fake, fake, o, fake, 1 << 30, 0)
+    assert rc == b.QRDM_ERR_UNSUPPORTED
     assert b.qrdm_strerror(2).startswith("the matrix")
     assert lib.qrdm_version() >= 100
 
