@@ -32,11 +32,10 @@ static_assert(sizeof(StepRecord) == sizeof(qrdm_step_record), "trace record layo
 size_t up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t st, u, uref, cols, mdst, msrc, Gp, G, T, Wp, W, total;
+  size_t st, u, uref, cols, mdst, msrc, Gp, G, T, Wp, W, vw, vu, wi, total;
 };
 
 Layout make_layout(int64_t m, int64_t n, int kmax) {
-  (void)m;
   Layout L;
   size_t off = 0;
   const size_t nn = (size_t)(n > 0 ? n : 1);
@@ -63,6 +62,16 @@ Layout make_layout(int64_t m, int64_t n, int kmax) {
   off = up(off + std::max((size_t)WCHUNKS * kmax * nn * sizeof(double), nn * (size_t)TC_LMAX * sizeof(float)));
   L.W = off;
   off = up(off + (size_t)kmax * nn * sizeof(double));
+  // operand images of the tensor-core forms (blocks of at most 64 columns)
+  const bool tc = kmax <= TC_LMAX;
+  const size_t mm = (size_t)(m > 0 ? m : 1);
+  off = (off + 1023) / 1024 * 1024;
+  L.vw = off;
+  off += tc ? tc_img_bytes((int64_t)mm) : 0;
+  L.vu = off;
+  off += tc ? tc_img_bytes((int64_t)mm) : 0;
+  L.wi = off;
+  off = up(off + (tc ? tc_img_bytes((int64_t)nn) : 0));
   L.total = off;
   return L;
 }
@@ -73,6 +82,7 @@ struct DeviceConfig {
   int cluster = 0;  // panel cluster size
   int coop = 0;     // cooperative launch supported
   int qrp_grid = 0; // CTAs of the fused single-column kernel (one per SM)
+  int tcu_occ[2] = {1, 1};  // resident CTAs per SM of k_tc_update<1>, <2> (TMEM caps them at 2)
   bool ok = false;
   cudaEvent_t ev[2 * QRDM_NKERNELS] = {};  // profile events, created on first use
   bool have_events = false;
@@ -97,6 +107,8 @@ int configure(DeviceConfig* cfg) {
   const int gram_smem = (int)(KMAX * (GRAM_ROWS + 1) * sizeof(double));
   if ((e = cudaFuncSetAttribute(k_trail_w, cudaFuncAttributeMaxDynamicSharedMemorySize, TRAIL_W_SMEM)) != cudaSuccess)
     return (int)e;
+  if ((e = cudaFuncSetAttribute(k_tc_tbuild, cudaFuncAttributeMaxDynamicSharedMemorySize, TCB_SMEM)) != cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(k_tc_w<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCW_SMEM)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_tc_w<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCW_SMEM)) != cudaSuccess)
@@ -158,6 +170,25 @@ int configure(DeviceConfig* cfg) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qrp_tail, QRP_THREADS, QRP_SMEM_MAX);
     if (e != cudaSuccess) return (int)e;
     c.qrp_grid = (c.coop && per_sm >= 1) ? c.sms : 0;
+  }
+  {
+    // the tensor-core kernels want the largest shared-memory carveout (the
+    // update fits two CTAs per SM in the BF16 form only with it)
+    for (const void* f : {(const void*)k_tc_update<1>, (const void*)k_tc_update<2>, (const void*)k_tc_w<1>,
+                          (const void*)k_tc_w<2>})
+      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+        return (int)e;
+    int o1 = 0, o2 = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_tc_update<1>, TC_THREADS, tcu_smem<1>())) !=
+        cudaSuccess)
+      return (int)e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_tc_update<2>, TC_THREADS, tcu_smem<2>())) !=
+        cudaSuccess)
+      return (int)e;
+    // each CTA holds 2 x TCU_COLS TMEM columns of the 512
+    const int tmem_cap = 512 / (2 * TCU_COLS);
+    c.tcu_occ[0] = std::max(1, std::min(o1, tmem_cap));
+    c.tcu_occ[1] = std::max(1, std::min(o2, tmem_cap));
   }
   c.ok = true;
   g_cfg = c;
@@ -362,6 +393,9 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   P.T = (double*)(w + L.T);
   P.Wp = (double*)(w + L.Wp);
   P.Wt = (float*)(w + L.Wp);
+  P.tc_vw = (unsigned char*)(w + L.vw);
+  P.tc_vu = (unsigned char*)(w + L.vu);
+  P.tc_wi = (unsigned char*)(w + L.wi);
   {
     // Wt and the W GEMM's segment partials share the W-partials buffer
     const size_t wp_bytes = std::max((size_t)WCHUNKS * k_max * (size_t)n * sizeof(double),
@@ -484,7 +518,11 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   };
   const unsigned tcv_grid = (unsigned)std::min<int64_t>(TCV_CHUNKS, (m + TCV_ROWS_MIN - 1) / TCV_ROWS_MIN);
   const dim3 tcw_grid((unsigned)((n + TCW_COLS - 1) / TCW_COLS), (unsigned)P.tc_nseg);
-  const dim3 tcu_grid((unsigned)((m + TCU_ROWS - 1) / TCU_ROWS), (unsigned)((n + TCU_COLS - 1) / TCU_COLS));
+  // persistent update: at most one CTA per tile of the first step's trailing block
+  const int64_t tcu_tiles = ((m + TCU_ROWS - 1) / TCU_ROWS) * ((n + TCU_COLS - 1) / TCU_COLS);
+  const int tcvi_grid = (int)std::min<int64_t>((int64_t)sms * 4, ((m + 127) / 128 * 128 * TC_LMAX + TC_THREADS - 1) / TC_THREADS);
+  const int tcu_grid1 = (int)std::min<int64_t>(tcu_tiles, (int64_t)sms * cfg.tcu_occ[0]);
+  const int tcu_grid2 = (int)std::min<int64_t>(tcu_tiles, (int64_t)sms * cfg.tcu_occ[1]);
   auto enqueue_step = [&](int nsub) -> cudaError_t {
     cudaError_t e;
     if ((e = run(QRDM_K_SELECT, [&] { k_select<<<1, SEL_THREADS, 0, stream>>>(P); })) != cudaSuccess) return e;
@@ -529,8 +567,17 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     if (merged) {
       // one update of the trailing block with all of the step's reflectors
       if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] {
-             k_tc_vtv<<<tcv_grid, TC_THREADS, 0, stream>>>(P);
-             k_tc_tbuild<<<1, TC_THREADS, 0, stream>>>(P);
+             if (merged64)
+               k_tc_vtv<double><<<tcv_grid, TC_THREADS, 0, stream>>>(P);
+             else
+               k_tc_vtv<float><<<tcv_grid, TC_THREADS, 0, stream>>>(P);
+             k_tc_tbuild<<<1, TC_THREADS, TCB_SMEM, stream>>>(P);
+             if (!merged64) {
+               if (tf32)
+                 k_tc_vimg<2><<<tcvi_grid, TC_THREADS, 0, stream>>>(P);
+               else
+                 k_tc_vimg<1><<<tcvi_grid, TC_THREADS, 0, stream>>>(P);
+             }
            })) != cudaSuccess)
         return e;
       if (merged64) {
@@ -549,18 +596,23 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
       } else {
         if ((e = run(QRDM_K_TRAIL_W, [&] {
                if (tf32)
-                 k_tc_w<2><<<tcw_grid, TC_THREADS, TCW_SMEM, stream>>>(P);
+                 k_tc_w<2><<<tcw_grid, TCW_THREADS, TCW_SMEM, stream>>>(P);
                else
-                 k_tc_w<1><<<tcw_grid, TC_THREADS, TCW_SMEM, stream>>>(P);
+                 k_tc_w<1><<<tcw_grid, TCW_THREADS, TCW_SMEM, stream>>>(P);
              })) != cudaSuccess)
           return e;
-        if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] { k_tc_wsum<<<2 * sms, TC_THREADS, 0, stream>>>(P); })) != cudaSuccess)
+        if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] {
+               if (tf32)
+                 k_tc_wsum<2><<<2 * sms, TC_THREADS, 0, stream>>>(P);
+               else
+                 k_tc_wsum<1><<<2 * sms, TC_THREADS, 0, stream>>>(P);
+             })) != cudaSuccess)
           return e;
         if ((e = run(QRDM_K_TRAIL_UPDATE, [&] {
                if (tf32)
-                 k_tc_update<2><<<tcu_grid, TC_THREADS, tcu_smem<2>(), stream>>>(P);
+                 k_tc_update<2><<<tcu_grid2, TC_THREADS, tcu_smem<2>(), stream>>>(P);
                else
-                 k_tc_update<1><<<tcu_grid, TC_THREADS, tcu_smem<1>(), stream>>>(P);
+                 k_tc_update<1><<<tcu_grid1, TC_THREADS, tcu_smem<1>(), stream>>>(P);
              })) != cudaSuccess)
           return e;
       }

@@ -98,6 +98,9 @@ struct Params {
   int32_t merged;       // 1: sub-panel updates stop at the panel's end; one merged trailing update per step
   float* Wt;            // merged form: [n][64] T^T V^T A22 per column, then tc_nseg segment partials (aliases Wp)
   int32_t tc_nseg;      // merged form: most row segments of the W GEMM
+  unsigned char* tc_vw; // tensor-core forms: V's operand image for the W pass
+  unsigned char* tc_vu; // V's operand image for the update
+  unsigned char* tc_wi; // W's operand image for the update
   // optional trace
   StepRecord* trace;
   int32_t* traceJ;
@@ -1081,14 +1084,25 @@ __device__ __forceinline__ int w_tg(int l) { return l >= 8 ? 8 : (l >= 4 ? 4 : (
 struct WGeom {
   int64_t nct, rows_per, nrc;
   int cols;
+  // partial W of row chunk q, reflector t, column c at Wp[q qstride + t tstride + c - cofs]
+  int64_t qstride, tstride, cofs;
 };
+
+// sub-panel updates of the merged form reach at most 64 columns (the rest of
+// the panel): more row chunks keep the SMs busy, their partials packed 64
+// columns wide so that up to wchunks * n / 64 of them fit the buffer
+constexpr int NARROW_WCHUNKS = 64;
+constexpr int NARROW_COLS = 64;
 
 // Row chunks of k_trail_w32: passes of at least S32_ROWS rows (one staged V
 // block per pass), at most wchunks of them.
 __device__ __forceinline__ int64_t w32_rows_per(const Params& P, int64_t mr);
 
-__device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int64_t mr) {
+__device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int64_t mr, int64_t narrow_c0 = -1) {
   WGeom g;
+  g.qstride = (int64_t)P.kmax * P.n;
+  g.tstride = P.n;
+  g.cofs = 0;
   if (P.mixed) {
     g.cols = 0;
     g.nct = 0;
@@ -1098,7 +1112,15 @@ __device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int6
   }
   g.cols = GEMM_THREADS / w_tg(l);
   g.nct = (n2 + g.cols - 1) / g.cols;
-  g.rows_per = wchunk_rows(mr, g.nct, P.wchunks, P.w_units);
+  int cap = P.wchunks;
+  if (narrow_c0 >= 0 && n2 <= NARROW_COLS) {
+    const int64_t fit = (int64_t)P.wchunks * P.n / NARROW_COLS;
+    cap = (int)max((int64_t)1, min((int64_t)NARROW_WCHUNKS, fit));
+    g.qstride = (int64_t)P.kmax * NARROW_COLS;
+    g.tstride = NARROW_COLS;
+    g.cofs = narrow_c0;
+  }
+  g.rows_per = wchunk_rows(mr, g.nct, cap, P.w_units);
   g.nrc = (mr + g.rows_per - 1) / g.rows_per;
   return g;
 }
@@ -1147,11 +1169,11 @@ __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int 
       }
     }
     if (c < ncols) {
-      double* out = P.Wp + rc * (int64_t)P.kmax * P.n;
+      double* out = P.Wp + rc * g.qstride;
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
         const int t = tg + q * TG;
-        if (t < l) out[(int64_t)t * P.n + cbase + c] = (double)acc[q];
+        if (t < l) out[(int64_t)t * g.tstride + cbase + c - g.cofs] = (double)acc[q];
       }
     }
   }
@@ -1172,7 +1194,7 @@ __device__ __forceinline__ void trail_w_kernel(Params& P, int j) {
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_W, 2.0 * (double)mr * (double)n2 * l);
   extern __shared__ double smw[];
-  const WGeom g = w_geom(P, l, n2, mr);
+  const WGeom g = w_geom(P, l, n2, mr, (P.merged && j >= 0) ? j0 : -1);
   const int tg = w_tg(l);
   const int nq = (l + tg - 1) / tg;
   if (tg == 1) {
@@ -1217,7 +1239,8 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j)
   const int64_t n2 = cend - j0, mr = P.m - sg.r0;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
   const int64_t nct = (n2 + TW_COLS - 1) / TW_COLS;
-  const int64_t nrc = w_geom(P, l, n2, mr).nrc;  // row chunks of k_trail_w
+  const WGeom g = w_geom(P, l, n2, mr, (P.merged && j >= 0) ? j0 : -1);  // row chunks of k_trail_w
+  const int64_t nrc = g.nrc;
   if (blockIdx.x == 0 && threadIdx.x == 0)
     add_flops(st, KID_TRAIL_WREDUCE, (double)n2 * l * ((double)(nrc - 1) + (l + 1.0)));
   __shared__ double s_w[KMAX][TW_COLS + 1];
@@ -1230,7 +1253,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j)
     for (int t = tg; t < l; t += TG) {
       double s = 0.0;
       if (ok)
-        for (int64_t q = 0; q < nrc; ++q) s += P.Wp[q * (int64_t)P.kmax * P.n + (int64_t)t * P.n + cbase + c];
+        for (int64_t q = 0; q < nrc; ++q) s += P.Wp[q * g.qstride + (int64_t)t * g.tstride + cbase + c - g.cofs];
       s_w[t][c] = s;
     }
     __syncthreads();

@@ -4,15 +4,19 @@
 // the trailing block A22 = A[ns:, ns+k:] then receives one merged update with
 // all l reflectors of the step (l <= 64), as in Alg. 4:
 //   T   = the l x l compact-WY factor of the step (k_tc_vtv + k_tc_tbuild),
-//   W   = T^T V^T A22          (k_tc_w over row segments, tcgen05; k_tc_wsum),
+//   V   -> hi/lo operand images in global memory (k_tc_vimg),
+//   W   = T^T V^T A22   (k_tc_w over row segments, tcgen05; k_tc_wsum, which
+//                        also writes W's hi/lo operand image),
 //   A22 = A22 - V W                                (k_tc_update, tcgen05).
 // One pass over A22 for W and one for the update instead of one pair per
 // sub-panel: the form is HBM-bound, and the merge divides its traffic by the
-// number of sub-panels.  Operands are converted on load: FP64 -> FP32 (round
-// to nearest, integer pipe) -> x = hi + lo with hi, lo BF16 (precision 2) or
+// number of sub-panels.  Operands are split on load: FP64 -> FP32 (round to
+// nearest, integer pipe) -> x = hi + lo with hi, lo BF16 (precision 2) or
 // TF32 (precision 3); each product uses hi*hi + hi*lo + lo*hi (lo*lo dropped:
 // about 2^-17 relative for BF16, 2^-21 for TF32), FP32 accumulation in TMEM.
-// A stays FP64 in HBM.
+// A stays FP64 in HBM.  V and W, small and read by many CTAs, are split once
+// per step into images laid out exactly as the MMA's shared-memory tiles
+// (K-major, 128-byte swizzle), which the kernels copy without conversion.
 #pragma once
 
 #include "qrdm_kernels.cuh"
@@ -22,8 +26,8 @@ namespace qrdm {
 
 constexpr int TC_THREADS = 256;
 constexpr int TCW_COLS = 128;   // columns per CTA of the W GEMM (its M)
-constexpr int TCU_ROWS = 128;   // rows per CTA of the update (its M)
-constexpr int TCU_COLS = 256;   // columns per CTA of the update (its N)
+constexpr int TCU_ROWS = 128;   // rows of one update tile (its M)
+constexpr int TCU_COLS = 128;   // columns of one update tile (its N)
 constexpr int TC_LMAX = 64;     // reflectors per merged update (K of the update, N of the W GEMM)
 constexpr long long TC_WAIT = 2000000000LL;  // clock cycles before an MMA wait gives up (about 1 s)
 constexpr int TCW_TILE_A = TCW_COLS * 128;   // bytes of one A tile (128 rows x one 128-byte atom of K)
@@ -38,12 +42,20 @@ struct TcFmt {
   static constexpr int KA = 128 / ESZ;        // elements of K per atom
   static constexpr int NA = TC_LMAX / KA;     // atoms for the 64 reflectors of the update
 };
+// V hi/lo for one row block, W hi/lo for two column tiles (double-buffered)
 template <int FMT>
 constexpr int tcu_smem() {
-  return 1024 + 2 * TCU_ROWS * 128 * TcFmt<FMT>::NA + 2 * TCU_COLS * 128 * TcFmt<FMT>::NA + 64;
+  return 1024 + 6 * 128 * 128 * TcFmt<FMT>::NA + 64;
 }
 constexpr int TCV_ROWS_MIN = 128;  // rows per CTA of k_tc_vtv (at least)
-constexpr int TCV_CHUNKS = 64;     // at most this many row chunks (partial V^T V in the Gram partials buffer)
+constexpr int TCV_CHUNKS = 128;    // at most this many row chunks (partial V^T V in the Gram partials buffer)
+constexpr int TC_ATOM = 128 * 128;  // bytes of one K atom of a 128-row operand tile
+
+// bytes of one operand image over `rows` rows (or columns), either format:
+// V for the W pass (per K chunk: 64 reflector rows x 128 B, hi then lo), V for
+// the update (per 128-row block: NA atoms hi, NA atoms lo) and W for the
+// update (per 128-column tile, the same) all fit in 512 B per row, padded
+__host__ __device__ constexpr size_t tc_img_bytes(int64_t rows) { return (size_t)(rows + 256) * 512; }
 
 template <int FMT>
 __device__ __forceinline__ void tc_put(unsigned char* hi, unsigned char* lo, uint32_t off, float x) {
@@ -68,84 +80,112 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
 }
 
 // the step's reflectors V^T V (pairs i < j, unit diagonal convention): partial
-// sums over row chunks, one chunk per CTA, into Gp[chunk][pair index]
+// sums over row chunks, one chunk per CTA, into Gp[chunk][pair index].  R is
+// the arithmetic within a chunk: FP64 for the exact merged form, FP32 for the
+// tensor-core forms (whose T is applied in FP32); chunks are added in FP64.
+template <typename R>
 __global__ void __launch_bounds__(TC_THREADS) k_tc_vtv(Params P) {
   DevState* st = P.st;
   if (st->done) return;
   const int l = st->l;
   const int64_t ns = st->ns, mr = P.m - ns;
   if (l <= 1 || st->k >= P.n - ns || mr <= 0) return;
-  __shared__ double s_v[64][TC_LMAX + 1];
+  __shared__ R s_v[64][TC_LMAX + 1];
   const int64_t per = max((int64_t)TCV_ROWS_MIN, (mr + TCV_CHUNKS - 1) / TCV_CHUNKS);
   const int64_t nch = (mr + per - 1) / per;
   const int tid = threadIdx.x;
   const int npair = l * (l - 1) / 2;
+  // this thread's pairs e = tid + 256 q -> (i < j)
+  int pi[8], pj[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = tid + q * TC_THREADS;
+    int j = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);
+    while (j * (j - 1) / 2 > e) --j;
+    while ((j + 1) * j / 2 <= e) ++j;
+    pj[q] = j;
+    pi[q] = e - j * (j - 1) / 2;
+  }
   for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
     const int64_t rb = ch * per, re = min(mr, rb + per);
-    double acc[8];
+    R acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 8; ++q) acc[q] = (R)0;
     for (int64_t r0 = rb; r0 < re; r0 += 64) {
       const int rows = (int)min((int64_t)64, re - r0);
       __syncthreads();
       for (int e = tid; e < 64 * l; e += TC_THREADS) {
         const int t = e / 64, rr = e % 64;
-        s_v[rr][t] = (rr < rows) ? vget(P.A, P.lda, ns, r0 + rr, t) : 0.0;
+        const double v = (rr < rows) ? vget(P.A, P.lda, ns, r0 + rr, t) : 0.0;
+        s_v[rr][t] = (sizeof(R) == 4) ? (R)f64_to_f32_rn(v) : (R)v;
       }
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const int e = tid + q * TC_THREADS;
-        if (e < npair) {
-          int j = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);  // e -> (i < j)
-          while (j * (j - 1) / 2 > e) --j;
-          while ((j + 1) * j / 2 <= e) ++j;
-          const int i = e - j * (j - 1) / 2;
-          double s = acc[q];
-          for (int rr = 0; rr < rows; ++rr) s = fma(s_v[rr][i], s_v[rr][j], s);
-          acc[q] = s;
+        if (tid + q * TC_THREADS < npair) {
+          R x = acc[q];
+          for (int rr = 0; rr < rows; ++rr) x = fmat(s_v[rr][pi[q]], s_v[rr][pj[q]], x);
+          acc[q] = x;
         }
       }
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int e = tid + q * TC_THREADS;
-      if (e < npair) P.Gp[ch * (int64_t)P.kmax * P.kmax + e] = acc[q];
+      if (e < npair) P.Gp[ch * (int64_t)P.kmax * P.kmax + e] = (sizeof(R) == 4) ? f32_to_f64((float)acc[q]) : (double)acc[q];
     }
   }
 }
 
 // T (l x l, forward columnwise): T_jj = htau_j, T[0:j, j] = -htau_j T[0:j, 0:j] S[0:j, j]
-// with S = V^T V summed from the partials; one CTA; T into P.T (column-major, ld KMAX)
+// with S = V^T V summed from the chunk partials (chunk-outer, so that each
+// thread's loads are independent; the order of the sum is the chunk order);
+// S and T in shared memory; one CTA; T into P.T (column-major, ld KMAX)
+constexpr int TCB_SMEM = 2 * TC_LMAX * (TC_LMAX + 1) * (int)sizeof(double);
 __global__ void __launch_bounds__(TC_THREADS) k_tc_tbuild(Params P) {
   DevState* st = P.st;
   if (st->done) return;
   const int l = st->l;
   const int64_t ns = st->ns, mr = P.m - ns;
   if (l <= 0 || st->k >= P.n - ns || mr <= 0) return;
-  __shared__ double s_t[TC_LMAX][TC_LMAX + 1];
-  double* S = P.G;  // V^T V (row i, column j at i * kmax + j); the step's Gram is no longer needed
+  extern __shared__ double tb_smem[];
+  double (*s_t)[TC_LMAX + 1] = reinterpret_cast<double (*)[TC_LMAX + 1]>(tb_smem);
+  double (*s_s)[TC_LMAX + 1] = reinterpret_cast<double (*)[TC_LMAX + 1]>(tb_smem + TC_LMAX * (TC_LMAX + 1));
   const int64_t per = max((int64_t)TCV_ROWS_MIN, (mr + TCV_CHUNKS - 1) / TCV_CHUNKS);
   const int64_t nch = (mr + per - 1) / per;
   const int tid = threadIdx.x;
   const int npair = l * (l - 1) / 2;
-  for (int e = tid; e < npair; e += TC_THREADS) {
-    int j = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);
-    while (j * (j - 1) / 2 > e) --j;
-    while ((j + 1) * j / 2 <= e) ++j;
-    const int i = e - j * (j - 1) / 2;
-    double s = 0.0;
-    for (int64_t c = 0; c < nch; ++c) s += P.Gp[c * (int64_t)P.kmax * P.kmax + e];
-    S[(int64_t)i * P.kmax + j] = s;
+  double acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  if (l > 1) {
+    for (int64_t c = 0; c < nch; ++c) {
+      const double* g = P.Gp + c * (int64_t)P.kmax * P.kmax;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = tid + q * TC_THREADS;
+        if (e < npair) acc[q] += g[e];
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = tid + q * TC_THREADS;
+    if (e < npair) {
+      int j = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);
+      while (j * (j - 1) / 2 > e) --j;
+      while ((j + 1) * j / 2 <= e) ++j;
+      s_s[e - j * (j - 1) / 2][j] = acc[q];
+    }
   }
   for (int e = tid; e < TC_LMAX * TC_LMAX; e += TC_THREADS) s_t[e / TC_LMAX][e % TC_LMAX] = 0.0;
   __syncthreads();
   for (int j = 0; j < l; ++j) {
     const double ht = P.htau[ns + j];
     if (tid < j) {
-      double s = 0.0;
-      for (int q = tid; q < j; ++q) s = fma(s_t[tid][q], S[(int64_t)q * P.kmax + j], s);
-      s_t[tid][j] = -ht * s;
+      double x = 0.0;
+      for (int q = tid; q < j; ++q) x = fma(s_t[tid][q], s_s[q][j], x);
+      s_t[tid][j] = -ht * x;
     }
     if (tid == 0) s_t[j][j] = ht;
     __syncthreads();
@@ -171,20 +211,128 @@ __device__ __forceinline__ void tc_segments(int64_t mr, int nseg_max, int ka, in
   *seg_rows = sr;
 }
 
-// partial V^T A22 over one row segment for 128 trailing columns: D (columns x
-// 64 reflectors) in TMEM, stages of one K atom of rows, double-buffered; every
-// thread issues its stage's global loads before converting them.  The tensor
-// core's FP32 accumulation does not round to nearest, so its error grows with
-// the number of MMAs summed into one accumulator: each chunk of rows gets its
-// own accumulator (two alternate in TMEM), which the warps add into FP32
-// registers (round to nearest) once the chunk's MMAs are done, while the next
-// chunk's MMAs run.  Raw sums to Wpart[segment][column][64].
+// V's operand images, one element per thread (rows padded with zeros to the
+// next 128): Vw for the W pass (chunk of KA rows: reflector t is the tile's
+// row, the chunk's rows its K) and Vu for the update (block of 128 rows: row
+// r is the tile's row, the reflectors its K, in NA atoms)
 template <int FMT>
-__global__ void __launch_bounds__(TC_THREADS) k_tc_w(Params P) {
-  constexpr int ESZ = TcFmt<FMT>::ESZ, KA = TcFmt<FMT>::KA;
-  constexpr int NLA = TCW_COLS * KA / TC_THREADS;  // A elements per thread and stage
-  constexpr int NLV = TC_LMAX * KA / TC_THREADS;   // V elements per thread and stage
-  constexpr int HALF = TC_LMAX / 2;                // reflector sums each thread keeps
+__global__ void __launch_bounds__(TC_THREADS) k_tc_vimg(Params P) {
+  constexpr int ESZ = TcFmt<FMT>::ESZ, KA = TcFmt<FMT>::KA, NA = TcFmt<FMT>::NA;
+  DevState* st = P.st;
+  if (st->done) return;
+  const int l = st->l;
+  const int64_t ns = st->ns, mr = P.m - ns;
+  if (l <= 0 || st->k >= P.n - ns || mr <= 0) return;
+  const int64_t pad = (mr + 127) / 128 * 128;
+  const int64_t total = pad * TC_LMAX;
+  for (int64_t e = (int64_t)blockIdx.x * TC_THREADS + threadIdx.x; e < total; e += (int64_t)gridDim.x * TC_THREADS) {
+    const int t = (int)(e / pad);
+    const int64_t r = e % pad;
+    const double v = (t < l && r < mr) ? vget(P.A, P.lda, ns, r, t) : 0.0;
+    const float f = f64_to_f32_rn(v);
+    unsigned char* w = P.tc_vw + (r / KA) * (2 * TC_LMAX * 128);
+    tc_put<FMT>(w, w + TC_LMAX * 128, tc::sw128_off_e<ESZ>(t, (int)(r % KA)), f);
+    unsigned char* u = P.tc_vu + (r / 128) * (2 * NA * TC_ATOM) + (t / KA) * TC_ATOM;
+    tc_put<FMT>(u, u + NA * TC_ATOM, tc::sw128_off_e<ESZ>((int)(r % 128), t % KA), f);
+  }
+}
+
+// FP32 x[0..EPC) -> one 16-byte chunk of hi and one of lo (EPC = 8 BF16 or
+// 4 TF32 elements)
+template <int FMT>
+__device__ __forceinline__ void tc_split16(const float* x, uint4* hi, uint4* lo) {
+  if (FMT == 1) {
+    uint32_t h[4], w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+      const float2 hf = __bfloat1622float2(hb);
+      const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * i] - hf.x, x[2 * i + 1] - hf.y);
+      h[i] = *reinterpret_cast<const uint32_t*>(&hb);
+      w[i] = *reinterpret_cast<const uint32_t*>(&lb);
+    }
+    *hi = make_uint4(h[0], h[1], h[2], h[3]);
+    *lo = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {
+    float h[4], w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      h[i] = tc::tf32_rna(x[i]);
+      w[i] = tc::tf32_rna(x[i] - h[i]);
+    }
+    *hi = make_uint4(__float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]), __float_as_uint(h[3]));
+    *lo = make_uint4(__float_as_uint(w[0]), __float_as_uint(w[1]), __float_as_uint(w[2]), __float_as_uint(w[3]));
+  }
+}
+
+// partial V^T A22 over one row segment for 128 trailing columns: D (columns x
+// 64 reflectors) in TMEM, stages of one K atom of rows, double-buffered in
+// shared memory.  Thread = (column, 16-byte chunk of the atom) for 2 columns
+// 64 apart: it loads the chunk's EPC doubles of each column with plain
+// pointer offsets (the loads of chunk i + 1 are issued before chunk i is
+// converted, so two chunks are in flight), splits them and stores one
+// 16-byte hi and lo chunk each; V's chunk comes from its image (16-byte
+// copies).  The tensor core's FP32 accumulation does not round to nearest, so
+// its error grows with the number of MMAs summed into one accumulator: each
+// chunk of rows gets its own accumulator (two alternate in TMEM), which the
+// warps add into FP32 registers (round to nearest) once the chunk's MMAs are
+// done, while the next chunk's MMAs run.  Raw sums to
+// Wpart[segment][column][64].
+constexpr int TCW_THREADS = 512;
+
+template <int FMT>
+struct TcwLoad {
+  static constexpr int ESZ = TcFmt<FMT>::ESZ, EPC = 16 / ESZ;
+  static constexpr int UPT = TCW_COLS * 8 / TCW_THREADS;           // (column, chunk) units per thread
+  static constexpr int VPT = 2 * TCW_TILE_V / 16 / TCW_THREADS;    // 16-byte pieces of V per thread
+  double a[UPT][EPC];
+  uint4 v[VPT];
+};
+
+// issue the global loads of chunk i (rows r0 .. r0 + KA relative to ns)
+template <int FMT>
+__device__ __forceinline__ void tcw_load(TcwLoad<FMT>& L, const double* const* colp, const bool* colok, int64_t i,
+                                         int64_t r0, int64_t rend, int kg, const uint4* vsrc, int tid) {
+  constexpr int KA = TcFmt<FMT>::KA, EPC = TcwLoad<FMT>::EPC;
+  const bool full = r0 + KA <= rend;
+#pragma unroll
+  for (int q = 0; q < TcwLoad<FMT>::UPT; ++q) {
+    const double* src = colp[q] + i * KA;
+#pragma unroll
+    for (int e = 0; e < EPC; ++e) L.a[q][e] = (colok[q] && (full || r0 + kg * EPC + e < rend)) ? src[e] : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < TcwLoad<FMT>::VPT; ++q) L.v[q] = vsrc[i * (2 * TCW_TILE_V / 16) + tid + q * TCW_THREADS];
+}
+
+template <int FMT>
+__device__ __forceinline__ void tcw_store(const TcwLoad<FMT>& L, unsigned char* stage, uint32_t a_off, int tid) {
+  constexpr int EPC = TcwLoad<FMT>::EPC;
+  unsigned char* aH = stage;
+  unsigned char* aL = aH + TCW_TILE_A;
+  unsigned char* vH = aL + TCW_TILE_A;  // V hi then lo, as in the image
+#pragma unroll
+  for (int q = 0; q < TcwLoad<FMT>::UPT; ++q) {
+    float f[EPC];
+#pragma unroll
+    for (int e = 0; e < EPC; ++e) f[e] = f64_to_f32_rn(L.a[q][e]);
+    uint4 h, w;
+    tc_split16<FMT>(f, &h, &w);
+    *reinterpret_cast<uint4*>(aH + a_off + q * (TCW_THREADS / 8) * 128) = h;
+    *reinterpret_cast<uint4*>(aL + a_off + q * (TCW_THREADS / 8) * 128) = w;
+  }
+#pragma unroll
+  for (int q = 0; q < TcwLoad<FMT>::VPT; ++q) reinterpret_cast<uint4*>(vH)[tid + q * TCW_THREADS] = L.v[q];
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w(Params P) {
+  constexpr int KA = TcFmt<FMT>::KA;
+  constexpr int EPC = TcwLoad<FMT>::EPC, UPT = TcwLoad<FMT>::UPT;
+  constexpr int NWQ = TCW_THREADS / 128;       // warps per TMEM lane quarter
+  constexpr int PART = TC_LMAX / NWQ;          // reflector sums each thread keeps
+  static_assert(KA == 8 * EPC, "an atom row is 8 chunks of 16 bytes");
+  static_assert(PART % 16 == 0, "TMEM loads of 16 columns");
   DevState* st = P.st;
   if (st->done) return;
   const int l = st->l;
@@ -201,7 +349,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_w(Params P) {
   const int64_t rbeg = seg * seg_rows, rend = min(mr, rbeg + seg_rows);
   extern __shared__ unsigned char tcw_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tcw_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* stg[2] = {base, base + TCW_STAGE};
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * TCW_STAGE);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   volatile int* s_fail = reinterpret_cast<volatile int*>(tslot + 1);
@@ -217,80 +364,79 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_w(Params P) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = *tslot;
-  // this thread's TMEM view: lanes of its warp quarter, its half of the reflectors
-  const uint32_t tview = taddr + ((uint32_t)((wp & 3) * 32) << 16) + (uint32_t)((wp >> 2) * HALF);
-  float wsum[HALF];
+  // this thread's TMEM view: lanes of its warp quarter, its part of the reflectors
+  const uint32_t tview = taddr + ((uint32_t)((wp & 3) * 32) << 16) + (uint32_t)((wp >> 2) * PART);
+  float wsum[PART];
 #pragma unroll
-  for (int t = 0; t < HALF; ++t) wsum[t] = 0.0f;
+  for (int t = 0; t < PART; ++t) wsum[t] = 0.0f;
+  // A units: column cq + (TCW_THREADS / 8) q of the tile, 16-byte chunk kg of the atom row
+  const int kg = tid & 7, cq = tid >> 3;
+  const double* colp[UPT];
+  bool colok[UPT];
+#pragma unroll
+  for (int q = 0; q < UPT; ++q) {
+    const int64_t col = c0 + cq + (TCW_THREADS / 8) * q;
+    colok[q] = col < P.n;
+    colp[q] = P.A + (colok[q] ? col : c0) * lda + ns + rbeg + kg * EPC;
+  }
+  const uint32_t a_off = (uint32_t)(cq * 128 + ((kg ^ (cq & 7)) << 4));
+  const uint4* vsrc = reinterpret_cast<const uint4*>(P.tc_vw + (rbeg / KA) * (2 * TCW_TILE_V));
   const uint32_t idesc = tc::idesc_f32acc(TCW_COLS, TC_LMAX, FMT);
   const int64_t nchunks = (rend - rbeg + KA - 1) / KA;
-  for (int64_t i = 0; i < nchunks; ++i) {
-    const int s = (int)(i & 1);
-    const int64_t r0 = rbeg + i * KA;  // relative to ns
-    double xa[NLA], xv[NLV];
+  int64_t issued = -1;
+  TcwLoad<FMT> buf[2];
+  tcw_load<FMT>(buf[0], colp, colok, 0, rbeg, rend, kg, vsrc, tid);
+  // one chunk per step; the loop body is unrolled twice so that the two load
+  // buffers are named registers
+  for (int64_t i0 = 0; i0 < nchunks; i0 += 2) {
 #pragma unroll
-    for (int q = 0; q < NLA; ++q) {
-      const int e = tid + q * TC_THREADS;
-      const int c = e / KA, kk = e % KA;
-      const int64_t col = c0 + c, rr = r0 + kk;
-      xa[q] = (col < P.n && rr < rend) ? P.A[col * lda + ns + rr] : 0.0;
-    }
+    for (int par = 0; par < 2; ++par) {
+      const int64_t i = i0 + par;
+      if (i < nchunks) {
+        const int s = par;  // = i & 1
+        if (i + 1 < nchunks) tcw_load<FMT>(buf[1 - par], colp, colok, i + 1, rbeg + (i + 1) * KA, rend, kg, vsrc, tid);
+        if (i >= 2) {  // the MMAs of chunk i - 2 have finished with this stage and accumulator
+          if (tid == 0 && !tc::mbar_wait(&bar[s], (uint32_t)(((i >> 1) - 1) & 1), TC_WAIT)) *s_fail = 1;
+          __syncthreads();
+          if (*s_fail) break;
+          tc::fence_after_sync();
 #pragma unroll
-    for (int q = 0; q < NLV; ++q) {
-      const int e = tid + q * TC_THREADS;
-      const int t = e / KA, kk = e % KA;
-      const int64_t rr = r0 + kk;
-      xv[q] = (t < l && rr < rend) ? vget(P.A, lda, ns, rr, t) : 0.0;
-    }
-    if (i >= 2) {  // the MMAs of chunk i - 2 have finished with this stage and accumulator
-      if (tid == 0 && !tc::mbar_wait(&bar[s], (uint32_t)(((i >> 1) - 1) & 1), TC_WAIT)) *s_fail = 1;
-      __syncthreads();
-      if (*s_fail) break;
-      tc::fence_after_sync();
+          for (int q = 0; q < PART / 16; ++q) {
+            float g[16];
+            tc::tmem_ld16(tview + (uint32_t)(s * TC_LMAX + q * 16), g);
 #pragma unroll
-      for (int q = 0; q < HALF / 16; ++q) {
-        float g[16];
-        tc::tmem_ld16(tview + (uint32_t)(s * TC_LMAX + q * 16), g);
+            for (int v = 0; v < 16; ++v) wsum[q * 16 + v] += g[v];
+          }
+        }
+        unsigned char* stage = base + s * TCW_STAGE;
+        tcw_store<FMT>(buf[par], stage, a_off, tid);
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          const uint32_t a_h = tc::smem_u32(stage), a_l = a_h + TCW_TILE_A;
+          const uint32_t v_h = a_l + TCW_TILE_A, v_l = v_h + TCW_TILE_V;
+          const uint32_t d = taddr + (uint32_t)(s * TC_LMAX);
+          // the small cross terms first: the truncation of each MMA's sum is
+          // then at the scale of the full sum only for the hi*hi terms
 #pragma unroll
-        for (int v = 0; v < 16; ++v) wsum[q * 16 + v] += g[v];
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t o = kk * 32;
+            tc_mma<FMT>(d, tc::sw128_desc(a_h + o), tc::sw128_desc(v_l + o), idesc, kk > 0 ? 1u : 0u);
+            tc_mma<FMT>(d, tc::sw128_desc(a_l + o), tc::sw128_desc(v_h + o), idesc, 1u);
+          }
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t o = kk * 32;
+            tc_mma<FMT>(d, tc::sw128_desc(a_h + o), tc::sw128_desc(v_h + o), idesc, 1u);
+          }
+          tc::mma_commit(&bar[s]);
+        }
+        issued = i;
       }
     }
-    unsigned char* aH = stg[s];
-    unsigned char* aL = aH + TCW_TILE_A;
-    unsigned char* vH = aL + TCW_TILE_A;
-    unsigned char* vL = vH + TCW_TILE_V;
-#pragma unroll
-    for (int q = 0; q < NLA; ++q) {
-      const int e = tid + q * TC_THREADS;
-      tc_put<FMT>(aH, aL, tc::sw128_off_e<ESZ>(e / KA, e % KA), f64_to_f32_rn(xa[q]));
-    }
-#pragma unroll
-    for (int q = 0; q < NLV; ++q) {
-      const int e = tid + q * TC_THREADS;
-      tc_put<FMT>(vH, vL, tc::sw128_off_e<ESZ>(e / KA, e % KA), f64_to_f32_rn(xv[q]));
-    }
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      const uint32_t a_h = tc::smem_u32(aH), a_l = tc::smem_u32(aL), v_h = tc::smem_u32(vH), v_l = tc::smem_u32(vL);
-      const uint32_t d = taddr + (uint32_t)(s * TC_LMAX);
-      // the small cross terms first: the truncation of each MMA's sum is then
-      // at the scale of the full sum only for the hi*hi terms
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint32_t o = kk * 32;
-        tc_mma<FMT>(d, tc::sw128_desc(a_h + o), tc::sw128_desc(v_l + o), idesc, kk > 0 ? 1u : 0u);
-        tc_mma<FMT>(d, tc::sw128_desc(a_l + o), tc::sw128_desc(v_h + o), idesc, 1u);
-      }
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint32_t o = kk * 32;
-        tc_mma<FMT>(d, tc::sw128_desc(a_h + o), tc::sw128_desc(v_h + o), idesc, 1u);
-      }
-      tc::mma_commit(&bar[s]);
-    }
+    if (*s_fail) break;
   }
   // the last one or two chunks are still in their accumulators; the commit of
   // the last chunk covers every MMA issued before it
@@ -299,23 +445,25 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_w(Params P) {
   __syncthreads();
   tc::fence_after_sync();
   if (*s_fail) {
+    // leave no MMA writing TMEM behind: a bounded wait for the last one issued
+    if (tid == 0 && issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), TC_WAIT);
     if (tid == 0 && atomicExch(&st->abort_flag, 1) == 0) st->diag_code = 4;
   } else {
     for (int64_t i = max((int64_t)0, last - 1); i <= last; ++i) {
 #pragma unroll
-      for (int q = 0; q < HALF / 16; ++q) {
+      for (int q = 0; q < PART / 16; ++q) {
         float g[16];
         tc::tmem_ld16(tview + (uint32_t)((int)(i & 1) * TC_LMAX + q * 16), g);
 #pragma unroll
         for (int v = 0; v < 16; ++v) wsum[q * 16 + v] += g[v];
       }
     }
-    // thread = trailing column (TMEM lane) and one half of its reflector sums
+    // thread = trailing column (TMEM lane) and one part of its reflector sums
     const int64_t col = c0 + (wp & 3) * 32 + lane;
     if (col < P.n) {
-      float4* o4 = reinterpret_cast<float4*>(P.Wt + ((seg + 1) * P.n + col) * TC_LMAX + (wp >> 2) * HALF);
+      float4* o4 = reinterpret_cast<float4*>(P.Wt + ((seg + 1) * P.n + col) * TC_LMAX + (wp >> 2) * PART);
 #pragma unroll
-      for (int v = 0; v < HALF / 4; ++v)
+      for (int v = 0; v < PART / 4; ++v)
         o4[v] = make_float4(wsum[4 * v], wsum[4 * v + 1], wsum[4 * v + 2], wsum[4 * v + 3]);
     }
   }
@@ -325,9 +473,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_w(Params P) {
 }
 
 // W = T^T (sum of the segments' V^T A22) per trailing column: one warp per
-// column; lanes t and t + 32 sum their reflector's segments in FP64, then
-// apply T (upper, from P.T) in FP32 and write Wt[col][64].
+// column; lanes t and t + 32 sum their reflector's segments in FP64, apply T
+// (upper, from P.T) in FP32 and write W's hi/lo operand image for the update
+// (128-column tiles from column ns + k; padding columns of the last tile are
+// zero).
+template <int FMT>
 __global__ void __launch_bounds__(TC_THREADS) k_tc_wsum(Params P) {
+  constexpr int ESZ = TcFmt<FMT>::ESZ, KA = TcFmt<FMT>::KA, NA = TcFmt<FMT>::NA;
   DevState* st = P.st;
   if (st->done) return;
   const int l = st->l;
@@ -347,126 +499,197 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_wsum(Params P) {
   (void)seg_rows;
   const int64_t gw = (int64_t)blockIdx.x * (TC_THREADS / 32) + wp;
   const int64_t nwarps = (int64_t)gridDim.x * (TC_THREADS / 32);
-  for (int64_t c = gw; c < n2; c += nwarps) {
-    const int64_t col = j0 + c;
-    double g0 = 0.0, g1 = 0.0;
-    for (int64_t sg = 0; sg < nseg; ++sg) {
-      const float* part = P.Wt + ((sg + 1) * P.n + col) * TC_LMAX;
-      g0 += (double)part[lane];
-      g1 += (double)part[lane + 32];
-    }
-    s_g[wp][lane] = (float)g0;
-    s_g[wp][lane + 32] = (float)g1;
-    __syncwarp();
+  const int64_t npad = (n2 + TCU_COLS - 1) / TCU_COLS * TCU_COLS;
+  for (int64_t c = gw; c < npad; c += nwarps) {
     float w0 = 0.0f, w1 = 0.0f;
-    for (int q = 0; q <= lane; ++q) w0 = fmaf(s_T[q][lane], s_g[wp][q], w0);
-    for (int q = 0; q <= lane + 32; ++q) w1 = fmaf(s_T[q][lane + 32], s_g[wp][q], w1);
-    P.Wt[col * TC_LMAX + lane] = w0;
-    P.Wt[col * TC_LMAX + lane + 32] = w1;
-    __syncwarp();
+    if (c < n2) {
+      const int64_t col = j0 + c;
+      double g0 = 0.0, g1 = 0.0;
+      for (int64_t sg = 0; sg < nseg; ++sg) {
+        const float* part = P.Wt + ((sg + 1) * P.n + col) * TC_LMAX;
+        g0 += (double)part[lane];
+        g1 += (double)part[lane + 32];
+      }
+      s_g[wp][lane] = (float)g0;
+      s_g[wp][lane + 32] = (float)g1;
+      __syncwarp();
+      for (int q = 0; q <= lane; ++q) w0 = fmaf(s_T[q][lane], s_g[wp][q], w0);
+      for (int q = 0; q <= lane + 32; ++q) w1 = fmaf(s_T[q][lane + 32], s_g[wp][q], w1);
+      __syncwarp();
+    }
+    unsigned char* img = P.tc_wi + (c / TCU_COLS) * (2 * NA * TC_ATOM);
+    const int cc = (int)(c % TCU_COLS);
+    tc_put<FMT>(img + (lane / KA) * TC_ATOM, img + (NA + lane / KA) * TC_ATOM,
+                tc::sw128_off_e<ESZ>(cc, lane % KA), w0);
+    tc_put<FMT>(img + ((lane + 32) / KA) * TC_ATOM, img + (NA + (lane + 32) / KA) * TC_ATOM,
+                tc::sw128_off_e<ESZ>(cc, (lane + 32) % KA), w1);
   }
 }
 
-// A22 tile (128 rows x 256 columns) -= V (rows x l) W (l x columns), K = 64
-// reflectors in NA atoms
+// A22 -= V W in tiles of 128 rows x 128 columns, K = 64 reflectors in NA
+// atoms.  Persistent: CTA b takes a contiguous, balanced range of tiles in
+// row-block-major order.  Thread 0 brings the operands in with bulk copies
+// from their images (V once per row block; W per tile into one of two
+// buffers, two tiles ahead) and issues the MMAs into one of two TMEM
+// accumulators (2 x 128 columns); meanwhile all warps stream the previous
+// tile through HBM (load A, subtract, store), 32 loads per thread in flight.
 template <int FMT>
-__global__ void __launch_bounds__(TC_THREADS) k_tc_update(Params P) {
-  constexpr int ESZ = TcFmt<FMT>::ESZ, KA = TcFmt<FMT>::KA, NA = TcFmt<FMT>::NA;
-  constexpr int TV = TCU_ROWS * 128;  // bytes of one atom of the V tile
-  constexpr int TW = TCU_COLS * 128;  // bytes of one atom of the W tile
+__global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
+  constexpr int NA = TcFmt<FMT>::NA;
+  constexpr int OPB = 2 * NA * TC_ATOM;  // bytes of one operand tile, hi and lo
+  static_assert(TCU_ROWS == 128 && TCU_COLS == 128, "tiles of 128 rows / columns");
   DevState* st = P.st;
   if (st->done) return;
   const int l = st->l;
   const int64_t ns = st->ns, j0 = ns + st->k;
   const int64_t n2 = P.n - j0, mr = P.m - ns, lda = P.lda;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
-  const int64_t r0 = (int64_t)blockIdx.x * TCU_ROWS;
-  const int64_t cb = j0 + (int64_t)blockIdx.y * TCU_COLS;
-  if (r0 >= mr || cb >= P.n) return;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
-    add_flops(st, KID_TRAIL_UPDATE, 2.0 * (double)mr * (double)n2 * l);
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_UPDATE, 2.0 * (double)mr * (double)n2 * l);
+  const int64_t nct = (n2 + TCU_COLS - 1) / TCU_COLS;
+  const int64_t ntiles = ((mr + TCU_ROWS - 1) / TCU_ROWS) * nct;
+  const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+  if (t0 >= t1) return;
   extern __shared__ unsigned char tcu_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tcu_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* vH = base;
-  unsigned char* vL = vH + NA * TV;
-  unsigned char* wH = vL + NA * TV;
-  unsigned char* wL = wH + NA * TW;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(wL + NA * TW);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  unsigned char* vbuf = base;        // hi atoms, then lo atoms
+  unsigned char* wbuf = base + OPB;  // two buffers of OPB bytes
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 3 * OPB);  // [0,1] MMA done, [2,3] W landed, [4] V landed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 5);
   volatile int* s_fail = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
-  if (wp == 0) tc::tmem_alloc(tslot, TCU_COLS);
+  const int64_t nloc = t1 - t0;
+  if (wp == 0) tc::tmem_alloc(tslot, 2 * TCU_COLS);
+  // copies issued / phases waited, per barrier (thread 0): a failed run still
+  // waits for every copy it started before the CTA's shared memory goes away
+  uint32_t w_iss[2] = {0u, 0u}, w_done[2] = {0u, 0u}, v_iss = 0u, v_done = 0u;
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
+#pragma unroll
+    for (int b = 0; b < 5; ++b) tc::mbar_init(&bar[b], 1);
     *s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // V for the first row block, W for the first two tiles
+    tc::mbar_expect_tx(&bar[4], OPB);
+    tc::bulk_g2s(vbuf, P.tc_vu + (t0 / nct) * OPB, OPB, &bar[4]);
+    ++v_iss;
+    for (int64_t i = 0; i < 2 && i < nloc; ++i) {
+      tc::mbar_expect_tx(&bar[2 + i], OPB);
+      tc::bulk_g2s(wbuf + i * OPB, P.tc_wi + ((t0 + i) % nct) * OPB, OPB, &bar[2 + i]);
+      ++w_iss[i];
+    }
   }
-  for (int e = tid; e < TCU_ROWS * 64; e += TC_THREADS) {
-    const int t = e >> 7, r = e & 127;
-    const int64_t rr = r0 + r;
-    const double v = (t < l && rr < mr) ? vget(P.A, lda, ns, rr, t) : 0.0;
-    tc_put<FMT>(vH, vL, (t / KA) * TV + tc::sw128_off_e<ESZ>(r, t % KA), f64_to_f32_rn(v));
-  }
-  for (int e = tid; e < TCU_COLS * 64; e += TC_THREADS) {
-    const int c = e >> 6, t = e & 63;
-    const int64_t col = cb + c;
-    const float w = (col < P.n && t < l) ? P.Wt[col * TC_LMAX + t] : 0.0f;
-    tc_put<FMT>(wH, wL, (t / KA) * TW + tc::sw128_off_e<ESZ>(c, t % KA), w);
-  }
-  tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = *tslot;
-  if (tid == 0) {
-    const uint32_t idesc = tc::idesc_f32acc(TCU_ROWS, TCU_COLS, FMT);
-    // cross terms first, then hi*hi (only those truncate at the scale of the sum)
+  const uint32_t idesc = tc::idesc_f32acc(TCU_ROWS, TCU_COLS, FMT);
+  const int q4 = wp & 3, half = wp >> 2;  // TMEM lane quarter and column half of this warp
+  int64_t cur_rb = -1, issued = -1;
+  for (int64_t i = 0; i <= nloc; ++i) {
+    if (i < nloc) {
+      const int64_t rb = (t0 + i) / nct;
+      if (tid == 0) {
+        bool ok = true;
+        if (rb != cur_rb && i > 0) {  // a new row block: the MMAs issued so far still read V
+          ok = tc::mbar_wait(&bar[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1), TC_WAIT);
+          if (ok) {
+            tc::mbar_expect_tx(&bar[4], OPB);
+            tc::bulk_g2s(vbuf, P.tc_vu + rb * OPB, OPB, &bar[4]);
+            ++v_iss;
+          }
+        }
+        if (ok && rb != cur_rb) {
+          ok = tc::mbar_wait(&bar[4], v_done & 1u, TC_WAIT);
+          if (ok) ++v_done;
+        }
+        if (ok) {
+          ok = tc::mbar_wait(&bar[2 + (i & 1)], (uint32_t)((i >> 1) & 1), TC_WAIT);
+          if (ok) ++w_done[i & 1];
+        }
+        if (ok) {
+          tc::fence_after_sync();
+          const uint32_t d = taddr + (uint32_t)((i & 1) * TCU_COLS);
+          const uint32_t vh = tc::smem_u32(vbuf), vl = vh + NA * TC_ATOM;
+          const uint32_t wh = tc::smem_u32(wbuf + (i & 1) * OPB), wl = wh + NA * TC_ATOM;
+          // cross terms first, then hi*hi (only those truncate at the scale of the sum)
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      const uint32_t v_h = tc::smem_u32(vH + a * TV), v_l = tc::smem_u32(vL + a * TV);
-      const uint32_t w_h = tc::smem_u32(wH + a * TW), w_l = tc::smem_u32(wL + a * TW);
+          for (int a = 0; a < NA; ++a) {
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint32_t o = kk * 32;
-        tc_mma<FMT>(taddr, tc::sw128_desc(v_h + o), tc::sw128_desc(w_l + o), idesc, (a > 0 || kk > 0) ? 1u : 0u);
-        tc_mma<FMT>(taddr, tc::sw128_desc(v_l + o), tc::sw128_desc(w_h + o), idesc, 1u);
-      }
-    }
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t o = a * TC_ATOM + kk * 32;
+              tc_mma<FMT>(d, tc::sw128_desc(vh + o), tc::sw128_desc(wl + o), idesc, (a > 0 || kk > 0) ? 1u : 0u);
+              tc_mma<FMT>(d, tc::sw128_desc(vl + o), tc::sw128_desc(wh + o), idesc, 1u);
+            }
+          }
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      const uint32_t v_h = tc::smem_u32(vH + a * TV), w_h = tc::smem_u32(wH + a * TW);
+          for (int a = 0; a < NA; ++a) {
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint32_t o = kk * 32;
-        tc_mma<FMT>(taddr, tc::sw128_desc(v_h + o), tc::sw128_desc(w_h + o), idesc, 1u);
-      }
-    }
-    tc::mma_commit(bar);
-    if (!tc::mbar_wait(bar, 0u, TC_WAIT)) *s_fail = 1;
-  }
-  __syncthreads();
-  tc::fence_after_sync();
-  if (*s_fail) {
-    if (tid == 0 && atomicExch(&st->abort_flag, 1) == 0) st->diag_code = 4;
-  } else {
-    // thread = row (TMEM lane of its quarter); warps w and w + 4 split the columns
-    const int q4 = wp & 3, half = wp >> 2;
-    const int64_t rr = r0 + q4 * 32 + lane;
-    double* a = P.A + ns + rr;
-    for (int cc = half * (TCU_COLS / 2); cc < (half + 1) * (TCU_COLS / 2); cc += 16) {
-      float v[16];
-      tc::tmem_ld16(taddr + ((uint32_t)(q4 * 32) << 16) + cc, v);
-      if (rr < mr) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int64_t col = cb + cc + i;
-          if (col < P.n) a[col * lda] -= (double)v[i];
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t o = a * TC_ATOM + kk * 32;
+              tc_mma<FMT>(d, tc::sw128_desc(vh + o), tc::sw128_desc(wh + o), idesc, 1u);
+            }
+          }
+          tc::mma_commit(&bar[i & 1]);
+          issued = i;
+        } else {
+          *s_fail = 1;
         }
       }
+      cur_rb = rb;
     }
+    if (i >= 1) {  // epilogue of tile i - 1
+      const int64_t pi = i - 1, t = t0 + pi, rb = t / nct, ct = t % nct;
+      if (tid == 0 && !*s_fail) {
+        if (!tc::mbar_wait(&bar[pi & 1], (uint32_t)((pi >> 1) & 1), TC_WAIT)) {
+          *s_fail = 1;
+        } else if (pi + 2 < nloc) {  // its W buffer is free: the tile two ahead
+          tc::mbar_expect_tx(&bar[2 + (pi & 1)], OPB);
+          tc::bulk_g2s(wbuf + (pi & 1) * OPB, P.tc_wi + ((t + 2) % nct) * OPB, OPB, &bar[2 + (pi & 1)]);
+          ++w_iss[pi & 1];
+        }
+      }
+      __syncthreads();
+      if (*s_fail) break;
+      tc::fence_after_sync();
+      const int64_t rr = rb * TCU_ROWS + q4 * 32 + lane;
+      const bool rok = rr < mr;
+      double* arow = P.A + ns + rr;
+      const uint32_t tb =
+          taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((pi & 1) * TCU_COLS + half * (TCU_COLS / 2));
+#pragma unroll 1
+      for (int c = 0; c < TCU_COLS / 2; c += 32) {
+        const int64_t cb = j0 + ct * TCU_COLS + half * (TCU_COLS / 2) + c;
+        double x[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) x[u] = (rok && cb + u < P.n) ? arow[(cb + u) * lda] : 0.0;
+        float v[32];
+        tc::tmem_ld16(tb + c, v);
+        tc::tmem_ld16(tb + c + 16, v + 16);
+        // FP32 -> FP64 on the integer pipe (exact): GB300's FP64 pipe, about
+        // two operations per clock per SM, is left the subtraction alone
+#pragma unroll
+        for (int u = 0; u < 32; ++u)
+          if (rok && cb + u < P.n) arow[(cb + u) * lda] = x[u] - f32_to_f64(v[u]);
+      }
+      tc::fence_before_sync();
+    }
+    __syncthreads();  // the epilogue has read its accumulator before the next MMAs reuse it
+    if (*s_fail) break;
+  }
+  if (*s_fail) {
+    // leave no copy or MMA in flight behind: bounded waits for the last ones
+    if (tid == 0) {
+      if (issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), TC_WAIT);
+      for (int b = 0; b < 2; ++b)
+        for (; w_done[b] < w_iss[b]; ++w_done[b])
+          if (!tc::mbar_wait(&bar[2 + b], w_done[b] & 1u, TC_WAIT)) break;
+      for (; v_done < v_iss; ++v_done)
+        if (!tc::mbar_wait(&bar[4], v_done & 1u, TC_WAIT)) break;
+    }
+    if (tid == 0 && atomicExch(&st->abort_flag, 1) == 0) st->diag_code = 4;
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (wp == 0) tc::tmem_dealloc(taddr, TCU_COLS);
+  if (wp == 0) tc::tmem_dealloc(taddr, 2 * TCU_COLS);
 }
 
 }  // namespace qrdm
