@@ -187,6 +187,13 @@ int configure(DeviceConfig* cfg) {
       return (int)e;
     // each CTA holds 2 x TCU_COLS TMEM columns of the 512
     const int tmem_cap = 512 / (2 * TCU_COLS);
+    // two BF16-form CTAs fit an SM's shared memory, registers (128 x 256)
+    // and TMEM; the CTAs never wait on one another, so a grid larger than
+    // what is resident only runs in more waves
+    int smem_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+      return (int)e;
+    if (2 * (tcu_smem<1>() + 1024) <= smem_sm) o1 = std::max(o1, 2);
     c.tcu_occ[0] = std::max(1, std::min(o1, tmem_cap));
     c.tcu_occ[1] = std::max(1, std::min(o2, tmem_cap));
   }
@@ -396,6 +403,7 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   P.tc_vw = (unsigned char*)(w + L.vw);
   P.tc_vu = (unsigned char*)(w + L.vu);
   P.tc_wi = (unsigned char*)(w + L.wi);
+  P.tc_al = ((lda & 1) == 0 && ((uintptr_t)dA & 15) == 0) ? 1 : 0;
   {
     // Wt and the W GEMM's segment partials share the W-partials buffer
     const size_t wp_bytes = std::max((size_t)WCHUNKS * k_max * (size_t)n * sizeof(double),

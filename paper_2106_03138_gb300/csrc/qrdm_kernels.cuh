@@ -101,6 +101,7 @@ struct Params {
   unsigned char* tc_vw; // tensor-core forms: V's operand image for the W pass
   unsigned char* tc_vu; // V's operand image for the update
   unsigned char* tc_wi; // W's operand image for the update
+  int32_t tc_al;        // 1: A and lda allow 16-byte loads from an even row (the W pass starts its rows there)
   // optional trace
   StepRecord* trace;
   int32_t* traceJ;

@@ -211,6 +211,11 @@ __device__ __forceinline__ void tc_segments(int64_t mr, int nseg_max, int ka, in
   *seg_rows = sr;
 }
 
+// The W pass reads A22 in 16-byte units when it can: with an even lda and a
+// 16-byte-aligned A, its rows start at the even row ns - o (o = ns mod 2);
+// row ns - 1 meets a zero row of V's image, so it adds nothing.
+__device__ __forceinline__ int tc_shift(const Params& P, int64_t ns) { return (P.tc_al && (ns & 1)) ? 1 : 0; }
+
 // V's operand images, one element per thread (rows padded with zeros to the
 // next 128): Vw for the W pass (chunk of KA rows: reflector t is the tile's
 // row, the chunk's rows its K) and Vu for the update (block of 128 rows: row
@@ -223,17 +228,18 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_vimg(Params P) {
   const int l = st->l;
   const int64_t ns = st->ns, mr = P.m - ns;
   if (l <= 0 || st->k >= P.n - ns || mr <= 0) return;
-  const int64_t pad = (mr + 127) / 128 * 128;
+  const int o = tc_shift(P, ns);  // Vw row r holds V row r - o
+  const int64_t pad = (mr + o + 127) / 128 * 128;
   const int64_t total = pad * TC_LMAX;
   for (int64_t e = (int64_t)blockIdx.x * TC_THREADS + threadIdx.x; e < total; e += (int64_t)gridDim.x * TC_THREADS) {
     const int t = (int)(e / pad);
     const int64_t r = e % pad;
-    const double v = (t < l && r < mr) ? vget(P.A, P.lda, ns, r, t) : 0.0;
-    const float f = f64_to_f32_rn(v);
+    const double vu = (t < l && r < mr) ? vget(P.A, P.lda, ns, r, t) : 0.0;
+    const double vw = (o == 0) ? vu : ((t < l && r >= 1 && r - 1 < mr) ? vget(P.A, P.lda, ns, r - 1, t) : 0.0);
     unsigned char* w = P.tc_vw + (r / KA) * (2 * TC_LMAX * 128);
-    tc_put<FMT>(w, w + TC_LMAX * 128, tc::sw128_off_e<ESZ>(t, (int)(r % KA)), f);
+    tc_put<FMT>(w, w + TC_LMAX * 128, tc::sw128_off_e<ESZ>(t, (int)(r % KA)), f64_to_f32_rn(vw));
     unsigned char* u = P.tc_vu + (r / 128) * (2 * NA * TC_ATOM) + (t / KA) * TC_ATOM;
-    tc_put<FMT>(u, u + NA * TC_ATOM, tc::sw128_off_e<ESZ>((int)(r % 128), t % KA), f);
+    tc_put<FMT>(u, u + NA * TC_ATOM, tc::sw128_off_e<ESZ>((int)(r % 128), t % KA), f64_to_f32_rn(vu));
   }
 }
 
@@ -292,14 +298,27 @@ struct TcwLoad {
 // issue the global loads of chunk i (rows r0 .. r0 + KA relative to ns)
 template <int FMT>
 __device__ __forceinline__ void tcw_load(TcwLoad<FMT>& L, const double* const* colp, const bool* colok, int64_t i,
-                                         int64_t r0, int64_t rend, int kg, const uint4* vsrc, int tid) {
+                                         int64_t r0, int64_t rend, int kg, const uint4* vsrc, int tid, bool al) {
   constexpr int KA = TcFmt<FMT>::KA, EPC = TcwLoad<FMT>::EPC;
   const bool full = r0 + KA <= rend;
+  if (full && al) {  // 16-byte loads: the unit starts at an even row of an aligned column
 #pragma unroll
-  for (int q = 0; q < TcwLoad<FMT>::UPT; ++q) {
-    const double* src = colp[q] + i * KA;
+    for (int q = 0; q < TcwLoad<FMT>::UPT; ++q) {
+      const double2* src = reinterpret_cast<const double2*>(colp[q] + i * KA);
 #pragma unroll
-    for (int e = 0; e < EPC; ++e) L.a[q][e] = (colok[q] && (full || r0 + kg * EPC + e < rend)) ? src[e] : 0.0;
+      for (int e = 0; e < EPC / 2; ++e) {
+        const double2 d = colok[q] ? src[e] : make_double2(0.0, 0.0);
+        L.a[q][2 * e] = d.x;
+        L.a[q][2 * e + 1] = d.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < TcwLoad<FMT>::UPT; ++q) {
+      const double* src = colp[q] + i * KA;
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) L.a[q][e] = (colok[q] && (full || r0 + kg * EPC + e < rend)) ? src[e] : 0.0;
+    }
   }
 #pragma unroll
   for (int q = 0; q < TcwLoad<FMT>::VPT; ++q) L.v[q] = vsrc[i * (2 * TCW_TILE_V / 16) + tid + q * TCW_THREADS];
@@ -336,17 +355,20 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w(Params P) {
   DevState* st = P.st;
   if (st->done) return;
   const int l = st->l;
-  const int64_t ns = st->ns, j0 = ns + st->k;
-  const int64_t n2 = P.n - j0, mr = P.m - ns, lda = P.lda;
-  if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  const int64_t j0 = st->ns + st->k, n2 = P.n - j0, lda = P.lda;
+  if (l <= 0 || n2 <= 0 || P.m - st->ns <= 0) return;
+  // rows from the even row ns - o (see tc_shift); row 0 meets V's zero row
+  const int o = tc_shift(P, st->ns);
+  const int64_t ns = st->ns - o, mr = P.m - ns;
   const int64_t c0 = j0 + (int64_t)blockIdx.x * TCW_COLS;
   int64_t nseg, seg_rows;
   tc_segments(mr, P.tc_nseg, TC_SEG_ALIGN, &nseg, &seg_rows);
   const int64_t seg = blockIdx.y;
   if (c0 >= P.n || seg >= nseg) return;
   if (blockIdx.x == 0 && seg == 0 && threadIdx.x == 0)
-    add_flops(st, KID_TRAIL_W, 2.0 * (double)mr * (double)n2 * l);
+    add_flops(st, KID_TRAIL_W, 2.0 * (double)(mr - o) * (double)n2 * l);
   const int64_t rbeg = seg * seg_rows, rend = min(mr, rbeg + seg_rows);
+  const bool al = P.tc_al != 0;
   extern __shared__ unsigned char tcw_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tcw_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * TCW_STAGE);
@@ -385,7 +407,7 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w(Params P) {
   const int64_t nchunks = (rend - rbeg + KA - 1) / KA;
   int64_t issued = -1;
   TcwLoad<FMT> buf[2];
-  tcw_load<FMT>(buf[0], colp, colok, 0, rbeg, rend, kg, vsrc, tid);
+  tcw_load<FMT>(buf[0], colp, colok, 0, rbeg, rend, kg, vsrc, tid, al);
   // one chunk per step; the loop body is unrolled twice so that the two load
   // buffers are named registers
   for (int64_t i0 = 0; i0 < nchunks; i0 += 2) {
@@ -394,7 +416,8 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w(Params P) {
       const int64_t i = i0 + par;
       if (i < nchunks) {
         const int s = par;  // = i & 1
-        if (i + 1 < nchunks) tcw_load<FMT>(buf[1 - par], colp, colok, i + 1, rbeg + (i + 1) * KA, rend, kg, vsrc, tid);
+        if (i + 1 < nchunks)
+          tcw_load<FMT>(buf[1 - par], colp, colok, i + 1, rbeg + (i + 1) * KA, rend, kg, vsrc, tid, al);
         if (i >= 2) {  // the MMAs of chunk i - 2 have finished with this stage and accumulator
           if (tid == 0 && !tc::mbar_wait(&bar[s], (uint32_t)(((i >> 1) - 1) & 1), TC_WAIT)) *s_fail = 1;
           __syncthreads();
@@ -495,7 +518,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_wsum(Params P) {
   }
   __syncthreads();
   int64_t nseg, seg_rows;
-  tc_segments(mr, P.tc_nseg, TC_SEG_ALIGN, &nseg, &seg_rows);
+  tc_segments(mr + tc_shift(P, ns), P.tc_nseg, TC_SEG_ALIGN, &nseg, &seg_rows);  // the W pass's segments
   (void)seg_rows;
   const int64_t gw = (int64_t)blockIdx.x * (TC_THREADS / 32) + wp;
   const int64_t nwarps = (int64_t)gridDim.x * (TC_THREADS / 32);

@@ -134,3 +134,24 @@ def test_merged_fp64_form_matches_the_oracle(shape, tau, delta, kmax):
     res, orth = factorization_errors(A, g["A"], g["htau"], g["perm"])
     assert res <= 1e-13 and orth <= 1e-13, (res, orth)
     print(f"\n[precision 4] {shape}: residual {res:.2e}, diverged at {rep['diverged_at']}")
+
+
+@pytest.mark.parametrize("precision", [2, 3])
+@pytest.mark.parametrize("m,n,lda,kmax", [(515, 301, 515, 64), (640, 384, 640, 63), (515, 301, 517, 63)])
+def test_tensor_core_forms_unaligned_storage(m, n, lda, kmax, precision):
+    """An odd leading dimension (the W pass then reads A in 8-byte units) and
+    an even one with odd panel starts (k_max = 63: 16-byte units from the even
+    row ns - 1): each gives a factorization of the precision class."""
+    A = inputs.from_spectrum(m, n, np.geomspace(1.0, 1e-3, min(m, n)), 23 + m)
+    buf = torch.zeros((n, lda), dtype=torch.float64, device="cuda")
+    buf[:, :m] = torch.as_tensor(A.T, device="cuda")
+    dA = buf.t()[:m, :]  # column-major view, stride(1) = lda
+    f = q.factor(dA, 0.15, 0.9, kmax, precision=precision, trace=True)
+    torch.cuda.synchronize()
+    Ag = dA.cpu().numpy()
+    res, orth = factorization_errors(A, Ag, f.htau.cpu().numpy(), f.perm.cpu().numpy().astype(np.int64))
+    odd_starts = int(np.sum(np.asarray(f.trace["ns"]) % 2))
+    print(f"\n[precision {precision}] {m}x{n} lda {lda} k_max {kmax}: residual {res:.2e}, orth {orth:.1e}, "
+          f"steps {f.nsteps}, odd panel starts {odd_starts}")
+    assert res <= BOUNDS[precision][0], res
+    assert orth <= 1e-13, orth
