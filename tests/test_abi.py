@@ -59,6 +59,14 @@ def test_workspace_size_and_argument_checks(lib):
     n1 = b.qrdm_workspace_size(256, 256, 32)
     n2 = b.qrdm_workspace_size(4096, 4096, 64)
     assert 0 < n1 < n2
+    # the shapes the header promises to the fixed scratch of qrdm_factor_noalloc
+    scratch = 32 << 20
+    assert b.qrdm_workspace_size(4096, 4096, 32) <= scratch
+    assert b.qrdm_workspace_size(2048, 2048, 64) <= scratch
+    # blocks of at most 64 columns also hold the tensor-core forms' operand
+    # images (512 B per padded row of V twice and per padded column of W)
+    img = (2 * (4096 + 256) + (4096 + 256)) * 512
+    assert b.qrdm_workspace_size(4096, 4096, 64) >= img
     with pytest.raises(ValueError):
         b.qrdm_workspace_size(-1, 4, 4)
     with pytest.raises(ValueError):
