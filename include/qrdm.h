@@ -102,7 +102,8 @@ typedef struct qrdm_opts {
      reflectors, W = T^T V^T A22 and A22 -= V W, operands converted on load
      (FP64 -> FP32 -> hi + lo BF16; hi*hi + hi*lo + lo*hi).  Requires
      k_max <= 64 (QRDM_ERR_UNSUPPORTED otherwise); eps1 = max(eps1,
-     2^-16 * sqrt(n)).  The candidate Gram matrix is FP32 as in 1.
+     2^-16 * sqrt(n)).  The candidate Gram matrix is computed on the tensor
+     cores with the same split (partials per 64-row chunk summed in FP64).
      3: as 2 with 3xTF32 (kind::tf32; hi, lo TF32, rounded to nearest): an
      FP32-class form on the tensor cores, about 2^-21 relative per product;
      eps1 = max(eps1, 8 * 2^-21 * sqrt(n)).

@@ -109,6 +109,10 @@ int configure(DeviceConfig* cfg) {
     return (int)e;
   if ((e = cudaFuncSetAttribute(k_tc_tbuild, cudaFuncAttributeMaxDynamicSharedMemorySize, TCB_SMEM)) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(k_tc_gram<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCG_SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_tc_gram<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCG_SMEM)) != cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(k_tc_w<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCW_SMEM)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_tc_w<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCW_SMEM)) != cudaSuccess)
@@ -535,10 +539,16 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     cudaError_t e;
     if ((e = run(QRDM_K_SELECT, [&] { k_select<<<1, SEL_THREADS, 0, stream>>>(P); })) != cudaSuccess) return e;
     if ((e = run(QRDM_K_GRAM, [&] {
-           if (gram32)
+           if (merged && !merged64) {  // the tensor-core forms: the Gram on tcgen05 too
+             if (tf32)
+               k_tc_gram<2><<<P.gram_chunks, TC_THREADS, TCG_SMEM, stream>>>(P);
+             else
+               k_tc_gram<1><<<P.gram_chunks, TC_THREADS, TCG_SMEM, stream>>>(P);
+           } else if (gram32) {
              k_gram32<<<P.gram_chunks, 256, gram_smem, stream>>>(P);
-           else
+           } else {
              k_gram<<<P.gram_chunks, 256, gram_smem, stream>>>(P);
+           }
          })) != cudaSuccess)
       return e;
     if ((e = run(QRDM_K_GRAM_REDUCE, [&] { k_gram_reduce<<<gred_grid, 256, 0, stream>>>(P); })) != cudaSuccess)

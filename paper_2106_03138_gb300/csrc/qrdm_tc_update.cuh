@@ -495,6 +495,162 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w(Params P) {
   if (wp == 0) tc::tmem_dealloc(taddr, 2 * TC_LMAX);
 }
 
+// The candidate Gram matrix G = C^T C of the tensor-core forms (C: the kc <=
+// 64 candidate columns of rows ns..m-1, gathered through P.cols).  CTA c
+// takes the 64-row chunks c, c + gridDim.x, ... as the FP64/FP32 Gram kernels
+// do, so k_gram_reduce sums the same partials.  Per K atom of rows the
+// candidates are split into one hi/lo tile (candidate a = tile row a, rows of
+// A along K); the tile is both operands: D (128 x 64) += X X^T, of which rows
+// and columns a, b < kc are used.  As in the W pass, each atom has its own
+// TMEM accumulator (two alternate) that the warps add into FP32 registers.
+constexpr int TCG_TILE = 128 * 128;  // bytes of one operand tile (128 rows x one atom)
+constexpr int TCG_SMEM = 1024 + 2 * 2 * TCG_TILE + 64;
+
+template <int FMT>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gram(Params P) {
+  constexpr int ESZ = TcFmt<FMT>::ESZ, KA = TcFmt<FMT>::KA;
+  constexpr int EPC = 16 / ESZ;
+  constexpr int SUB = GRAM_ROWS / KA;  // K atoms per 64-row chunk
+  static_assert(GRAM_ROWS % KA == 0, "chunks of whole atoms");
+  DevState* st = P.st;
+  if (st->done) return;
+  const int kc = st->kc;
+  if (kc <= 1) return;
+  const int64_t ns = st->ns, m = P.m, mr = m - ns, lda = P.lda;
+  const int64_t nchunks = (mr + GRAM_ROWS - 1) / GRAM_ROWS;
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(P.st, KID_GRAM, (double)mr * kc * (kc + 1.0));
+  if ((int64_t)blockIdx.x >= nchunks) return;
+  const int64_t my_chunks = (nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x;
+  const int64_t nsteps = my_chunks * SUB;
+  extern __shared__ unsigned char tcg_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)tcg_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 4 * TCG_TILE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(tslot + 1);
+  const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
+  if (wp == 0) tc::tmem_alloc(tslot, 2 * TC_LMAX);
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    *s_fail = 0;
+  }
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = *tslot;
+  const bool drains = (wp & 3) < 2;  // TMEM lanes 0..63 hold the candidates' rows of D
+  const uint32_t tview = taddr + ((uint32_t)((wp & 3) * 32) << 16) + (uint32_t)((wp >> 2) * 32);
+  float gsum[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) gsum[t] = 0.0f;
+  // units: candidate a = (tid >> 3) + 32 q (q = 0, 1), 16-byte chunk kg of the atom row
+  const int kg = tid & 7;
+  int64_t colb[2];
+  bool aok[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int a = (tid >> 3) + 32 * q;
+    aok[q] = a < kc;
+    colb[q] = aok[q] ? (int64_t)P.cols[a] * lda : 0;
+  }
+  const uint32_t idesc = tc::idesc_f32acc(128, TC_LMAX, FMT);
+  int64_t issued = -1;
+  for (int64_t i = 0; i < nsteps; ++i) {
+    const int s = (int)(i & 1);
+    const int64_t chunk = blockIdx.x + (i / SUB) * gridDim.x;
+    const int64_t r0 = ns + chunk * GRAM_ROWS + (i % SUB) * KA;  // absolute first row of the atom
+    double xa[2][EPC];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) {
+        const int64_t r = r0 + kg * EPC + e;
+        xa[q][e] = (aok[q] && r < m) ? P.A[colb[q] + r] : 0.0;
+      }
+    }
+    if (i >= 2) {  // the MMAs of step i - 2 have finished with this stage and accumulator
+      if (tid == 0 && !tc::mbar_wait(&bar[s], (uint32_t)(((i >> 1) - 1) & 1), TC_WAIT)) *s_fail = 1;
+      __syncthreads();
+      if (*s_fail) break;
+      tc::fence_after_sync();
+      if (drains) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          float g[16];
+          tc::tmem_ld16(tview + (uint32_t)(s * TC_LMAX + q * 16), g);
+#pragma unroll
+          for (int v = 0; v < 16; ++v) gsum[q * 16 + v] += g[v];
+        }
+      }
+    }
+    unsigned char* xH = base + s * 2 * TCG_TILE;
+    unsigned char* xL = xH + TCG_TILE;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int a = (tid >> 3) + 32 * q;
+      float f[EPC];
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) f[e] = f64_to_f32_rn(xa[q][e]);
+      uint4 h, w;
+      tc_split16<FMT>(f, &h, &w);
+      const uint32_t off = (uint32_t)(a * 128 + ((kg ^ (a & 7)) << 4));
+      *reinterpret_cast<uint4*>(xH + off) = h;
+      *reinterpret_cast<uint4*>(xL + off) = w;
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t x_h = tc::smem_u32(xH), x_l = x_h + TCG_TILE;
+      const uint32_t d = taddr + (uint32_t)(s * TC_LMAX);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t o = kk * 32;
+        tc_mma<FMT>(d, tc::sw128_desc(x_h + o), tc::sw128_desc(x_l + o), idesc, kk > 0 ? 1u : 0u);
+        tc_mma<FMT>(d, tc::sw128_desc(x_l + o), tc::sw128_desc(x_h + o), idesc, 1u);
+      }
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t o = kk * 32;
+        tc_mma<FMT>(d, tc::sw128_desc(x_h + o), tc::sw128_desc(x_h + o), idesc, 1u);
+      }
+      tc::mma_commit(&bar[s]);
+    }
+    issued = i;
+  }
+  const int64_t last = nsteps - 1;
+  if (tid == 0 && !*s_fail && !tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), TC_WAIT)) *s_fail = 1;
+  __syncthreads();
+  tc::fence_after_sync();
+  if (*s_fail) {
+    if (tid == 0 && issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), TC_WAIT);
+    if (tid == 0 && atomicExch(&st->abort_flag, 1) == 0) st->diag_code = 4;
+  } else if (drains) {
+    for (int64_t i = max((int64_t)0, last - 1); i <= last; ++i) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float g[16];
+        tc::tmem_ld16(tview + (uint32_t)((int)(i & 1) * TC_LMAX + q * 16), g);
+#pragma unroll
+        for (int v = 0; v < 16; ++v) gsum[q * 16 + v] += g[v];
+      }
+    }
+    // thread = candidate a, columns b of its half: the upper triangle a <= b < kc
+    const int a = (wp & 3) * 32 + lane;
+    double* out = P.Gp + (int64_t)blockIdx.x * P.kmax * P.kmax;
+#pragma unroll
+    for (int v = 0; v < 32; ++v) {
+      const int b = (wp >> 2) * 32 + v;
+      if (a <= b && b < kc) out[b * (b + 1) / 2 + a] = f32_to_f64(gsum[v]);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (wp == 0) tc::tmem_dealloc(taddr, 2 * TC_LMAX);
+}
+
 // W = T^T (sum of the segments' V^T A22) per trailing column: one warp per
 // column; lanes t and t + 32 sum their reflector's segments in FP64, apply T
 // (upper, from P.T) in FP32 and write W's hi/lo operand image for the update
