@@ -1,11 +1,14 @@
 // Thin wrappers over the sm_100-family tensor-core instructions (tcgen05,
-// TMEM, mbarrier) used by the split-BF16 kernels, written from the PTX ISA.
+// TMEM, mbarrier, bulk async copies) used by the split-BF16 and 3xTF32
+// kernels, written from the PTX ISA.
 //
 // Operand tiles in shared memory use the K-major 128-byte-swizzle layout: a
-// tile of R rows x 64 BF16 (one 128-byte row each) stores element (r, k) at
-//   r * 128 + (((k / 8) ^ (r % 8)) * 16) + (k % 8) * 2
+// tile of R rows x 128 bytes (64 BF16 or 32 TF32 elements of K) stores the
+// byte b = k * size of element (r, k) at
+//   r * 128 + (((b / 16) ^ (r % 8)) * 16) + b % 16
 // from a 1024-byte-aligned base; 8-row groups are 1024 bytes apart (SBO).
-// An MMA step over K = 16 elements starts 32 bytes further into the rows.
+// An MMA step over K = 16 BF16 or 8 TF32 elements starts 32 bytes further
+// into the rows.
 #pragma once
 
 #include <cuda_bf16.h>

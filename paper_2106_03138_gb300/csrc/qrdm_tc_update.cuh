@@ -17,6 +17,11 @@
 // A stays FP64 in HBM.  V and W, small and read by many CTAs, are split once
 // per step into images laid out exactly as the MMA's shared-memory tiles
 // (K-major, 128-byte swizzle), which the kernels copy without conversion.
+// The candidate Gram matrix of the DM selection (a3) runs on the tensor cores
+// with the same split (k_tc_gram).  Where many MMAs add into one result (the
+// W pass and the Gram, K = rows), each K atom gets its own TMEM accumulator,
+// summed in FP32 registers with round-to-nearest: the tensor core's own FP32
+// accumulation truncates.
 #pragma once
 
 #include "qrdm_kernels.cuh"
