@@ -1114,9 +1114,9 @@ __device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int6
   g.cols = GEMM_THREADS / w_tg(l);
   g.nct = (n2 + g.cols - 1) / g.cols;
   int cap = P.wchunks;
-  if (narrow_c0 >= 0 && n2 <= NARROW_COLS) {
-    const int64_t fit = (int64_t)P.wchunks * P.n / NARROW_COLS;
-    cap = (int)max((int64_t)1, min((int64_t)NARROW_WCHUNKS, fit));
+  const int64_t fit = (int64_t)P.wchunks * P.n / NARROW_COLS;  // packed chunks the buffer holds
+  if (narrow_c0 >= 0 && n2 <= NARROW_COLS && fit >= 1) {
+    cap = (int)min((int64_t)NARROW_WCHUNKS, fit);
     g.qstride = (int64_t)P.kmax * NARROW_COLS;
     g.tstride = NARROW_COLS;
     g.cofs = narrow_c0;
