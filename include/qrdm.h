@@ -105,7 +105,8 @@ typedef struct qrdm_opts {
      2^-16 * sqrt(n)).  The candidate Gram matrix is computed on the tensor
      cores with the same split (partials per 64-row chunk summed in FP64).
      3: as 2 with 3xTF32 (kind::tf32; hi, lo TF32, rounded to nearest): an
-     FP32-class form on the tensor cores, about 2^-21 relative per product;
+     FP32-class form on the tensor cores: a product is exact to about 2^-20
+     relative at worst (2^-24 typical), split-BF16x3 to 3 * 2^-16;
      eps1 = max(eps1, 8 * 2^-21 * sqrt(n)).
      In 2 and 3 each chunk of 64 rows of the W product has its own TMEM
      accumulator, summed in FP32 registers with round-to-nearest.

@@ -12,8 +12,9 @@
 // sub-panel: the form is HBM-bound, and the merge divides its traffic by the
 // number of sub-panels.  Operands are split on load: FP64 -> FP32 (round to
 // nearest, integer pipe) -> x = hi + lo with hi, lo BF16 (precision 2) or
-// TF32 (precision 3); each product uses hi*hi + hi*lo + lo*hi (lo*lo dropped:
-// about 2^-17 relative for BF16, 2^-21 for TF32), FP32 accumulation in TMEM.
+// TF32 (precision 3); each product uses hi*hi + hi*lo + lo*hi (lo*lo
+// dropped), exact to 3 * 2^-16 relative for BF16 and about 2^-20 for TF32 at
+// worst (2^-18.6 and 2^-24 typical); FP32 accumulation in TMEM.
 // A stays FP64 in HBM.  V and W, small and read by many CTAs, are split once
 // per step into images laid out exactly as the MMA's shared-memory tiles
 // (K-major, 128-byte swizzle), which the kernels copy without conversion.
