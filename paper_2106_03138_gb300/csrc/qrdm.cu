@@ -58,12 +58,15 @@ Layout make_layout(int64_t m, int64_t n, int kmax) {
   off = up(off + kk * sizeof(double));
   L.T = off;
   off = up(off + (size_t)KMAX * KMAX * sizeof(double));
-  L.Wp = off;  // also holds the merged form's Wt (n x 64 floats)
-  off = up(off + std::max((size_t)WCHUNKS * kmax * nn * sizeof(double), nn * (size_t)TC_LMAX * sizeof(float)));
+  // also holds the tensor-core forms' FP32 segment partials (Wt): TC_NSEG_MAX
+  // segments after one unused n x 64 block
+  const bool tc = kmax <= TC_LMAX;
+  L.Wp = off;
+  off = up(off + std::max((size_t)WCHUNKS * kmax * nn * sizeof(double),
+                          tc ? (size_t)(TC_NSEG_MAX + 1) * nn * TC_LMAX * sizeof(float) : (size_t)0));
   L.W = off;
   off = up(off + (size_t)kmax * nn * sizeof(double));
   // operand images of the tensor-core forms (blocks of at most 64 columns)
-  const bool tc = kmax <= TC_LMAX;
   const size_t mm = (size_t)(m > 0 ? m : 1);
   off = (off + 1023) / 1024 * 1024;
   L.vw = off;
@@ -410,11 +413,11 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   P.tc_wi = (unsigned char*)(w + L.wi);
   P.tc_al = ((lda & 1) == 0 && ((uintptr_t)dA & 15) == 0) ? 1 : 0;
   {
-    // Wt and the W GEMM's segment partials share the W-partials buffer
-    const size_t wp_bytes = std::max((size_t)WCHUNKS * k_max * (size_t)n * sizeof(double),
-                                     (size_t)n * TC_LMAX * sizeof(float));
+    // the W GEMM's segment partials live in the W-partials region after one
+    // n x 64 block: as many segments as the region holds, at most TC_NSEG_MAX
+    const size_t wp_bytes = L.W - L.Wp;
     const int64_t fit = (int64_t)(wp_bytes / ((size_t)n * TC_LMAX * sizeof(float))) - 1;
-    P.tc_nseg = (int32_t)std::max<int64_t>(1, std::min<int64_t>(16, fit));
+    P.tc_nseg = (int32_t)std::max<int64_t>(1, std::min<int64_t>(TC_NSEG_MAX, fit));
   }
   P.W = (double*)(w + L.W);
   const int sms = cfg.sms;

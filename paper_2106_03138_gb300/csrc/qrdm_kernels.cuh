@@ -96,7 +96,7 @@ struct Params {
   int32_t w_units;      // target work units of the W phase (same in k_trail_w and k_trail_wreduce)
   int32_t mixed;        // 1: FP32-class trailing update and Gram (geometry of k_trail_w32)
   int32_t merged;       // 1: sub-panel updates stop at the panel's end; one merged trailing update per step
-  float* Wt;            // merged form: [n][64] T^T V^T A22 per column, then tc_nseg segment partials (aliases Wp)
+  float* Wt;            // tensor-core forms: V^T A22 of row segment s at Wt + (s + 1) n 64, [column][64] (aliases Wp)
   int32_t tc_nseg;      // merged form: most row segments of the W GEMM
   unsigned char* tc_vw; // tensor-core forms: V's operand image for the W pass
   unsigned char* tc_vu; // V's operand image for the update

@@ -56,6 +56,7 @@ constexpr int tcu_smem() {
 constexpr int TCV_ROWS_MIN = 128;  // rows per CTA of k_tc_vtv (at least)
 constexpr int TCV_CHUNKS = 128;    // at most this many row chunks (partial V^T V in the Gram partials buffer)
 constexpr int TC_ATOM = 128 * 128;  // bytes of one K atom of a 128-row operand tile
+constexpr int TC_NSEG_MAX = 16;     // most row segments of the W pass (FP32 partials n x 64 each)
 
 // bytes of one operand image over `rows` rows (or columns), either format:
 // V for the W pass (per K chunk: 64 reflector rows x 128 B, hi then lo), V for

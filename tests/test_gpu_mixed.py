@@ -155,3 +155,22 @@ def test_tensor_core_forms_unaligned_storage(m, n, lda, kmax, precision):
           f"steps {f.nsteps}, odd panel starts {odd_starts}")
     assert res <= BOUNDS[precision][0], res
     assert orth <= 1e-13, orth
+
+
+@pytest.mark.parametrize("precision", [2, 3])
+@pytest.mark.parametrize("kmax", [2, 3, 16])
+def test_tensor_core_forms_small_blocks(kmax, precision):
+    """Blocks of a few columns: the W pass's segment partials must fit the
+    workspace whatever k_max is (their region is sized for the tensor-core
+    forms, not from k_max)."""
+    m, n, r = 600, 400, 150
+    A = inputs.from_spectrum(m, n, inputs.sigma_gap(n, r), 77)
+    dA = q.colmajor(A)
+    f = q.factor(dA, 0.15, 0.9, kmax, precision=precision)
+    torch.cuda.synchronize()
+    res, orth = factorization_errors(A, dA.cpu().numpy(), f.htau.cpu().numpy(), f.perm.cpu().numpy().astype(np.int64))
+    print(f"\n[precision {precision}] k_max {kmax}: residual {res:.2e}, orth {orth:.1e}, rank_colmax {f.rank_colmax}, "
+          f"steps {f.nsteps}")
+    assert res <= BOUNDS[precision][0], res
+    assert orth <= 1e-13, orth
+    assert r <= f.rank_colmax <= r + kmax, (f.rank_colmax, r)
