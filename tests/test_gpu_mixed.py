@@ -1,16 +1,20 @@
 """The reduced-precision forms against the FP64 oracle and the plain FP64
-form: precision=1 (FP32-class: trailing update and candidate Gram matrix in
-FP32 from FP64 storage) and precision=2 (split-BF16x3 on the tensor cores:
-one merged trailing update per step with tcgen05, FP32 accumulation in
-TMEM); panel, norms and rank stay FP64 in both.  Its results are not expected to match the FP64 oracle digit for digit,
-so each case reports its error against the oracle and checks the bounds of
-this precision class and the rank quality the FP64 form reaches:
+form. In every form the panel, norms and rank stay FP64:
+  precision=1: FP32-class trailing update and candidate Gram (FP32 from FP64
+    storage, CUDA cores);
+  precision=2: split-BF16x3 on the tensor cores (tcgen05), one merged
+    trailing update per step, the Gram on the tensor cores too;
+  precision=3: the same with 3xTF32.
 
-  ||A Pi - Q R|| / ||A|| <= 1e-5 (FP32 roundoff accumulated over the updates),
-  ||Q^T Q - I|| <= 1e-13 (the reflectors themselves are FP64),
-  the precision-aware criterion finds the gap rank,
-  sigma_min(R11) / sigma_r(A) within 2x of the plain FP64 form (the north
-  star's acceptance for the variants)."""
+Results are not expected to match the FP64 oracle digit for digit. Each case
+reports its error against the oracle and checks the bounds of its precision
+class: residual and R error 1e-5 for FP32 and 3xTF32, 5e-5 for BF16x3. It
+also checks the rank quality the FP64 form reaches:
+  ||Q^T Q - I|| <= 1e-13 (the reflectors themselves are FP64);
+  the precision-aware criterion finds the gap rank;
+  sigma_min(R11) / sigma_r(A) within 2x of the plain FP64 form (the
+  acceptance for the variants).
+precision=4, the merged structure in FP64, must reproduce the oracle."""
 from __future__ import annotations
 
 import numpy as np
