@@ -180,3 +180,21 @@ def test_full_size_sample_of_the_uneven_batch():
         assert e.rank <= g["rank_colmax"] <= min(e.m, e.n), (e, g["rank_colmax"])
     print("\n[batched] full-size sample:", [(e.m, e.n, e.rank, g["rank"], g["rank_colmax"]) for e, g in zip(pick, got)],
           "divergences", [r["diverged_at"] for r in reps])
+
+
+def test_equality_edges_in_the_batched_kernel():
+    """The hand-derived equality edges of tests/golden/dm_equality.json
+    (candidate u = tau mu admitted, residual = eps_s does not break, equal
+    norms in position order) in the batched kernel's own selection and panel
+    code: each case's first step equals the golden decisions."""
+    from tests._helpers import golden
+    from tests.test_oracle_pins import dm_equality_matrix
+
+    for case in golden("dm_equality.json")["cases"]:
+        A = dm_equality_matrix(case["matrix"])
+        (g,) = _run([A], case["tau"], case["delta"], case["k_max"], check_last=case["check_last"])
+        tr = g["trace"][0]
+        assert int(tr["ncand_all"]) == case["ncand_all"], case["why"]
+        assert int(tr["k"]) == case["k"] and int(tr["l"]) == case["l"], case["why"]
+        assert list(g["J"][0][: case["k"]]) == case["J"], case["why"]
+        _check([A], [g], case["tau"], case["delta"], case["k_max"], check_last=case["check_last"])

@@ -256,3 +256,29 @@ def test_full_size(name, tau, delta, kmax):
         ok = sig > 1e4 * EPS * n * sig[0]
         ratio = d[ok] / sig[ok]
         assert ratio.min() > 1e-1 and ratio.max() < 10.0, (ratio.min(), ratio.max())
+
+
+# ----------------------------------------------------------------- equality edges
+from tests._helpers import golden  # noqa: E402
+from tests.test_oracle_pins import dm_equality_matrix  # noqa: E402
+
+
+@pytest.mark.parametrize("case", golden("dm_equality.json")["cases"], ids=lambda c: c["why"][:48])
+def test_dm_equality_edges_on_gpu(case):
+    """The hand-derived equality edges (candidate u = tau mu admitted, residual
+    = eps_s does not break, equal norms in position order) through the C ABI:
+    the first step's decisions equal the golden values, and the whole
+    factorization equals the oracle's."""
+    A = dm_equality_matrix(case["matrix"])
+    kw = dict(check_last=case["check_last"])
+    g = run_gpu(A, case["tau"], case["delta"], case["k_max"], max_steps=1, **kw)
+    tr = g["trace"][0]
+    assert int(tr["ncand_all"]) == case["ncand_all"]
+    assert int(tr["k"]) == case["k"] and int(tr["l"]) == case["l"]
+    assert list(g["J"][0][: case["k"]]) == case["J"]
+    assert float(tr["eps_s"]) == case["tau"] * float(tr["mu"])
+    full = run_gpu(A, case["tau"], case["delta"], case["k_max"], **kw)
+    o = O.qrdm(A, case["tau"], case["delta"], case["k_max"], **kw)
+    rep = compare(A, full, o)
+    assert rep["diverged_at"] is None
+    np.testing.assert_array_equal(full["perm"], o["perm"])

@@ -109,6 +109,32 @@ def test_dm_first_step_golden(case):
     assert list(r["J"][0][: case["k"]]) == case["J"]
 
 
+def dm_equality_matrix(name: str) -> np.ndarray:
+    """A matrix of tests/golden/dm_equality.json, column-major."""
+    g = golden("dm_equality.json")
+    cols = np.array(g["matrices"][name]["columns"], dtype=np.float64)
+    assert cols.shape[1] == g["rows"]
+    return np.asfortranarray(cols.T)
+
+
+@pytest.mark.parametrize("case", golden("dm_equality.json")["cases"], ids=lambda c: c["why"][:48])
+def test_dm_equality_edges(case):
+    """The equality edges of the first step, from exactly representable
+    columns: u_i = tau mu is a candidate (eq. def_candidate_set, >=), a
+    residual equal to eps_s does not stop the panel (eq. lenght_check, <),
+    and equal-norm candidates are visited in position order (reading R4)."""
+    A = dm_equality_matrix(case["matrix"])
+    r = O.qrdm(A, case["tau"], case["delta"], case["k_max"], check_last=case["check_last"], max_steps=1)
+    tr = r["trace"][0]
+    assert int(tr["ncand_all"]) == case["ncand_all"]
+    assert int(tr["k"]) == case["k"]
+    assert int(tr["l"]) == case["l"]
+    assert list(r["J"][0][: case["k"]]) == case["J"]
+    # the exact values behind the decisions
+    assert float(tr["mu"]) == float(np.max(np.linalg.norm(A, axis=0)))
+    assert float(tr["eps_s"]) == case["tau"] * float(tr["mu"])
+
+
 def test_dm_duplicate_columns_never_accepted():
     """|theta| = 1 for equal columns: 1 < delta fails even at delta = 1."""
     a = np.array([1.0, 2.0, -1.0, 0.5])
