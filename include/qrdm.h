@@ -37,6 +37,17 @@ extern "C" {
 #define QRDM_ERR_WORKSPACE 3 /* workspace too small or misaligned (256-byte alignment) */
 #define QRDM_ERR_UNSUPPORTED 4 /* the device or an option is not supported */
 #define QRDM_ERR_INTERNAL 5  /* an internal consistency check failed on the device */
+#define QRDM_ERR_TIMEOUT 6   /* a bounded device-side wait gave up (qrdm_info.fail_* say where); A is
+                                partially factored, the context stays usable */
+#define QRDM_ERR_CHECKED 7   /* with opts.checked: a device-side index check tripped; the access was
+                                skipped, the factorization abandoned, A is partially factored */
+
+/* Where a device-side wait or check gave up (qrdm_info.fail_code). */
+#define QRDM_FAIL_NONE 0
+#define QRDM_FAIL_GRID_BARRIER 1 /* grid barrier of a cooperative kernel: fail_value = arrivals seen */
+#define QRDM_FAIL_PIVOT_RANGE 2  /* a pivot position outside [n_s, n): fail_value = the position */
+#define QRDM_FAIL_MMA_WAIT 4     /* an mbarrier wait of a tensor-core kernel: fail_value = kernel id */
+#define QRDM_FAIL_CHECK 8        /* a checked-path index check: fail_value = the bad index, fail_cta = kernel id */
 
 #define QRDM_KMAX_LIMIT 128 /* largest supported k_max */
 
@@ -117,12 +128,36 @@ typedef struct qrdm_opts {
      unit roundoff of that form's trailing update, instead of sqrt(eps).
      Any other value: -11. */
   int32_t precision;
-  int32_t reserved1;
+  /* 1: the checked path.  Every index the kernels derive on the device
+     (argmax and candidate positions, the column moves of the permutation,
+     the block and panel sizes, the step advance) is range-checked before it
+     is used; a check that trips records itself in a device status word,
+     skips the access and ends the factorization with QRDM_ERR_CHECKED (no
+     trap, no assert: the context stays usable).  Results are identical to
+     checked = 0.  Stands in for a memory checker. */
+  int32_t checked;
   /* host, optional: per-kernel event timing (see qrdm_profile). */
   qrdm_profile* profile;
   /* host, optional: learned per-step (tau, delta) and feature logging (see
      qrdm_policy); NULL: tau and delta fixed for the whole factorization. */
   const struct qrdm_policy* policy;
+  /* Limit of every device-side wait (the grid barriers of the cooperative
+     single-column kernel, the mbarrier waits of the tensor-core kernels), in
+     microseconds of the GPU's global timer; 0: 2 s.  A wait that runs out
+     sets an abort flag that every CTA of the factorization observes, waits
+     (bounded) for its own copies and MMAs in flight, frees its tensor
+     memory, and the call returns QRDM_ERR_TIMEOUT.  Negative: -11. */
+  int64_t wait_limit_us;
+  /* Test hook, 0 in normal use.  1: the first grid barrier of the
+     cooperative single-column kernel waits for one arrival more than the
+     grid makes (a wait nothing completes; QRDM_ERR_TIMEOUT).  2 (needs
+     checked = 1): the first column-move list gets a destination one past
+     the last column, which the checked path must refuse (QRDM_ERR_CHECKED).
+     3 (precision 2 or 3): the first tile of the tensor-core update waits
+     on an mbarrier nothing arrives on (QRDM_ERR_TIMEOUT after its in-flight
+     copies drained and its tensor memory was freed).  Other values: -11. */
+  int32_t test_fault;
+  int32_t reserved2;
 } qrdm_opts;
 
 /*
@@ -172,7 +207,12 @@ typedef struct qrdm_info {
   int64_t nsteps;      /* block steps executed */
   int64_t launches;    /* kernels this call launched */
   int32_t cuda_error;  /* cudaError_t of the failing call when QRDM_ERR_CUDA */
+  int32_t fail_code;   /* QRDM_FAIL_*: where a device-side wait or check gave up (0: none) */
+  int32_t fail_cta;    /* CTA that recorded it (QRDM_FAIL_CHECK: the kernel id, QRDM_K_*) */
   int32_t reserved;
+  int64_t fail_step;   /* block step at which it happened */
+  int64_t fail_ns;     /* n_s at that step */
+  int64_t fail_value;  /* code-specific value (see QRDM_FAIL_*) */
 } qrdm_info;
 
 /* One record per block step, written on the device when a trace is requested. */
@@ -219,8 +259,11 @@ int qrdm_workspace_size(int64_t m, int64_t n, int32_t k_max, size_t* bytes);
  *           indices of J per step (-1 padded).
  *
  * Error behaviour: -1..-7 for invalid m, n, dA, lda, tau, delta, k_max; -8/-9
- * for NULL d_htau/d_perm when needed, -10 for NULL info, -12 for a NULL
- * workspace when one is needed.  m = 0 or n = 0 returns 0 with rank 0.
+ * for NULL d_htau/d_perm when needed, -10 for NULL info, -11 for invalid
+ * opts, -12 for a NULL workspace when one is needed.  m = 0 or n = 0 returns
+ * 0 with rank 0 (after the same argument and option checks).
+ * QRDM_ERR_TIMEOUT / QRDM_ERR_CHECKED / QRDM_ERR_INTERNAL fill info's fail_*
+ * fields; the CUDA context stays usable and the next call starts afresh.
  */
 int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, double delta, int32_t k_max,
                 double* d_htau, int32_t* d_perm, qrdm_info* info, const qrdm_opts* opts, void* d_work,
@@ -234,11 +277,17 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
 #define QRDM_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 /*
- * qrdm_factor for callers that cannot allocate device memory: code that
- * runs where cudaMalloc is unavailable or forbidden (inside a stream
- * capture, under an allocator that owns the whole device, in a callback or
- * a real-time loop), or that has no spare buffer to offer as workspace.
- * The paper has no counterpart; this is a property of the library.
+ * qrdm_factor for callers that cannot allocate device memory: code running
+ * under an allocator that owns the whole device (a framework's caching
+ * pool, a fixed-footprint service), a real-time loop that must not call
+ * cudaMalloc or cudaFree because they may synchronize the device, or a
+ * caller with no spare buffer to offer as workspace.  The paper has no
+ * counterpart; this is a property of the library.
+ *
+ * Like qrdm_factor it drives the factorization from the host: it copies the
+ * step state to the host and synchronizes `stream` several times per
+ * factorization, so it blocks the calling thread, cannot be captured into a
+ * CUDA graph and must not be called from a stream callback.
  *
  * Same arguments, outputs and error codes as qrdm_factor() minus d_work and
  * work_bytes.  The workspace is one array of QRDM_NOALLOC_SCRATCH_BYTES in
@@ -248,8 +297,8 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
  *   - Shapes whose workspace exceeds the scratch are rejected with
  *     QRDM_ERR_WORKSPACE before anything is touched.
  *   - The first call on a device looks up the scratch's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     process.
  *   - All calls share the one scratch.  Each call re-initializes every part
  *     of it that it reads, so earlier contents do not matter, but calls whose
  *     work overlaps on the GPU (other streams, other host threads) race on it:
@@ -299,7 +348,8 @@ int qrdm_factor_noalloc(double* dA, int64_t m, int64_t n, int64_t lda, double ta
  * (n).  Matrices must not overlap.  An optional per-matrix step trace
  * (d_trace, d_trace_J, trace_cap) is written as in qrdm_factor.  opts may be
  * NULL; eps1_mode, stop_at_rank, check_last, no_break and sdd are honoured,
- * max_steps is ignored, precision must be 0 (QRDM_ERR_UNSUPPORTED
+ * max_steps and wait_limit_us are ignored (no CTA ever waits on another),
+ * precision, checked and test_fault must be 0 (QRDM_ERR_UNSUPPORTED
  * otherwise).  opts->policy applies to every matrix (its d_weights, ranges and
  * rho_min; the per-matrix logs come from qrdm_batch_matrix).  A profile
  * (qrdm_factor_batched only; it then times the launch
@@ -437,7 +487,7 @@ int qrdm_ls_solve(const double* dA, int64_t lda, const double* dQR, int64_t ldqr
  * bytes, 256-byte aligned.  Synchronizes the stream.
  * Errors: -i for an invalid i-th argument, QRDM_ERR_WORKSPACE,
  * QRDM_ERR_NONFINITE (A left unmodified), QRDM_ERR_UNSUPPORTED (no
- * cooperative launch), QRDM_ERR_INTERNAL (a grid barrier wait gave up),
+ * cooperative launch), QRDM_ERR_TIMEOUT (a grid barrier wait gave up after 2 s; info.fail_*),
  * QRDM_ERR_CUDA.
  */
 int qrdm_qp3_workspace_size(int64_t m, int64_t n, int32_t nb, size_t* bytes);

@@ -15,8 +15,14 @@ import numpy as np
 
 from ._binding import (  # noqa: F401
     EXPORTS,
+    QRDM_ERR_CHECKED,
     QRDM_ERR_CUDA,
     QRDM_ERR_INTERNAL,
+    QRDM_ERR_TIMEOUT,
+    QRDM_FAIL_CHECK,
+    QRDM_FAIL_GRID_BARRIER,
+    QRDM_FAIL_MMA_WAIT,
+    QRDM_FAIL_PIVOT_RANGE,
     QRDM_ERR_NONFINITE,
     QRDM_ERR_UNSUPPORTED,
     QRDM_ERR_WORKSPACE,
@@ -41,9 +47,17 @@ TRACE_DTYPE = np.dtype([("ns", np.int64), ("jstar", np.int64), ("ncand_all", np.
 
 
 class QRDMError(RuntimeError):
-    def __init__(self, code: int, where: str = "qrdm_factor"):
+    """A nonzero return code; ``info`` (a qrdm_info, when the call returns
+    one) carries the device-side failure record (fail_code, fail_cta,
+    fail_step, fail_ns, fail_value)."""
+
+    def __init__(self, code: int, where: str = "qrdm_factor", info=None):
         self.code = code
+        self.info = info
         msg = f"{where} failed: {code} ({qrdm_strerror(code)})"
+        if info is not None and getattr(info, "fail_code", 0):
+            msg += (f" [fail_code {info.fail_code}, cta {info.fail_cta}, step {info.fail_step}, "
+                    f"ns {info.fail_ns}, value {info.fail_value}]")
         super().__init__(msg)
 
 
@@ -62,7 +76,8 @@ class Factorization:
 
 def make_opts(eps1_mode=0, stop_at_rank=False, check_last=False, no_break=False, sdd=False, max_steps=0,
               profile: qrdm_profile | None = None, precision: int = 0,
-              policy: qrdm_policy | None = None) -> qrdm_opts:
+              policy: qrdm_policy | None = None, checked: bool = False, wait_limit_us: int = 0,
+              test_fault: int = 0) -> qrdm_opts:
     import ctypes
 
     o = qrdm_opts()
@@ -77,6 +92,9 @@ def make_opts(eps1_mode=0, stop_at_rank=False, check_last=False, no_break=False,
     o.sdd = int(bool(sdd))
     o.max_steps = int(max_steps)
     o.precision = int(precision)
+    o.checked = int(bool(checked))
+    o.wait_limit_us = int(wait_limit_us)
+    o.test_fault = int(test_fault)
     return o
 
 
@@ -101,7 +119,8 @@ def factor(A, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mod
            stop_at_rank: bool = False, check_last: bool = False, no_break: bool = False, sdd: bool = False,
            max_steps: int = 0, trace: bool = False, workspace=None, out_htau=None, out_perm=None,
            stream=None, profile: qrdm_profile | None = None, precision: int = 0,
-           policy: qrdm_policy | None = None) -> Factorization:
+           policy: qrdm_policy | None = None, checked: bool = False, wait_limit_us: int = 0,
+           test_fault: int = 0) -> Factorization:
     """Factor A Pi = Q R in place.  ``A`` is a CUDA float64 tensor with
     stride(0) == 1 (column-major, lda = stride(1)).  ``precision`` selects the
     arithmetic of the trailing update: 0 FP64, 1 FP32 on the CUDA cores, 2
@@ -131,13 +150,14 @@ def factor(A, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mod
         tr = torch.zeros(cap * TRACE_DTYPE.itemsize, dtype=torch.uint8, device=dev)
         trJ = torch.empty(cap * k_max, dtype=torch.int32, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
-    opts = make_opts(eps1_mode, stop_at_rank, check_last, no_break, sdd, max_steps, profile, precision, policy)
+    opts = make_opts(eps1_mode, stop_at_rank, check_last, no_break, sdd, max_steps, profile, precision, policy,
+                     checked, wait_limit_us, test_fault)
     rc, info = qrdm_factor(A.data_ptr() if m * n else 0, m, n, lda, float(tau), float(delta), int(k_max),
                            htau.data_ptr(), perm.data_ptr(), opts, workspace.data_ptr(), workspace.numel(),
                            s.cuda_stream, tr.data_ptr() if tr is not None else 0,
                            trJ.data_ptr() if trJ is not None else 0, cap)
     if rc != 0:
-        raise QRDMError(rc)
+        raise QRDMError(rc, info=info)
     out = Factorization(A=A, htau=htau[:kmin], perm=perm[:n], rank=int(info.rank), rank_colmax=int(info.rank_colmax),
                         nsteps=int(info.nsteps), launches=int(info.launches))
     if trace:

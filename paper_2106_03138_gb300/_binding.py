@@ -20,6 +20,13 @@ QRDM_ERR_NONFINITE = 2
 QRDM_ERR_WORKSPACE = 3
 QRDM_ERR_UNSUPPORTED = 4
 QRDM_ERR_INTERNAL = 5
+QRDM_ERR_TIMEOUT = 6
+QRDM_ERR_CHECKED = 7
+QRDM_FAIL_NONE = 0
+QRDM_FAIL_GRID_BARRIER = 1
+QRDM_FAIL_PIVOT_RANGE = 2
+QRDM_FAIL_MMA_WAIT = 4
+QRDM_FAIL_CHECK = 8
 QRDM_KMAX_LIMIT = 128
 
 
@@ -43,13 +50,15 @@ QRDM_POLICY_NPARAM = 5378
 
 class qrdm_opts(ctypes.Structure):
     _fields_ = [("eps1_mode", c_i32), ("stop_at_rank", c_i32), ("check_last", c_i32), ("no_break", c_i32),
-                ("sdd", c_i32), ("max_steps", c_i32), ("precision", c_i32), ("reserved1", c_i32),
-                ("profile", ctypes.POINTER(qrdm_profile)), ("policy", ctypes.POINTER(qrdm_policy))]
+                ("sdd", c_i32), ("max_steps", c_i32), ("precision", c_i32), ("checked", c_i32),
+                ("profile", ctypes.POINTER(qrdm_profile)), ("policy", ctypes.POINTER(qrdm_policy)),
+                ("wait_limit_us", c_i64), ("test_fault", c_i32), ("reserved2", c_i32)]
 
 
 class qrdm_info(ctypes.Structure):
     _fields_ = [("rank", c_i64), ("rank_colmax", c_i64), ("nsteps", c_i64), ("launches", c_i64),
-                ("cuda_error", c_i32), ("reserved", c_i32)]
+                ("cuda_error", c_i32), ("fail_code", c_i32), ("fail_cta", c_i32), ("reserved", c_i32),
+                ("fail_step", c_i64), ("fail_ns", c_i64), ("fail_value", c_i64)]
 
 
 class qrdm_step_record(ctypes.Structure):

@@ -235,6 +235,45 @@ PolicyParams policy_params(const qrdm_policy* p) {
   return pp;
 }
 
+// identity permutation (empty matrices)
+__global__ void k_iota(int32_t* perm, int64_t n) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    perm[j] = (int32_t)j;
+}
+
+constexpr int64_t WAIT_DEFAULT_NS = 2000000000LL;  // 2 s
+
+// Argument and option checks of qrdm_factor (0, -i, or QRDM_ERR_UNSUPPORTED);
+// on success *o holds the options (zero when opts is NULL) and info is zeroed.
+int validate_factor(int64_t m, int64_t n, const double* dA, int64_t lda, double tau, double delta, int32_t k_max,
+                    const double* d_htau, const int32_t* d_perm, qrdm_info* info, const qrdm_opts* opts,
+                    qrdm_opts* o) {
+  if (m < 0) return -1;
+  if (n < 0 || n > INT32_MAX) return -2;
+  if (!dA && m > 0 && n > 0) return -3;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  if (!(tau > 0.0 && tau <= 1.0)) return -5;
+  if (!(delta >= 0.0 && delta <= 1.0)) return -6;
+  if (k_max < 1 || k_max > QRDM_KMAX_LIMIT) return -7;
+  const int64_t kmin = m < n ? m : n;
+  if (!d_htau && kmin > 0) return -8;
+  if (!d_perm && n > 0) return -9;
+  if (!info) return -10;
+  memset(info, 0, sizeof(*info));
+  memset(o, 0, sizeof(*o));
+  if (opts) *o = *opts;
+  if (o->eps1_mode != 0 && o->eps1_mode != 1) return -11;
+  if (o->precision < 0 || o->precision > 4) return -11;
+  if (o->checked != 0 && o->checked != 1) return -11;
+  if (o->wait_limit_us < 0) return -11;
+  if (o->test_fault < 0 || o->test_fault > 3) return -11;
+  if (o->test_fault == 2 && !o->checked) return -11;
+  if (o->test_fault == 3 && o->precision != 2 && o->precision != 3) return -11;
+  if (!policy_valid(o->policy)) return -11;
+  if (o->precision >= 2 && k_max > TC_LMAX) return QRDM_ERR_UNSUPPORTED;
+  return 0;
+}
+
 #define CK(call)                                  \
   do {                                            \
     cudaError_t e_ = (call);                      \
@@ -254,7 +293,7 @@ void set_last_cuda_error(int e) { g_last_cuda = e; }
 
 extern "C" {
 
-int qrdm_version(void) { return 100; }
+int qrdm_version(void) { return 200; }
 
 int qrdm_last_cuda_error(void) { return g_last_cuda; }
 
@@ -272,6 +311,10 @@ const char* qrdm_strerror(int code) {
       return "unsupported device or option";
     case QRDM_ERR_INTERNAL:
       return "internal consistency check failed";
+    case QRDM_ERR_TIMEOUT:
+      return "a bounded device-side wait gave up";
+    case QRDM_ERR_CHECKED:
+      return "a checked-path index check tripped";
     default:
       return code < 0 ? "invalid argument" : "unknown error";
   }
@@ -289,37 +332,21 @@ int qrdm_workspace_size(int64_t m, int64_t n, int32_t k_max, size_t* bytes) {
 int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, double delta, int32_t k_max,
                 double* d_htau, int32_t* d_perm, qrdm_info* info, const qrdm_opts* opts, void* d_work,
                 size_t work_bytes, void* stream_, qrdm_step_record* d_trace, int32_t* d_trace_J, int64_t trace_cap) {
-  if (m < 0) return -1;
-  if (n < 0 || n > INT32_MAX) return -2;
-  if (!dA && m > 0 && n > 0) return -3;
-  if (lda < (m > 1 ? m : 1)) return -4;
-  if (!(tau > 0.0 && tau <= 1.0)) return -5;
-  if (!(delta >= 0.0 && delta <= 1.0)) return -6;
-  if (k_max < 1 || k_max > QRDM_KMAX_LIMIT) return -7;
-  const int64_t kmin = m < n ? m : n;
-  if (!d_htau && kmin > 0) return -8;
-  if (!d_perm && n > 0) return -9;
-  if (!info) return -10;
-  memset(info, 0, sizeof(*info));
   qrdm_opts o;
-  memset(&o, 0, sizeof(o));
-  if (opts) o = *opts;
-  if (o.eps1_mode != 0 && o.eps1_mode != 1) return -11;
-  if (o.precision < 0 || o.precision > 4) return -11;
-  if (!policy_valid(o.policy)) return -11;
-  if (o.precision >= 2 && k_max > TC_LMAX) return QRDM_ERR_UNSUPPORTED;
+  {
+    const int rc = validate_factor(m, n, dA, lda, tau, delta, k_max, d_htau, d_perm, info, opts, &o);
+    if (rc) return rc;
+  }
+  const int64_t kmin = m < n ? m : n;
   cudaStream_t stream = (cudaStream_t)stream_;
 
   if (n == 0 || m == 0) {
     // nothing to factor; the permutation is the identity
     if (n > 0) {
-      // identity permutation via a tiny host copy
-      int32_t* h = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-      if (!h) return QRDM_ERR_INTERNAL;
-      for (int64_t j = 0; j < n; ++j) h[j] = (int32_t)j;
-      cudaError_t e = cudaMemcpyAsync(d_perm, h, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, stream);
+      const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+      k_iota<<<g, 256, 0, stream>>>(d_perm, n);
+      cudaError_t e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-      free(h);
       if (e != cudaSuccess) {
         g_last_cuda = (int)e;
         info->cuda_error = (int32_t)e;
@@ -412,6 +439,9 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   P.tc_vu = (unsigned char*)(w + L.vu);
   P.tc_wi = (unsigned char*)(w + L.wi);
   P.tc_al = ((lda & 1) == 0 && ((uintptr_t)dA & 15) == 0) ? 1 : 0;
+  P.checked = o.checked;
+  P.test_fault = o.test_fault;
+  P.wait_ns = o.wait_limit_us > 0 ? o.wait_limit_us * 1000 : WAIT_DEFAULT_NS;
   {
     // the W GEMM's segment partials live in the W-partials region after one
     // n x 64 block: as many segments as the region holds, at most TC_NSEG_MAX
@@ -662,9 +692,6 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   for (;;) {
     const int nsub = dm_off ? 1 : nsub_full;
     if (dm_off && qrp_fused) {
-      if (getenv("QRDM_DEBUG"))
-        fprintf(stderr, "qrdm: fused single-column kernel from ns=%lld step=%lld (grid %d, smem %lld)\n",
-                (long long)hs.ns, (long long)hs.step, cfg.qrp_grid, (long long)(m * 8));
       CK(launch_qrp());
     } else {
       for (int b = 0; b < batch; ++b) CK(enqueue_step(nsub));
@@ -688,12 +715,17 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     for (int i = 0; i < QRDM_NKERNELS; ++i) prof->flops[i] += hs.flops[i];
   }
   info->launches = launches;
-  if (!hs.done || hs.nonfinite) {
-    if (getenv("QRDM_DEBUG"))
-      fprintf(stderr,
-              "qrdm: internal error: done=%d flag=%d diag_code=%d cta=%d step=%lld ns=%lld value=%lld gbar=%u\n",
-              hs.done, hs.nonfinite, hs.diag_code, hs.diag_cta, (long long)hs.diag_step, (long long)hs.diag_ns,
-              (long long)hs.diag_value, hs.gbar);
+  info->nsteps = hs.step;
+  if (hs.abort_flag || !hs.done || hs.nonfinite) {
+    // where a bounded wait gave up or a check tripped (recorded on the device)
+    info->fail_code = hs.diag_code;
+    info->fail_cta = hs.diag_cta;
+    info->fail_step = hs.diag_step;
+    info->fail_ns = hs.diag_ns;
+    info->fail_value = hs.diag_value;
+    if (hs.abort_flag && (hs.diag_code == FAIL_GRID_BARRIER || hs.diag_code == FAIL_MMA_WAIT))
+      return QRDM_ERR_TIMEOUT;
+    if (hs.abort_flag && hs.diag_code == FAIL_CHECK) return QRDM_ERR_CHECKED;
     return QRDM_ERR_INTERNAL;
   }
   info->rank = hs.rank >= 0 ? hs.rank : (hs.ns >= kmin ? kmin : hs.ns);
@@ -815,7 +847,9 @@ int batch_opts(const qrdm_opts* opts, qrdm_opts* o) {
   o->max_steps = 0;
   if (o->eps1_mode != 0 && o->eps1_mode != 1) return -1;
   if (!policy_valid(o->policy)) return -1;
-  if (o->precision != 0) return QRDM_ERR_UNSUPPORTED;
+  if (o->checked < 0 || o->checked > 1 || o->wait_limit_us < 0 || o->test_fault < 0 || o->test_fault > 3) return -1;
+  // no cross-CTA waits to bound here, and no checked variant of the batched kernel
+  if (o->precision != 0 || o->checked || o->test_fault) return QRDM_ERR_UNSUPPORTED;
   return 0;
 }
 

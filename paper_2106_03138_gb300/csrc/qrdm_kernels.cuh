@@ -53,8 +53,9 @@ struct alignas(128) DevState {
   double flops[16]; // algorithmic FP64 flops per kernel id (profile)
   // grid barrier of the fused single-column kernel and its diagnostics
   unsigned int gbar;     // arrivals (monotonic within one launch)
-  int32_t abort_flag;    // set when a barrier wait gave up or a check failed
-  int32_t diag_code;     // 1: barrier wait timed out, 2: pivot index out of range
+  int32_t abort_flag;    // set when a bounded wait gave up or a check failed; every kernel then stops
+  int32_t diag_code;     // where (QRDM_FAIL_* of the C header): 1 grid barrier wait, 2 pivot index out
+                         // of range, 4 tensor-core mbarrier wait, 8 checked-path index check
   int32_t diag_cta;
   int64_t diag_step;
   int64_t diag_ns;
@@ -102,6 +103,9 @@ struct Params {
   unsigned char* tc_vu; // V's operand image for the update
   unsigned char* tc_wi; // W's operand image for the update
   int32_t tc_al;        // 1: A and lda allow 16-byte loads from an even row (the W pass starts its rows there)
+  int32_t checked;      // 1: range-check every device-derived index before use (opts.checked)
+  int32_t test_fault;   // test hook of opts.test_fault (0: none)
+  int64_t wait_ns;      // limit of every bounded device-side wait, in global-timer nanoseconds
   // optional trace
   StepRecord* trace;
   int32_t* traceJ;
@@ -116,6 +120,42 @@ enum KernelId {
 };
 
 __device__ __forceinline__ void add_flops(DevState* st, int kid, double f) { atomicAdd(&st->flops[kid], f); }
+
+// failure codes of DevState::diag_code (same values as QRDM_FAIL_* in the C header)
+constexpr int FAIL_GRID_BARRIER = 1;
+constexpr int FAIL_PIVOT_RANGE = 2;
+constexpr int FAIL_MMA_WAIT = 4;
+constexpr int FAIL_CHECK = 8;
+
+// The GPU's global timer in nanoseconds: the clock of every bounded wait, so
+// that a limit means the same time at any SM clock.
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Record the first failure of a factorization (later ones keep the first
+// record) and raise the abort flag that every kernel observes.
+__device__ __forceinline__ void record_fail(DevState* st, int code, int who, int64_t step, int64_t ns,
+                                            int64_t value) {
+  if (atomicExch(&st->abort_flag, 1) == 0) {
+    st->diag_code = code;
+    st->diag_cta = who;
+    st->diag_step = step;
+    st->diag_ns = ns;
+    st->diag_value = value;
+    __threadfence();
+  }
+}
+
+// A checked-path index check: true when lo <= v < hi; otherwise the failure is
+// recorded (kernel id `kid`, the bad value) and the caller skips the access.
+__device__ __forceinline__ bool in_range(const Params& P, int kid, int64_t v, int64_t lo, int64_t hi) {
+  if (v >= lo && v < hi) return true;
+  record_fail(P.st, FAIL_CHECK, kid, P.st->step, P.st->ns, v);
+  return false;
+}
 
 // FP64 <-> FP32 by integer operations on the IEEE-754 fields.  GB300 executes
 // F2F conversions that involve FP64 on its narrow FP64 pipe (about 2 per clock
@@ -288,6 +328,10 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
   if (tid == 0) {
     int go = 1;
     if (st->done) go = 0;
+    if (go && *(volatile int32_t*)&st->abort_flag) {
+      st->done = 1;
+      go = 0;
+    }
     if (go && (st->ns >= P.kmin || (P.max_steps > 0 && st->step >= P.max_steps))) {
       st->done = 1;
       go = 0;
@@ -353,6 +397,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
         st->dm_on = 0;
         if (P.stop_at_rank) stop = 1;
       }
+      if (P.checked && !stop && !in_range(P, KID_SELECT, jstar, ns, n)) stop = 1;
       if (stop) {
         st->done = 1;
       } else {
@@ -524,7 +569,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
     for (int b = 0; b < got; ++b) {
       if (better(s_lu[b], s_list[b], xv, xp)) ++r;
     }
-    P.cols[1 + r] = xp;
+    if (!P.checked || (in_range(P, KID_SELECT, xp, ns, n) && in_range(P, KID_SELECT, 1 + r, 1, P.kmax)))
+      P.cols[1 + r] = xp;
   }
   if (tid == 0) {
     int bad = (got != keep);
@@ -755,6 +801,22 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
         ++nm;
       }
     }
+    if (P.checked) {
+      if (P.test_fault == 2 && st->step == 0) {
+        // test hook: a destination one past the last column (refused below)
+        if (nm == 0) {
+          P.msrc[0] = (int32_t)ns;
+          s_mvp[0] = 0;
+          nm = 1;
+        }
+        P.mdst[0] = (int32_t)P.n;
+      }
+      bool ok = in_range(P, KID_PICK, k, 1, kc + 1) && in_range(P, KID_PICK, nm, 0, 2 * KMAX + 1);
+      for (int e = 0; ok && e < nm; ++e)
+        ok = in_range(P, KID_PICK, P.mdst[e], ns, P.n) && in_range(P, KID_PICK, P.msrc[e], ns, P.n) &&
+             in_range(P, KID_PICK, s_mvp[e], 0, np);
+      if (!ok) nm = 0;  // no move is made; the factorization stops at this step's end
+    }
     st->npairs = nm;
     st->k = k;
     s_np = nm;
@@ -800,10 +862,20 @@ __global__ void __launch_bounds__(256) k_permute(Params P) {
   for (int64_t r0 = (int64_t)blockIdx.x * 32; r0 < P.m; r0 += (int64_t)gridDim.x * 32) {
     const int64_t i = r0 + lane;
     __syncthreads();
-    for (int e = w; e < nm; e += nw) s[e * 33 + lane] = (i < P.m) ? P.A[(int64_t)P.msrc[e] * P.lda + i] : 0.0;
+    for (int e = w; e < nm; e += nw) {
+      const int64_t src = P.msrc[e];
+      const bool ok = !P.checked || (src >= 0 && src < P.n);
+      s[e * 33 + lane] = (i < P.m && ok) ? P.A[src * P.lda + i] : 0.0;
+    }
     __syncthreads();
-    for (int e = w; e < nm; e += nw)
-      if (i < P.m) P.A[(int64_t)P.mdst[e] * P.lda + i] = s[e * 33 + lane];
+    for (int e = w; e < nm; e += nw) {
+      const int64_t dst = P.mdst[e];
+      if (P.checked && !(dst >= 0 && dst < P.n)) {
+        if (lane == 0 && r0 == (int64_t)blockIdx.x * 32) record_fail(P.st, FAIL_CHECK, KID_PERMUTE, P.st->step, P.st->ns, dst);
+        continue;
+      }
+      if (i < P.m) P.A[dst * P.lda + i] = s[e * 33 + lane];
+    }
   }
 }
 
@@ -845,6 +917,11 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
   DevState* st = P.st;
   if (st->done) return;  // uniform across the cluster
   const int k = st->k;
+  // checked path: the block size and its columns and rows (values fixed for
+  // the launch, so every CTA of the cluster takes the same decision)
+  if (P.checked && !(in_range(P, KID_PANEL, k, 1, P.kmax + 1) && in_range(P, KID_PANEL, st->ns + k, 1, P.n + 1) &&
+                     in_range(P, KID_PANEL, st->ns, 0, P.m)))
+    return;
   const int jb = j * PB;
   const int crank = (int)cluster.block_rank();
   const int tid = threadIdx.x;
@@ -1610,30 +1687,25 @@ __global__ void __launch_bounds__(256) k_downdate(Params P) {
 // per step: after all CTAs have read the pivot column, and after all updates.
 // ---------------------------------------------------------------------------
 constexpr int QRP_THREADS = 256;
-constexpr long long GBAR_SPIN_LIMIT = 4000000000LL;  // clock cycles (about 2 s) before a wait gives up
 
 // Grid-wide barrier for a cooperative launch: arrival counter with release,
-// polling with acquire, bounded.  Returns false (and sets the abort flag)
-// when the wait gave up; every CTA then leaves its loop.
-__device__ __forceinline__ bool grid_barrier(DevState* st, unsigned int target, int64_t step, int64_t ns) {
+// polling with acquire, bounded by limit_ns of the global timer.  Returns
+// false (and raises the abort flag) when the wait gave up or another CTA's
+// did; every CTA then leaves its loop.
+__device__ __forceinline__ bool grid_barrier(DevState* st, unsigned int target, int64_t step, int64_t ns,
+                                             int64_t limit_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int* ctr = &st->gbar;
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(1u) : "memory");
-    const long long t0 = clock64();
+    const unsigned long long t0 = gtimer_ns();
     unsigned int cur = 0;
     for (;;) {
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(ctr) : "memory");
       if ((int)(cur - target) >= 0) break;
       if (*(volatile int32_t*)&st->abort_flag) break;
-      if (clock64() - t0 > GBAR_SPIN_LIMIT) {
-        if (atomicExch(&st->abort_flag, 1) == 0) {
-          st->diag_code = 1;
-          st->diag_cta = (int)blockIdx.x;
-          st->diag_step = step;
-          st->diag_ns = ns;
-          st->diag_value = (int64_t)cur;
-        }
+      if ((int64_t)(gtimer_ns() - t0) > limit_ns) {
+        record_fail(st, FAIL_GRID_BARRIER, (int)blockIdx.x, step, ns, (int64_t)cur);
         break;
       }
       __nanosleep(64);
@@ -1707,21 +1779,16 @@ __global__ void __launch_bounds__(QRP_THREADS) k_qrp_tail(Params P) {
   double flops = 0.0;
   unsigned int bar = 0;  // barriers passed in this launch
   bar += G;
-  if (!grid_barrier(st, bar, step, ns)) goto out;  // every CTA has read the state
+  // every CTA has read the state (test hook 1: one arrival more than the grid
+  // makes, so that this wait runs out)
+  if (!grid_barrier(st, bar + (P.test_fault == 1 ? 1u : 0u), step, ns, P.wait_ns)) goto out;
   for (;;) {
     if (ns >= kmin || (P.max_steps > 0 && step >= P.max_steps)) break;
     double mu;
     int64_t jstar;
     qrp_block_argmax(P.u, ns, n, s_v, s_p, &mu, &jstar);
     if (jstar < ns || jstar >= n) {  // identical in every CTA
-      if (cta == 0 && tid == 0) {
-        st->abort_flag = 1;
-        st->diag_code = 2;
-        st->diag_cta = 0;
-        st->diag_step = step;
-        st->diag_ns = ns;
-        st->diag_value = jstar;
-      }
+      if (cta == 0 && tid == 0) record_fail(st, FAIL_PIVOT_RANGE, 0, step, ns, jstar);
       break;
     }
     // stopping test (Sec. 3.4) and the DM safeguard, identical in every CTA
@@ -1766,7 +1833,7 @@ __global__ void __launch_bounds__(QRP_THREADS) k_qrp_tail(Params P) {
     __syncthreads();
     const double beta = s_sc[0], ht = s_sc[1], rden = s_sc[2];
     bar += G;
-    if (!grid_barrier(st, bar, step, ns)) break;  // all CTAs have read column jstar
+    if (!grid_barrier(st, bar, step, ns, P.wait_ns)) break;  // all CTAs have read column jstar
     // the owner of position jstar moves the columns: ns <- pivot (R part, beta,
     // v), jstar <- old column ns; it also swaps u, uref and perm
     if ((int)(jstar % G) == cta) {
@@ -1865,13 +1932,12 @@ __global__ void __launch_bounds__(QRP_THREADS) k_qrp_tail(Params P) {
       atomicAdd((unsigned long long*)&P.trace[step].nrecomp, (unsigned long long)nrec);
     flops += 4.0 * (double)mr * (double)(n - ns - 1) / G + 2.0 * (double)mr;
     bar += G;
-    if (!grid_barrier(st, bar, step, ns)) break;  // all columns and partial norms updated
+    if (!grid_barrier(st, bar, step, ns, P.wait_ns)) break;  // all columns and partial norms updated
     ++ns;
     ++step;
   }
 out:
   if (cta == 0 && tid == 0) {
-    if (*(volatile int32_t*)&st->abort_flag) st->nonfinite = 4;
     st->ns = ns;
     st->step = step;
     st->dm_on = dm_on;
@@ -1889,6 +1955,15 @@ out:
 __global__ void k_step_end(Params P) {
   DevState* st = P.st;
   if (st->done) return;
+  if (*(volatile int32_t*)&st->abort_flag) {  // a wait gave up or a check tripped in this step
+    st->done = 1;
+    return;
+  }
+  if (P.checked && !(in_range(P, KID_STEP_END, st->l, 1, (int64_t)st->k + 1) &&
+                     in_range(P, KID_STEP_END, st->ns + st->l, 1, P.kmin + 1))) {
+    st->done = 1;
+    return;
+  }
   if (P.pol.active && st->dm_on) {
     // carry for the next step's features and for the guard of the learned
     // (tau, delta), checked at the next step's start against its mu

@@ -19,12 +19,6 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void* g_ptr[MAX_DEVICES] = {};
 
-// identity permutation for an empty matrix (m == 0 with n > 0)
-__global__ void k_iota(int32_t* perm, int64_t n) {
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-    perm[j] = (int32_t)j;
-}
-
 // Device address of the scratch on the current device, looked up once.
 int scratch_address(void** out, int* cuda_err) {
   int dev = 0;
@@ -55,31 +49,9 @@ extern "C" int qrdm_factor_noalloc(double* dA, int64_t m, int64_t n, int64_t lda
                                    const qrdm_opts* opts, void* stream, qrdm_step_record* d_trace,
                                    int32_t* d_trace_J, int64_t trace_cap) {
   if (opts && opts->profile) return QRDM_ERR_UNSUPPORTED;  // profiling creates CUDA events
-  if (m == 0 || n == 0) {
-    // nothing to factor: the same argument checks as qrdm_factor, then only
-    // the identity permutation is written
-    if (m < 0) return -1;
-    if (n < 0 || n > INT32_MAX) return -2;
-    if (lda < (m > 1 ? m : 1)) return -4;
-    if (!(tau > 0.0 && tau <= 1.0)) return -5;
-    if (!(delta >= 0.0 && delta <= 1.0)) return -6;
-    if (k_max < 1 || k_max > QRDM_KMAX_LIMIT) return -7;
-    if (!d_perm && n > 0) return -9;
-    if (!info) return -10;
-    if (opts && opts->eps1_mode != 0 && opts->eps1_mode != 1) return -11;
-    for (size_t i = 0; i < sizeof(*info); ++i) ((char*)info)[i] = 0;
-    if (n > 0) {
-      k_iota<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, (cudaStream_t)stream>>>(d_perm,
-                                                                                                        n);
-      cudaError_t e = cudaGetLastError();
-      if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
-      if (e != cudaSuccess) {
-        info->cuda_error = (int32_t)e;
-        return QRDM_ERR_CUDA;
-      }
-    }
-    return QRDM_OK;
-  }
+  if (m == 0 || n == 0)  // nothing to factor: qrdm_factor checks every argument and needs no workspace
+    return qrdm_factor(dA, m, n, lda, tau, delta, k_max, d_htau, d_perm, info, opts, nullptr, 0, stream, d_trace,
+                       d_trace_J, trace_cap);
   size_t need = 0;
   if (m >= 0 && n >= 0 && n <= INT32_MAX && k_max >= 1 && k_max <= QRDM_KMAX_LIMIT) {
     if (qrdm_workspace_size(m, n, k_max, &need) == 0 && need > (size_t)QRDM_NOALLOC_SCRATCH_BYTES)

@@ -34,7 +34,7 @@ constexpr int QW = QT / 32;
 constexpr int QP3_NB_MAX = 32;     // block size cap (one lane per block column)
 constexpr int QV_ROWS = 128;       // rows of V staged per pass of the trailing update
 constexpr double QEPS = 2.220446049250313080847e-16;
-constexpr long long QSPIN = 4000000000LL;  // clock cycles before a barrier wait gives up
+constexpr long long QSPIN_NS = 2000000000LL;  // global-timer nanoseconds before a barrier wait gives up (2 s)
 
 struct alignas(128) Qp3State {
   unsigned int gbar;
@@ -74,13 +74,15 @@ __device__ bool qbarrier(Qp3State* st, unsigned int target, int64_t k) {
   if (threadIdx.x == 0) {
     unsigned int* ctr = &st->gbar;
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(ctr), "r"(1u) : "memory");
-    const long long t0 = clock64();
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     unsigned int cur = 0;
     for (;;) {
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(ctr) : "memory");
       if ((int)(cur - target) >= 0) break;
       if (*(volatile int32_t*)&st->abort_flag) break;
-      if (clock64() - t0 > QSPIN) {
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if ((long long)(t - t0) > QSPIN_NS) {
         if (atomicExch(&st->abort_flag, 1) == 0) {
           st->diag_code = 1;
           st->diag_cta = (int)blockIdx.x;
@@ -553,7 +555,13 @@ int qrdm_qp3_factor(double* dA, int64_t m, int64_t n, int64_t lda, int32_t nb, d
     return QRDM_ERR_CUDA;
   }
   if (hs.nonfinite) return QRDM_ERR_NONFINITE;
-  if (hs.abort_flag) return QRDM_ERR_INTERNAL;
+  if (hs.abort_flag) {
+    info->fail_code = hs.diag_code;
+    info->fail_cta = hs.diag_cta;
+    info->fail_step = hs.diag_k;
+    info->fail_ns = hs.diag_k;
+    return hs.diag_code == 1 ? QRDM_ERR_TIMEOUT : QRDM_ERR_INTERNAL;
+  }
   info->rank = hs.rank >= 0 ? hs.rank : kmin;
   info->rank_colmax = hs.rank_colmax >= 0 ? hs.rank_colmax : kmin;
   info->nsteps = hs.blocks;

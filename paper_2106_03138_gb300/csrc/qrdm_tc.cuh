@@ -70,10 +70,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // bounded wait on an mbarrier phase; false when the limit (clock cycles) ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
-  const long long t0 = clock64();
+// bounded wait for the phase of `parity`: false once limit_ns nanoseconds of
+// the global timer have passed without it
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit_ns) {
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > limit) return false;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if ((long long)(t - t0) > limit_ns) return false;
   }
   return true;
 }

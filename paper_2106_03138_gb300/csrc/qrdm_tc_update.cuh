@@ -35,7 +35,6 @@ constexpr int TCW_COLS = 128;   // columns per CTA of the W GEMM (its M)
 constexpr int TCU_ROWS = 128;   // rows of one update tile (its M)
 constexpr int TCU_COLS = 128;   // columns of one update tile (its N)
 constexpr int TC_LMAX = 64;     // reflectors per merged update (K of the update, N of the W GEMM)
-constexpr long long TC_WAIT = 2000000000LL;  // clock cycles before an MMA wait gives up (about 1 s)
 constexpr int TCW_TILE_A = TCW_COLS * 128;   // bytes of one A tile (128 rows x one 128-byte atom of K)
 constexpr int TCW_TILE_V = TC_LMAX * 128;    // bytes of one V tile (64 rows x one atom of K)
 constexpr int TCW_STAGE = 2 * TCW_TILE_A + 2 * TCW_TILE_V;
@@ -426,7 +425,7 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w(Params P) {
         if (i + 1 < nchunks)
           tcw_load<FMT>(buf[1 - par], colp, colok, i + 1, rbeg + (i + 1) * KA, rend, kg, vsrc, tid, al);
         if (i >= 2) {  // the MMAs of chunk i - 2 have finished with this stage and accumulator
-          if (tid == 0 && !tc::mbar_wait(&bar[s], (uint32_t)(((i >> 1) - 1) & 1), TC_WAIT)) *s_fail = 1;
+          if (tid == 0 && !tc::mbar_wait(&bar[s], (uint32_t)(((i >> 1) - 1) & 1), P.wait_ns)) *s_fail = 1;
           __syncthreads();
           if (*s_fail) break;
           tc::fence_after_sync();
@@ -471,13 +470,13 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w(Params P) {
   // the last one or two chunks are still in their accumulators; the commit of
   // the last chunk covers every MMA issued before it
   const int64_t last = nchunks - 1;
-  if (tid == 0 && !*s_fail && !tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), TC_WAIT)) *s_fail = 1;
+  if (tid == 0 && !*s_fail && !tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), P.wait_ns)) *s_fail = 1;
   __syncthreads();
   tc::fence_after_sync();
   if (*s_fail) {
     // leave no MMA writing TMEM behind: a bounded wait for the last one issued
-    if (tid == 0 && issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), TC_WAIT);
-    if (tid == 0 && atomicExch(&st->abort_flag, 1) == 0) st->diag_code = 4;
+    if (tid == 0 && issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), P.wait_ns);
+    if (tid == 0) record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TRAIL_W);
   } else {
     for (int64_t i = max((int64_t)0, last - 1); i <= last; ++i) {
 #pragma unroll
@@ -577,7 +576,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gram(Params P) {
       }
     }
     if (i >= 2) {  // the MMAs of step i - 2 have finished with this stage and accumulator
-      if (tid == 0 && !tc::mbar_wait(&bar[s], (uint32_t)(((i >> 1) - 1) & 1), TC_WAIT)) *s_fail = 1;
+      if (tid == 0 && !tc::mbar_wait(&bar[s], (uint32_t)(((i >> 1) - 1) & 1), P.wait_ns)) *s_fail = 1;
       __syncthreads();
       if (*s_fail) break;
       tc::fence_after_sync();
@@ -628,12 +627,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gram(Params P) {
     issued = i;
   }
   const int64_t last = nsteps - 1;
-  if (tid == 0 && !*s_fail && !tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), TC_WAIT)) *s_fail = 1;
+  if (tid == 0 && !*s_fail && !tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), P.wait_ns)) *s_fail = 1;
   __syncthreads();
   tc::fence_after_sync();
   if (*s_fail) {
-    if (tid == 0 && issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), TC_WAIT);
-    if (tid == 0 && atomicExch(&st->abort_flag, 1) == 0) st->diag_code = 4;
+    if (tid == 0 && issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), P.wait_ns);
+    if (tid == 0) record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_GRAM);
   } else if (drains) {
     for (int64_t i = max((int64_t)0, last - 1); i <= last; ++i) {
 #pragma unroll
@@ -739,8 +738,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
   unsigned char* base = (unsigned char*)(((uintptr_t)tcu_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* vbuf = base;        // hi atoms, then lo atoms
   unsigned char* wbuf = base + OPB;  // two buffers of OPB bytes
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 3 * OPB);  // [0,1] MMA done, [2,3] W landed, [4] V landed
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 5);
+  // [0,1] MMA done, [2,3] W landed, [4] V landed, [5] never arrived on (test hook 3)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 3 * OPB);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 6);
   volatile int* s_fail = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
   const int64_t nloc = t1 - t0;
@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
   uint32_t w_iss[2] = {0u, 0u}, w_done[2] = {0u, 0u}, v_iss = 0u, v_done = 0u;
   if (tid == 0) {
 #pragma unroll
-    for (int b = 0; b < 5; ++b) tc::mbar_init(&bar[b], 1);
+    for (int b = 0; b < 6; ++b) tc::mbar_init(&bar[b], 1);
     *s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // V for the first row block, W for the first two tiles
@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
       if (tid == 0) {
         bool ok = true;
         if (rb != cur_rb && i > 0) {  // a new row block: the MMAs issued so far still read V
-          ok = tc::mbar_wait(&bar[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1), TC_WAIT);
+          ok = tc::mbar_wait(&bar[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1), P.wait_ns);
           if (ok) {
             tc::mbar_expect_tx(&bar[4], OPB);
             tc::bulk_g2s(vbuf, P.tc_vu + rb * OPB, OPB, &bar[4]);
@@ -784,13 +784,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
           }
         }
         if (ok && rb != cur_rb) {
-          ok = tc::mbar_wait(&bar[4], v_done & 1u, TC_WAIT);
+          ok = tc::mbar_wait(&bar[4], v_done & 1u, P.wait_ns);
           if (ok) ++v_done;
         }
         if (ok) {
-          ok = tc::mbar_wait(&bar[2 + (i & 1)], (uint32_t)((i >> 1) & 1), TC_WAIT);
+          ok = tc::mbar_wait(&bar[2 + (i & 1)], (uint32_t)((i >> 1) & 1), P.wait_ns);
           if (ok) ++w_done[i & 1];
         }
+        // test hook 3: a wait nothing completes, before the first MMA (the
+        // copies already issued drain in the give-up path below)
+        if (ok && i == 0 && P.test_fault == 3) ok = tc::mbar_wait(&bar[5], 0u, P.wait_ns);
         if (ok) {
           tc::fence_after_sync();
           const uint32_t d = taddr + (uint32_t)((i & 1) * TCU_COLS);
@@ -825,7 +828,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
     if (i >= 1) {  // epilogue of tile i - 1
       const int64_t pi = i - 1, t = t0 + pi, rb = t / nct, ct = t % nct;
       if (tid == 0 && !*s_fail) {
-        if (!tc::mbar_wait(&bar[pi & 1], (uint32_t)((pi >> 1) & 1), TC_WAIT)) {
+        if (!tc::mbar_wait(&bar[pi & 1], (uint32_t)((pi >> 1) & 1), P.wait_ns)) {
           *s_fail = 1;
         } else if (pi + 2 < nloc) {  // its W buffer is free: the tile two ahead
           tc::mbar_expect_tx(&bar[2 + (pi & 1)], OPB);
@@ -864,14 +867,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
   if (*s_fail) {
     // leave no copy or MMA in flight behind: bounded waits for the last ones
     if (tid == 0) {
-      if (issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), TC_WAIT);
+      if (issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), P.wait_ns);
       for (int b = 0; b < 2; ++b)
         for (; w_done[b] < w_iss[b]; ++w_done[b])
-          if (!tc::mbar_wait(&bar[2 + b], w_done[b] & 1u, TC_WAIT)) break;
+          if (!tc::mbar_wait(&bar[2 + b], w_done[b] & 1u, P.wait_ns)) break;
       for (; v_done < v_iss; ++v_done)
-        if (!tc::mbar_wait(&bar[4], v_done & 1u, TC_WAIT)) break;
+        if (!tc::mbar_wait(&bar[4], v_done & 1u, P.wait_ns)) break;
     }
-    if (tid == 0 && atomicExch(&st->abort_flag, 1) == 0) st->diag_code = 4;
+    if (tid == 0) record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TRAIL_UPDATE);
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -43,14 +43,43 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(_binding.EXPORTS) == set(declared_functions())
 
 
-def test_struct_layouts():
+STRUCTS = ("qrdm_opts", "qrdm_policy", "qrdm_info", "qrdm_profile", "qrdm_step_record", "qrdm_batch_matrix",
+           "qrdm_batch_tuning")
+
+
+def c_layouts(tmp_path) -> dict:
+    """sizeof and offsetof of every field, as a C compiler lays out the
+    header's structs (gcc on the header alone)."""
     from paper_2106_03138_gb300 import _binding
 
-    assert ctypes.sizeof(_binding.qrdm_opts) == 48
-    assert ctypes.sizeof(_binding.qrdm_policy) == 72
-    assert ctypes.sizeof(_binding.qrdm_info) == 40
-    assert ctypes.sizeof(_binding.qrdm_profile) == 16 * 8 * 3
-    assert ctypes.sizeof(_binding.qrdm_step_record) == 80
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
+    for st in STRUCTS:
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f, _ in getattr(_binding, st)._fields_:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    res = {}
+    for line in out.splitlines():
+        st, f, v = line.split()
+        res[(st, f)] = int(v)
+    return res
+
+
+def test_struct_layouts(tmp_path):
+    """The ctypes structs of the binding match the header field by field."""
+    from paper_2106_03138_gb300 import _binding
+
+    lay = c_layouts(tmp_path)
+    for st in STRUCTS:
+        cls = getattr(_binding, st)
+        assert ctypes.sizeof(cls) == lay[(st, "size")], st
+        for f, _ in cls._fields_:
+            assert getattr(cls, f).offset == lay[(st, f)], (st, f)
 
 
 def test_workspace_size_and_argument_checks(lib):
@@ -99,8 +128,27 @@ def test_workspace_size_and_argument_checks(lib):
     o.precision = 3  # the tensor-core forms take blocks of at most 64
     rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 65, fake, fake, o, fake, 1 << 30, 0)
     assert rc == b.QRDM_ERR_UNSUPPORTED
+    # checked, wait limit and test hook values
+    for field, bad in (("checked", 2), ("checked", -1), ("wait_limit_us", -5), ("test_fault", 4),
+                       ("test_fault", -1), ("test_fault", 2), ("test_fault", 3)):
+        o = b.qrdm_opts()
+        setattr(o, field, bad)  # hook 2 needs checked = 1, hook 3 a tensor-core precision
+        rc, _ = b.qrdm_factor(fake, 4, 4, 4, 0.5, 0.5, 4, fake, fake, o, fake, 1 << 30, 0)
+        assert rc == -11, (field, bad)
+    # the same checks apply to an empty matrix (nothing to factor)
+    o = b.qrdm_opts()
+    o.precision = 9
+    rc, _ = b.qrdm_factor(0, 0, 4, 1, 0.5, 0.5, 4, 0, fake, o, 0, 0, 0)
+    assert rc == -11
+    rc, _ = b.qrdm_factor_noalloc(0, 0, 4, 1, 0.5, 0.5, 4, 0, fake, o, 0)
+    assert rc == -11
+    o.precision = 2
+    rc, _ = b.qrdm_factor_noalloc(0, 4, 0, 4, 0.5, 0.5, 65, 0, 0, o, 0)
+    assert rc == b.QRDM_ERR_UNSUPPORTED
     assert b.qrdm_strerror(2).startswith("the matrix")
-    assert lib.qrdm_version() >= 100
+    assert b.qrdm_strerror(b.QRDM_ERR_TIMEOUT).startswith("a bounded")
+    assert b.qrdm_strerror(b.QRDM_ERR_CHECKED).startswith("a checked")
+    assert lib.qrdm_version() >= 200
 
 
 def test_batched_struct_layouts():
