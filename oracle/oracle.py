@@ -22,8 +22,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qrdm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 EPS = 2.0 ** -52
 
@@ -65,6 +67,45 @@ def build(force: bool = False) -> str:
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_omp(force: bool = False) -> str | None:
+    """The same source with OpenMP on (the trailing update's column loops run
+    on all host cores, with bit-identical results): oracle/_build/
+    liboracle_omp.so, or None when the compiler has no OpenMP."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_OMP) and os.path.getmtime(_LIB_OMP) >= os.path.getmtime(_SRC):
+        return _LIB_OMP
+    tmp = _LIB_OMP + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c99", "-o", tmp,
+           _SRC, "-lm"]
+    if subprocess.run(cmd, capture_output=True).returncode != 0:
+        return None
+    os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def _declare(lib):
+    i64, f64, p = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    lib.oq_qrdm.restype = ctypes.c_int
+    lib.oq_qrdm.argtypes = [i64, i64, p, i64, f64, f64, i64, i64, i64, i64, i64, i64, i64, p, p, p, p, p, p,
+                            p, i64, p, p]
+    lib.oq_step_size.restype = i64
+    assert lib.oq_step_size() == STEP_DTYPE.itemsize, "oracle trace layout mismatch"
+
+
+def _load_omp():
+    """The OpenMP build (None if unavailable)."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            path = build_omp()
+            if path is None:
+                return None
+            lib = ctypes.CDLL(path)
+            _declare(lib)
+            _lib_omp = lib
+    return _lib_omp
 
 
 def _load():
@@ -133,8 +174,9 @@ def cosine(A: np.ndarray, cols, r0: int = 0):
 
 def qrdm(A: np.ndarray, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *, eps1_mode: int = 0,
          stop_at_rank: bool = False, check_last: bool = False, no_break: bool = False, sdd: bool = False,
-         max_steps: int = 0, trace_cap: int | None = None, schedule=None) -> dict:
-    """Factor A Pi = Q R by QRDM2.  Returns a dict:
+         max_steps: int = 0, trace_cap: int | None = None, schedule=None, parallel: bool = False) -> dict:
+    """Factor A Pi = Q R by QRDM2.  ``parallel``: run the OpenMP build (all
+    host cores on the trailing update, identical results).  Returns a dict:
 
     ``A`` (R above the diagonal, reflector tails below), ``htau``, ``perm``,
     ``rank``, ``rank_colmax``, ``u``/``uref`` (partial norms at exit),
@@ -142,6 +184,12 @@ def qrdm(A: np.ndarray, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *
     original indices of the selected columns, -1 padded), ``status``.
     """
     lib = _load()
+    if parallel:
+        if schedule is not None:
+            raise ValueError("the OpenMP build takes no schedule")
+        lib = _load_omp()
+        if lib is None:
+            raise RuntimeError("the oracle's OpenMP build is unavailable (no OpenMP in the C compiler)")
     A = np.array(A, dtype=np.float64, order="F", copy=True)
     m, n = A.shape
     kmin = min(m, n)

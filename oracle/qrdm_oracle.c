@@ -237,7 +237,6 @@ int oq_qrdm_sched(int64_t m, int64_t n, double* A, int64_t lda, double tau, doub
   double* Th = (double*)malloc(sizeof(double) * (size_t)(kmax * kmax + 1));
   double* T = (double*)malloc(sizeof(double) * (size_t)(kmax * kmax + 1));
   double* W = (double*)malloc(sizeof(double) * (size_t)(kmax * (n > 0 ? n : 1) + 1));
-  double* wc = (double*)malloc(sizeof(double) * (size_t)(kmax + 1));
 
   int dm_on = 1;
   int64_t ns = 0, step = 0;
@@ -442,7 +441,11 @@ int oq_qrdm_sched(int64_t m, int64_t n, double* A, int64_t lda, double tau, doub
     const int64_t n2 = n - j0;
     if (lacc > 0 && n2 > 0 && mr > 0) {
       oq_larft(mr, lacc, &A_(ns, ns), lda, &htau[ns], T, kmax);
+      /* the three loops below treat each trailing column on its own, in the
+         same order whether or not the OpenMP build spreads the columns over
+         threads, so both builds give identical bits */
       /* W = V^T A22  (lacc x n2) */
+#pragma omp parallel for schedule(static)
       for (int64_t j = 0; j < n2; ++j) {
         const double* a = &A_(ns, j0 + j);
         for (int64_t t = 0; t < lacc; ++t) {
@@ -452,16 +455,17 @@ int oq_qrdm_sched(int64_t m, int64_t n, double* A, int64_t lda, double tau, doub
           W[j * kmax + t] = s;
         }
       }
-      /* W = T^T W */
+      /* W = T^T W, in place: entry t needs entries q <= t, so t descends */
+#pragma omp parallel for schedule(static)
       for (int64_t j = 0; j < n2; ++j) {
-        for (int64_t t = 0; t < lacc; ++t) {
+        for (int64_t t = lacc - 1; t >= 0; --t) {
           double s = 0.0;
           for (int64_t q = 0; q <= t; ++q) s += T[t * kmax + q] * W[j * kmax + q];
-          wc[t] = s;
+          W[j * kmax + t] = s;
         }
-        for (int64_t t = 0; t < lacc; ++t) W[j * kmax + t] = wc[t];
       }
       /* A22 -= V W */
+#pragma omp parallel for schedule(static)
       for (int64_t j = 0; j < n2; ++j) {
         double* a = &A_(ns, j0 + j);
         for (int64_t t = 0; t < lacc; ++t) {
@@ -476,6 +480,10 @@ int oq_qrdm_sched(int64_t m, int64_t n, double* A, int64_t lda, double tau, doub
     /* ---- a10: partial norm update (Sec. 3.2 block form, R8/R9/R16) ---- */
     const int64_t nsn = ns + lacc;
     int64_t nrec = 0;
+    double s_recomp = rec.s_recomp;
+    /* each column on its own; the count and the smallest margin do not
+       depend on the order in which columns are visited */
+#pragma omp parallel for schedule(static) reduction(+ : nrec) reduction(min : s_recomp)
     for (int64_t j = j0; j < n; ++j) {
       if (u[j] == 0.0) continue;
       double q = 0.0;
@@ -492,7 +500,7 @@ int oq_qrdm_sched(int64_t m, int64_t n, double* A, int64_t lda, double tau, doub
         /* t is known to about c eps (uref/u)^2 */
         double amp = uref[j] / u[j];
         double tol = 1e-12 + cerr * OQ_EPS * amp * amp / sqeps;
-        if (g / tol < rec.s_recomp) rec.s_recomp = g / tol;
+        if (g / tol < s_recomp) s_recomp = g / tol;
       }
       if (test <= sqeps) {
         u[j] = (nsn < m) ? sqrt(sumsq(&A_(nsn, j), m - nsn)) : 0.0;
@@ -502,6 +510,7 @@ int oq_qrdm_sched(int64_t m, int64_t n, double* A, int64_t lda, double tau, doub
         u[j] = u[j] * sqrt(t);
       }
     }
+    rec.s_recomp = s_recomp;
     for (int64_t j = nsn; j < j0; ++j) {
       u[j] = (nsn < m) ? sqrt(sumsq(&A_(nsn, j), m - nsn)) : 0.0;
       uref[j] = u[j];
@@ -532,7 +541,6 @@ int oq_qrdm_sched(int64_t m, int64_t n, double* A, int64_t lda, double tau, doub
   free(Th);
   free(T);
   free(W);
-  free(wc);
   return 0;
 }
 
