@@ -3,14 +3,31 @@
 The permutation must be identical until the first step where the two sides
 take a different decision; that step must be one where the oracle logged a
 decision margin below the rounding uncertainty of the compared quantities
-(a tie).  Until then |R_ii| must agree within
+(a tie).  Every row of R finished before that step, and every reflector of
+it, is then compared element by element, columns matched by original index.
 
-    1e-11 |R_ii| + c eps anorm (1 + anorm / min_{i'<i} |R_i'i'|),  c = sqrt(m n),
+Row i of R is column j after i reflector applications.  Each application
+adds a rounding error of norm about sqrt(m) eps ||a_j|| (an inner product of
+length <= m, probabilistic rounding model) in its own direction, so two FP64
+programs that sum in different orders leave errors of norm about
+e_i = sqrt(m (i + 1)) eps anorm in that column.  Hence:
 
-the first-order perturbation of R_ii = dist(a_i, span(a_1..a_{i-1})) under a
-backward error c eps anorm in A (two backward-stable FP64 programs differ by
-that much); for well-separated leading columns the 1e-11 relative term
-dominates.
+* |R_ii| >= 1e-3 anorm: |R_ii| within 1e-11 relative, nothing else;
+* every other entry of those rows: |dR_ij| <= 1e-11 |R_ij| + e_i;
+* reflector tails and htau while the column stands above that error
+  (|R_ii| >= 4 e_i): v = x / (alpha - beta) with |alpha - beta| >= |R_ii|
+  and |v_k| <= 1 moves by at most 3 e_i / |R_ii| per entry, and
+  htau = 1 - alpha / beta by at most 2 e_i / |R_ii| (first order).
+* From the first row i0 whose column is rounding noise (|R_ii| < 4 e_i) on,
+  the remaining rows are fixed only up to a rotation of that noise: there
+  |R_ii| keeps its bound (the largest residual norm is known within e_i),
+  the other entries agree within e_i plus twice the largest column norm of
+  the oracle's rows i0.. (both are noise of that size), and the reflectors
+  are checked only through ||A Pi - QR|| and ||Q^T Q - I||.
+
+``compare`` returns a report with the largest error of each kind divided by
+its bound, and how many diagonal entries the relative and the absolute term
+each govern.
 """
 from __future__ import annotations
 
@@ -47,13 +64,15 @@ def is_tie(otrace, s) -> tuple[bool, float]:
     return (score < 1.0 or prev < 1.0), min(score, prev)
 
 
-def rdiag_tol(rdiag_ref: np.ndarray, anorm: float, m: int, n: int) -> np.ndarray:
+def row_err(m: int, ncmp: int, anorm: float) -> np.ndarray:
+    """e_i = sqrt(m (i + 1)) eps anorm for rows i < ncmp (module docstring)."""
+    return np.sqrt(float(max(m, 1)) * (np.arange(ncmp, dtype=np.float64) + 1.0)) * EPS * anorm
+
+
+def rdiag_tol(rdiag_ref: np.ndarray, anorm: float, m: int) -> np.ndarray:
+    """Bound on | |R_ii| - |R_ii ref| | (module docstring)."""
     d = np.abs(rdiag_ref)
-    run_min = np.minimum.accumulate(np.concatenate([[np.inf], d[:-1]]))
-    run_min = np.where(np.isfinite(run_min), run_min, anorm)
-    run_min = np.maximum(run_min, 1e-300)
-    c = np.sqrt(float(m) * float(n))
-    return 1e-11 * d + c * EPS * anorm * (1.0 + anorm / run_min)
+    return np.where(d >= 1e-3 * anorm, 1e-11 * d, 1e-11 * d + row_err(m, d.size, anorm))
 
 
 def compare(A: np.ndarray, g: dict, o: dict) -> dict:
@@ -74,19 +93,7 @@ def compare(A: np.ndarray, g: dict, o: dict) -> dict:
         assert g["rank"] == o["rank"]
     report["ncmp"] = ncmp
     assert np.array_equal(g["perm"][:ncmp], o["perm"][:ncmp])
-    dg = np.abs(np.diag(g["A"])[:ncmp])
-    do = np.abs(np.diag(o["A"])[:ncmp])
-    tol = rdiag_tol(np.diag(o["A"])[:p], anorm, m, n)[:ncmp]
-    err = np.abs(dg - do)
-    bad = np.nonzero(err > tol)[0]
-    assert bad.size == 0, f"|R_ii| differs at i={bad[:5]}: {err[bad[:5]]} > {tol[bad[:5]]}"
-    rel = err / np.maximum(do, 1e-300)
-    report["max_rel_rdiag"] = float(np.max(rel[do > 1e-3 * anorm])) if np.any(do > 1e-3 * anorm) else 0.0
-    # htau_i = 1 - alpha_i/beta_i inherits R_ii's conditioning: |d htau| <= 2 tol_i / |R_ii|
-    hg, ho = g["htau"][:ncmp], o["htau"][:ncmp]
-    htol = 2.0 * tol / np.maximum(do, 1e-300) + 1e-15
-    badh = np.nonzero(np.abs(hg - ho) > htol)[0]
-    assert badh.size == 0, f"htau differs at i={badh[:5]}: {np.abs(hg - ho)[badh[:5]]} > {htol[badh[:5]]}"
+    report.update(compare_rows(A, g, o, ncmp))
     # rank_colmax (mu <= eps1 anorm, no sqrt factor) changes no decision, so it
     # is not in the trace walk; it may differ only where the oracle's mu at
     # that step lay within the roundoff band sqrt(mn) eps anorm of the threshold
@@ -101,3 +108,69 @@ def compare(A: np.ndarray, g: dict, o: dict) -> dict:
                 mu = float(tr["mu"][hit[0]])
                 assert abs(mu - eps1 * anorm) <= band, f"rank_colmax {rc_g} vs {rc_o} without a tie"
     return report
+
+
+def compare_rows(A: np.ndarray, g: dict, o: dict, ncmp: int) -> dict:
+    """Element-wise comparison of the first ncmp rows of R (columns matched by
+    original index) and of the first ncmp reflectors, under the bounds of the
+    module docstring.  Returns the report entries."""
+    m, n = A.shape
+    rep: dict = {}
+    anorm = float(np.max(np.linalg.norm(A, axis=0))) if n else 0.0
+    if ncmp == 0 or anorm == 0.0:
+        if ncmp:  # a zero matrix: R and the reflectors are exactly zero on both sides
+            assert np.array_equal(np.triu(g["A"][:ncmp, :]), np.triu(o["A"][:ncmp, :]))
+        return rep
+    e = row_err(m, ncmp, anorm)
+    # R rows by original column
+    Rg = np.triu(g["A"][:ncmp, :])
+    Ro = np.triu(o["A"][:ncmp, :])
+    Rg_o = np.empty_like(Rg)
+    Ro_o = np.empty_like(Ro)
+    Rg_o[:, g["perm"]] = Rg
+    Ro_o[:, o["perm"]] = Ro
+    do = np.abs(np.diag(o["A"])[:ncmp])
+    dg = np.abs(np.diag(g["A"])[:ncmp])
+    # diagonal: pure relative where |R_ii| >= 1e-3 anorm
+    hi = do >= 1e-3 * anorm
+    derr = np.abs(dg - do)
+    tol_d = rdiag_tol(do, anorm, m)
+    bad = np.nonzero(derr > tol_d)[0]
+    assert bad.size == 0, f"|R_ii| differs at i={bad[:5]}: {derr[bad[:5]]} > {tol_d[bad[:5]]}"
+    rep["rdiag_rows_relative_only"] = int(hi.sum())
+    rep["rdiag_max_rel_above_1e-3"] = float(np.max(derr[hi] / do[hi])) if hi.any() else 0.0
+    lo = ~hi
+    rel_term = 1e-11 * do
+    rep["rdiag_rows_relative_governs"] = int(hi.sum() + np.sum(lo & (rel_term >= e)))
+    rep["rdiag_rows_absolute_governs"] = int(np.sum(lo & (rel_term < e)))
+    rep["rdiag_max_err_over_bound"] = float(np.max(derr / tol_d))
+    # every entry of the finished rows; from the noise onset i0 on, within
+    # the size of the noise block
+    noisy = np.nonzero(do < 4.0 * e)[0]
+    i0 = int(noisy[0]) if noisy.size else ncmp
+    rep["noise_onset_row"] = i0
+    tol_r = 1e-11 * np.abs(Ro_o) + e[:, None]
+    if i0 < ncmp:
+        tol_r[i0:] += 2.0 * float(np.max(np.linalg.norm(Ro_o[i0:], axis=0)))
+    rerr = np.abs(Rg_o - Ro_o)
+    worst = np.unravel_index(np.argmax(rerr / tol_r), rerr.shape)
+    rep["r_entries_compared"] = int(ncmp * n - ncmp * (ncmp - 1) // 2)
+    rep["r_max_err_over_bound"] = float(rerr[worst] / tol_r[worst])
+    rep["r_max_abs_err_over_eps_anorm"] = float(rerr.max() / (EPS * anorm))
+    assert rep["r_max_err_over_bound"] <= 1.0, (
+        f"R entry ({worst[0]}, original column {worst[1]}) differs by {rerr[worst]:.3e} > {tol_r[worst]:.3e}")
+    # reflector tails and htau up to the noise onset
+    live = range(i0)
+    vmax, hmax = 0.0, 0.0
+    for i in live:
+        if i + 1 < m:
+            dv = float(np.max(np.abs(g["A"][i + 1:, i] - o["A"][i + 1:, i])))
+            vmax = max(vmax, dv / (3.0 * e[i] / do[i] + 1e-15))
+        dh = abs(float(g["htau"][i]) - float(o["htau"][i]))
+        hmax = max(hmax, dh / (2.0 * e[i] / do[i] + 1e-15))
+    rep["reflectors_compared"] = i0
+    rep["v_max_err_over_bound"] = float(vmax)
+    rep["htau_max_err_over_bound"] = float(hmax)
+    assert vmax <= 1.0, f"reflector tail differs by {vmax:.3g} x its bound"
+    assert hmax <= 1.0, f"htau differs by {hmax:.3g} x its bound"
+    return rep

@@ -9,7 +9,7 @@ import pytest
 from oracle import oracle as O
 from paper_2106_03138_gb300 import inputs
 from tests._helpers import EPS, factorization_errors
-from tests._parity import compare
+from tests._parity import SCORES, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -76,6 +76,8 @@ def test_parity_with_oracle(kind, m, n, tau, delta, kmax):
     res, orth = factorization_errors(A, g["A"], g["htau"], g["perm"])
     assert res <= 1e-13 and orth <= 1e-13, (res, orth)
     assert rep["ncmp"] >= 1
+    print(f"\n[parity] {kind} {m}x{n} tau {tau} delta {delta} k_max {kmax}: " +
+          ", ".join(f"{k} {v:.3g}" if isinstance(v, float) else f"{k} {v}" for k, v in rep.items()))
 
 
 @pytest.mark.parametrize(
@@ -202,38 +204,29 @@ def _norm2(A, iters=30):
 
 @pytest.mark.parametrize("name,tau,delta,kmax", FULL)
 def test_full_size(name, tau, delta, kmax):
+    """The benchmark's matrices at full size, in its launch configuration,
+    against the oracle run to completion: identical decisions up to the
+    first logged tie, then every R entry of the rows finished before it (by
+    original column) and every reflector, element by element (tests/_parity).
+    Invariants cover the rest."""
     spec = inputs.named(name)
     A = spec.build()
     m, n = A.shape
     g = run_gpu(A, tau, delta, kmax)
-    # sampled element-wise parity: the first steps against the oracle
-    steps = 3
-    o = O.qrdm(A, tau, delta, kmax, max_steps=steps)
-    gt = {"trace": g["trace"][:steps], "J": g["J"][:steps]}
-    from tests._parity import is_tie, rdiag_tol, walk
-
-    div, ns_div = walk(gt["trace"], gt["J"], o["trace"], o["J"])
-    ns_done = int(o["trace"]["ns"][-1] + o["trace"]["l"][-1])
-    if div is not None:
-        tie, score = is_tie(o["trace"], div)
-        assert tie, f"{name}: divergence at step {div} without a tie ({score})"
-        ns_done = ns_div
-    perm_g = g["perm"]
-    if ns_done > 0:
-        assert np.array_equal(perm_g[:ns_done], o["perm"][:ns_done])
-        anorm = float(np.max(np.linalg.norm(A, axis=0)))
-        Rg = np.triu(g["A"][:ns_done, :])
-        Ro = np.triu(o["A"][:ns_done, :])
-        # the first ns_done rows of R are final after those steps
-        tol = rdiag_tol(np.diag(Ro), anorm, m, n)
-        assert np.all(np.abs(np.abs(np.diag(Rg)) - np.abs(np.diag(Ro))) <= tol)
-        # later steps reorder the trailing columns: compare R rows by original column
-        Rg_o = np.empty_like(Rg)
-        Ro_o = np.empty_like(Ro)
-        Rg_o[:, perm_g] = Rg
-        Ro_o[:, o["perm"]] = Ro
-        rows_err = np.linalg.norm(Rg_o - Ro_o, axis=1) / anorm
-        assert np.all(rows_err <= 1e-11), rows_err.max()
+    o = O.qrdm(A, tau, delta, kmax)
+    rep = compare(A, g, o)
+    # the oracle's first logged near-tie: the GPU must agree at least that far
+    # (compare() accepts a divergence only at a logged tie)
+    tr = o["trace"]
+    sc = np.min(np.stack([tr[f] for f in SCORES]), axis=0)
+    tied = np.nonzero((sc < 1.0) | (np.minimum.accumulate(tr["s_recomp"]) < 1.0))[0]
+    first_tie = int(tr["ns"][tied[0]]) if tied.size else min(m, n)
+    assert rep["ncmp"] >= first_tie
+    print(f"\n[full size] {name} tau {tau} delta {delta} k_max {kmax}: {rep['ncmp']} of {min(m, n)} columns "
+          f"identical to the oracle (first oracle near-tie at column {first_tie}; divergence at step "
+          f"{rep['diverged_at']}, tie score {rep['tie_score']}); "
+          + ", ".join(f"{k} {v:.3g}" if isinstance(v, float) else f"{k} {v}" for k, v in rep.items()
+                      if k not in ("ncmp", "diverged_at", "tie_score")))
     # invariants at full size
     perm = g["perm"]
     assert sorted(perm.tolist()) == list(range(n))
@@ -256,6 +249,33 @@ def test_full_size(name, tau, delta, kmax):
         ok = sig > 1e4 * EPS * n * sig[0]
         ratio = d[ok] / sig[ok]
         assert ratio.min() > 1e-1 and ratio.max() < 10.0, (ratio.min(), ratio.max())
+
+
+def test_mixed_precision_rank_quality_at_16384():
+    """The 16384^2 rank-8192 gap matrix (sigma geometric 1 -> 1e-3 over 8192
+    values, then 1e-14), stopping at the rank, in every reduced-precision form
+    and in FP64: each form's sigma_min(R11) / sigma_r is within 2x of the FP64
+    GPU form's (sigma_min(R11) by inverse iteration with the same start and
+    iteration count for every form), and its rank lands at the gap."""
+    from paper_2106_03138_gb300 import policy as Pol
+
+    n, r = 16384, 8192
+    sig = inputs.sigma_gap_geometric(n, r)
+    A0 = inputs.from_spectrum_gpu(n, n, sig, 0)
+    ws = torch.empty(q.qrdm_workspace_size(n, n, 64), dtype=torch.uint8, device=A0.device)
+    qual = {}
+    for prec in (0, 1, 3, 2):
+        dA = A0.clone()
+        f = q.factor(dA, 0.15, 0.9, 64, workspace=ws, precision=prec, stop_at_rank=True)
+        torch.cuda.synchronize()
+        assert abs(f.rank_colmax - r) <= 64, (prec, f.rank_colmax)
+        qual[prec] = float(Pol.smin_r11([dA], [r], iters=80)[0]) / float(sig[r - 1])
+        del dA
+    print("\n[16384^2] sigma_min(R11)/sigma_r: " + ", ".join(f"precision {p} {v:.4f}" for p, v in qual.items()))
+    for prec in (1, 2, 3):
+        assert qual[prec] >= 0.5 * qual[0], (prec, qual)
+    del A0, ws
+    torch.cuda.empty_cache()
 
 
 # ----------------------------------------------------------------- equality edges

@@ -40,7 +40,7 @@ def test_noalloc_matches_qrdm_factor_on_consecutive_calls(shape, kmax):
     assert need <= b.QRDM_NOALLOC_SCRATCH_BYTES
     Aref, href, pref, rank, rank_cm = _reference(A, tau, delta, kmax)
     anorm = float(np.max(np.linalg.norm(A, axis=0)))
-    tol = rdiag_tol(np.diag(Aref), anorm, m, n)
+    tol = rdiag_tol(np.diag(Aref), anorm, m)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
         dA = q.colmajor(A)
