@@ -46,6 +46,38 @@ def metric_flops(m: int, n: int) -> float:
     return 4.0 * m * n * n - 4.0 * n ** 3 / 3.0
 
 
+def executed_flops(m: int, n: int, r: int) -> float:
+    """The metric's count for the work actually done when the factorization
+    stops after r columns: twice the Householder flops of the first r
+    columns, 2 * sum_{i<r} 4 (m - i)(n - i) ~ 8 (m n r - (m + n) r^2 / 2 +
+    r^3 / 3); equals metric_flops(m, n) at r = n <= m."""
+    return 8.0 * (m * n * r - (m + n) * r * r / 2.0 + r ** 3 / 3.0)
+
+
+def host_cpu() -> dict:
+    """Core count and CPU model of this host."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown", "machine": os.uname().machine}
+
+
 def cpu_sample_matrices():
     from paper_2106_03138_gb300 import inputs
 
@@ -58,22 +90,40 @@ def cpu_sample_matrices():
     return out
 
 
-def time_oracle_sample(mats) -> tuple[float, float]:
-    """(seconds, metric flops) of the CPU oracle on the sample (single thread)."""
+def time_oracle_sample(mats, parallel: bool = False) -> tuple[float, float]:
+    """(seconds, metric flops) of the CPU oracle on the sample: the plain
+    single-threaded build, or (parallel) its OpenMP build on every host core
+    (identical results)."""
     from oracle import oracle as orc
 
     t0 = time.perf_counter()
     fl = 0.0
     for A in mats:
-        r = orc.qrdm(A, TAU, DELTA, KMAX)
+        r = orc.qrdm(A, TAU, DELTA, KMAX, parallel=parallel)
         assert r["status"] == 0
         fl += metric_flops(*A.shape)
     return time.perf_counter() - t0, fl
 
 
-def sample_desc() -> str:
-    return ("oracle (single-threaded C, -O2) on the workload recipes at half linear size: " +
-            ", ".join(f"{k} {m}x{n}" for k, m, n in CPU_SAMPLE))
+def oracle_parallel_available() -> bool:
+    from oracle import oracle as orc
+
+    return orc.build_omp() is not None
+
+
+CPU_SAMPLE_DESC = ("the workload's recipes at half linear size: " +
+                   ", ".join(f"{k} {m}x{n}" for k, m, n in CPU_SAMPLE) + f" (tau {TAU}, delta {DELTA}, k_max {KMAX})")
+
+
+def sample_desc(parallel: bool) -> str:
+    kind = ("the oracle's OpenMP build (C, -O2, trailing update on every host core, results identical to the "
+            "single-threaded build)" if parallel else "the oracle (single-threaded C, -O2)")
+    return f"{kind} on {CPU_SAMPLE_DESC}"
+
+
+def cpu_config() -> dict:
+    return {"workload": "CPU sample: " + CPU_SAMPLE_DESC, "matrices": [f"{k}{m}x{n}" for k, m, n in CPU_SAMPLE],
+            "tau": TAU, "delta": DELTA, "k_max": KMAX, "global_batch": len(CPU_SAMPLE), "parallelism": "host cores"}
 
 
 class ClockSampler:
@@ -185,11 +235,13 @@ def run_reference(args, sample=None) -> int:
     if rank != 0:
         return 0
     mats = cpu_sample_matrices() if sample is None else sample
+    par = oracle_parallel_available()
+    cpu = host_cpu()
     for _ in range(args.warmup):
-        time_oracle_sample(mats)
+        time_oracle_sample(mats, parallel=par)
     secs, fl = 0.0, 0.0
     for _ in range(args.steps):
-        s, f = time_oracle_sample(mats)
+        s, f = time_oracle_sample(mats, parallel=par)
         secs += s
         fl += f
     value = fl / secs / 1e9
@@ -197,8 +249,9 @@ def run_reference(args, sample=None) -> int:
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(world),
-        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample_desc()},
+        "config": cpu_config(),
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cpu["nproc"] if par else 1, "kind": "oracle",
+                         "sample": sample_desc(par), **cpu},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -247,13 +300,18 @@ def measure_c3(q, inputs, torch, stream, hbm_gbs: float | None = None) -> dict:
     A22 -= V W reads and writes it: 8 and 16 bytes per element per step)."""
     import numpy as np
 
+    from paper_2106_03138_gb300 import policy as Pol
+
     n = 16384
     r = n // 2
     sig = inputs.sigma_gap_geometric(n, r)
     A0 = inputs.from_spectrum_gpu(n, n, sig, 0)
     ws = torch.empty(q.qrdm_workspace_size(n, n, KMAX), dtype=torch.uint8, device=A0.device)
     out = {"workload": "16384x16384, sigma geometric 1->1e-3 over 8192 values then 1e-14; stop at the rank",
-           "tau": TAU, "delta": DELTA, "k_max": KMAX}
+           "tau": TAU, "delta": DELTA, "k_max": KMAX,
+           "flops_note": "GFLOP/s applies the metric 4mn^2-4n^3/3 to the whole matrix (full-rank equivalent); "
+                         "executed_GFLOP/s counts the metric's convention (2x Householder) for the columns "
+                         "factored before the stop at the rank"}
     flops = metric_flops(n, n)
     forms = ((0, "fp64"), (1, "mixed_fp32"), (3, "tc_3xtf32"), (2, "tc_bf16x3"))
     for prec, key in forms:
@@ -270,8 +328,16 @@ def measure_c3(q, inputs, torch, stream, hbm_gbs: float | None = None) -> dict:
         # rank quality as in the paper (Sec. 5): d_i / sigma_i, d_i the sorted |R_ii|, i < r
         d = torch.sort(torch.diagonal(dA)[:r].abs(), descending=True).values.cpu().numpy()
         ratio = d / sig[:r]
-        out[key] = {"ms": ms, "GFLOP/s": flops / ms / 1e6, "rank": f.rank, "rank_colmax": f.rank_colmax,
-                    "steps": f.nsteps, "d_over_sigma_min": float(ratio.min()), "d_over_sigma_max": float(ratio.max())}
+        # and the acceptance measure sigma_min(R11) / sigma_r (inverse iteration,
+        # the same start and iteration count for every form)
+        smin = float(Pol.smin_r11([dA], [r], iters=80)[0]) / float(sig[r - 1])
+        exe = executed_flops(n, n, f.rank)
+        out[key] = {"ms": ms, "GFLOP/s": flops / ms / 1e6, "executed_GFLOP/s": exe / ms / 1e6,
+                    "executed_columns": f.rank, "rank": f.rank, "rank_colmax": f.rank_colmax,
+                    "steps": f.nsteps, "d_over_sigma_min": float(ratio.min()), "d_over_sigma_max": float(ratio.max()),
+                    "smin_R11_over_sigma_r": smin}
+        if key != "fp64":
+            out[key]["quality_vs_fp64"] = smin / out["fp64"]["smin_R11_over_sigma_r"]
         if prec >= 2:
             pr = q.qrdm_profile()
             dA = A0.clone()
@@ -509,6 +575,40 @@ def measure_c5(q, torch, stream, n_train: int = 150, n_held: int = 60, big: int 
     return out
 
 
+def forms_summary(c3, c4, c5) -> dict:
+    """The forms of the metric's comparison "vs plain FP64 GPU QRDM at equal
+    rank quality", compactly: the 16384^2 mixed-precision forms, the batched
+    form and the learned (tau, delta), each against its plain FP64 GPU
+    comparator."""
+    out = {}
+    if c3:
+        f3 = {}
+        for key in ("fp64", "mixed_fp32", "tc_3xtf32", "tc_bf16x3"):
+            r = c3.get(key)
+            if r:
+                f3[key] = {"ms": round(r["ms"], 1), "speedup": round(c3["fp64"]["ms"] / r["ms"], 2),
+                           "executed_GFLOP/s": round(r["executed_GFLOP/s"], 1),
+                           "smin_R11_over_sigma_r": r.get("smin_R11_over_sigma_r"),
+                           "quality_vs_fp64": r.get("quality_vs_fp64"), "rank_colmax": r["rank_colmax"]}
+        out["c3_16384_gap"] = f3
+    if c4:
+        out["c4_batch2000"] = {"batched_ms": round(c4["batched"]["ms"], 1),
+                               "plain_ms": round(c4["plain_fp64_per_matrix"]["ms"], 1),
+                               "speedup": round(c4["speedup_vs_plain"], 2),
+                               "quality_min_ratio": c4["rank_quality_sample"]["min_ratio_batched_over_plain"]}
+    if c5:
+        hs = c5.get("held_out_seeds")
+        if hs:
+            out["c5_learned_4096"] = {"seeds": hs["seeds"], "speedup_median": hs["speedup_median"],
+                                      "speedup_min": hs["speedup_min"], "quality_ratio_min": hs["quality_ratio_min"],
+                                      "quality_ratio_median": hs["quality_ratio_median"]}
+        else:
+            hsn = c5["held_out_single"]
+            out["c5_learned_4096"] = {"speedup": round(hsn["speedup"], 3),
+                                      "quality_ratio": round(hsn["quality_ratio"], 3)}
+    return out
+
+
 def config_dict(world: int) -> dict:
     return {"workload": WORKLOAD_DESC, "matrices": list(WORKLOAD), "tau": TAU, "delta": DELTA, "k_max": KMAX,
             "global_batch": 3 * world, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -583,7 +683,6 @@ def main() -> int:
         step()
     torch.cuda.synchronize()
 
-    prof = q.qrdm_profile()
     step_ms = []
     launches = 0
     infos = None
@@ -598,7 +697,7 @@ def main() -> int:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            nl, infos = step(prof)
+            nl, infos = step()
             e1.record(stream)
             e1.synchronize()
             launches += nl
@@ -611,6 +710,22 @@ def main() -> int:
     torch.cuda.synchronize()
     total_ms = max_over_ranks(sum(step_ms), device=dev)
     value = aggregate_gflops(world, flops_step, args.steps, total_ms)
+
+    # kernel durations: a second timed pass over the same steps with CUDA
+    # events around every launch (the events add host work between launches,
+    # not device time to a kernel), kept apart from the headline value
+    prof = q.qrdm_profile()
+    prof_steps = max(1, min(args.steps, 2))
+    prof_ms = 0.0
+    for _ in range(prof_steps):
+        restore()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(prof)
+        e1.record(stream)
+        e1.synchronize()
+        prof_ms += e0.elapsed_time(e1)
 
     # dominant kernel and its roofline (FP64 ALU bound)
     ms = list(prof.ms)
@@ -628,7 +743,9 @@ def main() -> int:
         "frac": achieved / peak if peak else None, "traffic": traffic_for(kname),
         "peak_source": "FP64 FMA rate 2/clk/SM x 152 SMs x sm_max_mhz (derived; nominal 1.25 TFLOP/s)",
         "share_of_kernel_time": ms[kid] / total_kernel_ms if total_kernel_ms else None,
-        "kernel_ms": {q.KERNEL_NAMES[i]: round(ms[i], 3) for i in range(len(q.KERNEL_NAMES))},
+        "launches_timed": nlaunch, "profiled_steps": prof_steps,
+        "profiled_ms_per_step": prof_ms / prof_steps,
+        "kernel_ms_per_step": {q.KERNEL_NAMES[i]: round(ms[i] / prof_steps, 3) for i in range(len(q.KERNEL_NAMES))},
     }
 
     # end to end through the public API with host buffers (pinned)
@@ -718,9 +835,18 @@ def main() -> int:
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        secs, fl = time_oracle_sample(cpu_sample_matrices())
-        cpu = {"value": fl / secs / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample_desc(),
-               "seconds": secs}
+        mats = cpu_sample_matrices()
+        host = host_cpu()
+        secs1, fl = time_oracle_sample(mats)
+        single = {"value": fl / secs1 / 1e9, "cores": 1, "seconds": secs1, "sample": sample_desc(False)}
+        if oracle_parallel_available():
+            secs, fl = time_oracle_sample(mats, parallel=True)
+            cpu = {"value": fl / secs / 1e9, "unit": "GFLOP/s", "cores": host["nproc"], "kind": "oracle",
+                   "sample": sample_desc(True), "seconds": secs, **host, "single_thread": single}
+        else:
+            cpu = {"value": single["value"], "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                   "sample": single["sample"], "seconds": secs1, **host,
+                   "all_cores": "unavailable: the C compiler has no OpenMP"}
 
     if rank == 0:
         per = [{"matrix": nm, "m": m, "n": n, "rank": f.rank, "rank_colmax": f.rank_colmax, "steps": f.nsteps}
@@ -733,6 +859,7 @@ def main() -> int:
             "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": csum, "gpu_launches": launches, "wall_s": t_wall, "per_matrix": per,
             "comparators": comparators, "mixed_precision_c3": c3, "batched_c4": c4, "learned_c5": c5,
+            "forms": forms_summary(c3, c4, c5),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
