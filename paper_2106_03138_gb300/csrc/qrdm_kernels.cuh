@@ -938,11 +938,11 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
   const int64_t rb = r0 + (int64_t)crank * rpc;
   const int64_t re = min(m, rb + rpc);
   __shared__ double s_slot[2][2 * PB];
-  __shared__ double s_part[MAX_CLUSTER][2 * PB];
   __shared__ double s_tot[2 * PB];
   __shared__ double s_y[PB];
   __shared__ double s_T[PB][PB];
   __shared__ double s_sc[8];
+  __shared__ double s_rden[PB], s_beta[PB];  // per reflector: 1 / (alpha - beta) and beta (applied at the end)
   extern __shared__ double s_pan[];  // SMEM: [PB][lds]
   const int lane = tid & 31, wp = tid >> 5;
   const int nw = PANEL_THREADS / 32;
@@ -967,6 +967,11 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
     V.c0 = r0;
   }
   const double eps_s = st->eps_s;
+  // The FP32-class form applies each sub-panel with the panel's compact-WY T;
+  // every other form gets W = T^T V^T A by forward substitution with V^T V,
+  // which its W pass computes on all SMs, so the panel skips T and the dot
+  // products it would need (v_t^T v_l, t < l).
+  const bool keep_t = P.mixed != 0;
   int lacc = w;
   bool broke = false;
   double flops = 0.0;
@@ -976,7 +981,10 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
     double* slot = s_slot[l & 1];
     const int64_t i0 = max(rb, p + 1);
     const bool own_p = (p >= rb && p < re);
-    for (int t = wp; t < w; t += nw) {
+    const int lo = keep_t ? 0 : l;  // first column whose dot product this reflector needs
+    // partial dot products x_l^T x_t over this CTA's rows below the pivot
+    // (t = l: the squared tail norm), and the pivot-row entries
+    for (int t = lo + wp; t < w; t += nw) {
       double acc = 0.0;
       for (int64_t i = i0 + lane; i < re; i += 32) acc = fma(V.at(i, l), V.at(i, t), acc);
 #pragma unroll
@@ -987,47 +995,43 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
       }
     }
     cluster.sync();
-    // gather every CTA's partial vector in parallel, then sum in rank order
-    for (int e = tid; e < cs * 2 * PB; e += PANEL_THREADS) {
-      const int c = e / (2 * PB), f = e % (2 * PB);
-      const int t = (f < PB) ? f : f - PB;
-      if (t < w) {
-        const double* rs = cluster.map_shared_rank(&s_slot[l & 1][0], c);
-        s_part[c][f] = rs[f];
+    // cluster-wide sums: lane c of a warp reads CTA c's partial, a shuffle
+    // tree adds them (the same tree, so the same bits, in every CTA)
+    {
+      const int nv = w - lo;
+      for (int e = wp; e < 2 * nv; e += nw) {
+        const int f = (e < nv) ? lo + e : PB + lo + (e - nv);
+        double x = 0.0;
+        if (lane < cs) x = cluster.map_shared_rank(&s_slot[l & 1][0], lane)[f];
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) s_tot[f] = x;
       }
     }
     __syncthreads();
-    if (tid < 2 * PB) {
-      const int t = (tid < PB) ? tid : tid - PB;
-      if (t < w) {
-        double s = 0.0;
-        for (int c = 0; c < cs; ++c) s += s_part[c][tid];
-        s_tot[tid] = s;
-      }
-    }
-    __syncthreads();
-    // the reflector's scalars, once per CTA (FP64 sqrt and division are long
-    // instruction sequences on this GPU; one thread computes, all read)
+    // the reflector's scalars in warp 0: beta from the norm, then the two
+    // quotients htau = (beta - alpha) / beta and 1 / (alpha - beta) at once in
+    // lanes 0 and 1 (FP64 division is a long instruction sequence here)
     const int lg = jb + l;  // column index within the whole panel
-    if (tid == 0) {
+    if (wp == 0) {
       const double alpha = s_tot[PB + l];
       const double s2 = s_tot[l];
       const double nrm = sqrt(alpha * alpha + s2);
-      const bool check = (lg >= 1) && !P.no_break && (P.check_last ? (lg < k) : (lg + 1 < k));
-      s_sc[4] = (check && nrm < eps_s) ? 1.0 : 0.0;
-      if (s2 == 0.0) {
-        s_sc[0] = alpha;  // beta
-        s_sc[1] = 0.0;    // htau
-        s_sc[2] = 0.0;    // 1 / (alpha - beta)
-      } else {
-        const double beta = (alpha >= 0.0) ? -nrm : nrm;
+      const double beta = (s2 == 0.0) ? alpha : ((alpha >= 0.0) ? -nrm : nrm);
+      const double num = (lane == 0) ? (beta - alpha) : 1.0;
+      const double den = (lane == 0) ? beta : (alpha - beta);
+      const double qv = num / den;
+      const double q1 = __shfl_sync(0xffffffffu, qv, 1);
+      if (lane == 0) {
+        const bool check = (lg >= 1) && !P.no_break && (P.check_last ? (lg < k) : (lg + 1 < k));
+        s_sc[4] = (check && nrm < eps_s) ? 1.0 : 0.0;
         s_sc[0] = beta;
-        s_sc[1] = (beta - alpha) / beta;
-        s_sc[2] = 1.0 / (alpha - beta);
+        s_sc[1] = (s2 == 0.0) ? 0.0 : qv;  // htau (a zero tail: H = I)
+        s_sc[2] = (s2 == 0.0) ? 0.0 : q1;  // 1 / (alpha - beta)
       }
     }
     __syncthreads();
-    flops += 2.0 * (double)(m - p - 1) * w;
+    flops += 2.0 * (double)(m - p - 1) * (w - lo);
     if (s_sc[4] != 0.0) {  // break test of Alg. 4 (identical in every CTA)
       lacc = l;
       broke = true;
@@ -1035,21 +1039,24 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
     }
     const double beta = s_sc[0], ht = s_sc[1], rden = s_sc[2];
     minb = fmin(minb, fabs(beta));
-    // compact-WY T_j column l (rank-0 CTA): y_t = v_t^T v_l for t < l
-    if (crank == 0) {
-      if (tid < l) s_y[tid] = s_tot[PB + tid] + s_tot[tid] * rden;
+    if (tid == 0) {
+      s_rden[l] = (ht != 0.0) ? rden : 1.0;  // v_l = x_l / (alpha - beta) below the pivot
+      s_beta[l] = beta;
+      if (crank == 0) P.htau[p] = ht;
+    }
+    if (keep_t && crank == 0) {
+      // compact-WY T_j column l: y_t = v_t^T v_l for t < l, from the unscaled
+      // x_t (v_t = x_t / (alpha_t - beta_t) below its pivot, scaled at the end)
+      if (tid < l) s_y[tid] = s_rden[tid] * (s_tot[PB + tid] + s_tot[tid] * rden);
       __syncthreads();
       if (tid < l) {
         double sacc = 0.0;
         for (int q = tid; q < l; ++q) sacc += s_T[tid][q] * s_y[q];
         s_T[tid][l] = (ht == 0.0) ? 0.0 : -ht * sacc;
       }
-      if (tid == 0) {
-        s_T[l][l] = ht;
-        P.htau[p] = ht;
-      }
+      if (tid == 0) s_T[l][l] = ht;
     }
-    // apply H_l to the rest of the sub-panel (own rows)
+    // apply H_l to the rest of the sub-panel (own rows); x_l stays unscaled
     if (ht != 0.0) {
       for (int t = l + 1 + wp; t < w; t += nw) {
         const double hw = ht * (s_tot[PB + t] + s_tot[t] * rden);
@@ -1060,12 +1067,15 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
       flops += 2.0 * (double)(m - p) * (w - l - 1);
     }
     __syncthreads();
-    // store v_l (scaled tail) and beta
-    if (ht != 0.0)
-      for (int64_t i = i0 + tid; i < re; i += PANEL_THREADS) V.at(i, l) = V.at(i, l) * rden;
-    if (own_p && tid == 0) V.at(p, l) = beta;
-    __syncthreads();
   }
+  // the accepted columns become v_t below the pivot and beta_t on it
+  for (int t = wp; t < lacc; t += nw) {
+    const int64_t pt = r0 + t;
+    const double sc = s_rden[t];
+    for (int64_t i = max(rb, pt + 1) + lane; i < re; i += 32) V.at(i, t) = V.at(i, t) * sc;
+    if (pt >= rb && pt < re && lane == 0) V.at(pt, t) = s_beta[t];
+  }
+  __syncthreads();
   if (SMEM) {  // write the slice back
     for (int t = wp; t < w; t += nw) {
       double* dst = A + (r0 + t) * lda;
@@ -1074,10 +1084,11 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
   }
   cluster.sync();  // every gather of this CTA's shared memory is done
   if (crank == 0) {
-    for (int e = tid; e < lacc * lacc; e += PANEL_THREADS) {
-      const int r = e % lacc, c = e / lacc;
-      P.T[(int64_t)c * KMAX + r] = (r <= c) ? s_T[r][c] : 0.0;
-    }
+    if (keep_t)
+      for (int e = tid; e < lacc * lacc; e += PANEL_THREADS) {
+        const int r = e % lacc, c = e / lacc;
+        P.T[(int64_t)c * KMAX + r] = (r <= c) ? s_T[r][c] : 0.0;
+      }
     if (tid == 0) {
       st->cur_lj = lacc;
       st->l += lacc;
@@ -1166,6 +1177,18 @@ struct WGeom {
   int64_t qstride, tstride, cofs;
 };
 
+// Columns of a sub-panel's W pass (j >= 0, every form but the FP32-class
+// one): first the sub-panel's own l accepted columns, read as V (so their
+// partials sum to S = V^T V, which replaces the compact-WY T), then the
+// columns it updates, [c0, cend).  Logical column c maps to a matrix column.
+struct WCols {
+  int64_t r0, c0;  // first sub-panel column, first updated column
+  int ns;          // S columns in front (0: none)
+  __device__ __forceinline__ int64_t phys(int64_t c) const { return c < ns ? r0 + c : c0 + (c - ns); }
+};
+
+__device__ __forceinline__ bool w_has_s(const Params& P, int j) { return j >= 0 && !P.mixed; }
+
 // sub-panel updates of the merged form reach at most 64 columns (the rest of
 // the panel): more row chunks keep the SMs busy, their partials packed 64
 // columns wide so that up to wchunks * n / 64 of them fit the buffer
@@ -1176,7 +1199,10 @@ constexpr int NARROW_COLS = 64;
 // block per pass), at most wchunks of them.
 __device__ __forceinline__ int64_t w32_rows_per(const Params& P, int64_t mr);
 
-__device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int64_t mr, int64_t narrow_c0 = -1) {
+// n2: columns of the pass; narrow_c0 >= 0: the pass covers matrix columns
+// [narrow_c0, narrow_c0 + span) of a merged form's panel, packed 64 wide
+__device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int64_t mr, int64_t narrow_c0 = -1,
+                                        int64_t span = 0) {
   WGeom g;
   g.qstride = (int64_t)P.kmax * P.n;
   g.tstride = P.n;
@@ -1192,7 +1218,7 @@ __device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int6
   g.nct = (n2 + g.cols - 1) / g.cols;
   int cap = P.wchunks;
   const int64_t fit = (int64_t)P.wchunks * P.n / NARROW_COLS;  // packed chunks the buffer holds
-  if (narrow_c0 >= 0 && n2 <= NARROW_COLS && fit >= 1) {
+  if (narrow_c0 >= 0 && span <= NARROW_COLS && fit >= 1) {
     cap = (int)min((int64_t)NARROW_WCHUNKS, fit);
     g.qstride = (int64_t)P.kmax * NARROW_COLS;
     g.tstride = NARROW_COLS;
@@ -1204,8 +1230,8 @@ __device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int6
 }
 
 template <int TG, int NQ, typename TC>
-__device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int l, int64_t ns, int64_t j0,
-                                             int64_t mr, const WGeom& g, int64_t cend) {
+__device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int l, int64_t ns, const WCols& wc,
+                                             int64_t mr, const WGeom& g, int64_t ncol_all) {
   constexpr int COLS = GEMM_THREADS / TG;
   constexpr int LDA_S = COLS + 1;
   constexpr int LDV_S = KMAX + 1;
@@ -1217,8 +1243,8 @@ __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int 
   const int64_t units = g.nct * g.nrc;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t ct = u % g.nct, rc = u / g.nct;
-    const int64_t cbase = j0 + ct * COLS;
-    const int ncols = (int)min((int64_t)COLS, cend - cbase);
+    const int64_t cbase = ct * COLS;  // logical
+    const int ncols = (int)min((int64_t)COLS, ncol_all - cbase);
     const int64_t rbeg = rc * g.rows_per, rend = min(mr, rbeg + g.rows_per);
     TC acc[NQ];
 #pragma unroll
@@ -1229,7 +1255,10 @@ __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int 
       for (int e = tid; e < TW_SUB * COLS; e += GEMM_THREADS) {
         const int cc = e / TW_SUB, rr = e % TW_SUB;
         double v = 0.0;
-        if (rr < rows && cc < ncols) v = P.A[(cbase + cc) * lda + ns + r0 + rr];
+        if (rr < rows && cc < ncols) {
+          const int64_t cl = cbase + cc;
+          v = (cl < wc.ns) ? vget(P.A, lda, ns, r0 + rr, (int)cl) : P.A[wc.phys(cl) * lda + ns + r0 + rr];
+        }
         s_a[rr * LDA_S + cc] = (TC)v;
       }
       for (int e = tid; e < TW_SUB * l; e += GEMM_THREADS) {
@@ -1248,10 +1277,11 @@ __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int 
     }
     if (c < ncols) {
       double* out = P.Wp + rc * g.qstride;
+      const int64_t pc = wc.phys(cbase + c) - g.cofs;
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
         const int t = tg + q * TG;
-        if (t < l) out[(int64_t)t * g.tstride + cbase + c - g.cofs] = (double)acc[q];
+        if (t < l) out[(int64_t)t * g.tstride + pc] = (double)acc[q];
       }
     }
   }
@@ -1270,43 +1300,55 @@ __device__ __forceinline__ void trail_w_kernel(Params& P, int j) {
   const int64_t cend = trail_end(P, st, j);
   const int64_t n2 = cend - j0, mr = P.m - ns;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_W, 2.0 * (double)mr * (double)n2 * l);
+  WCols wc;
+  wc.r0 = ns;
+  wc.c0 = j0;
+  wc.ns = w_has_s(P, j) ? l : 0;
+  const int64_t ncol_all = wc.ns + n2;
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_W, 2.0 * (double)mr * (double)ncol_all * l);
   extern __shared__ double smw[];
-  const WGeom g = w_geom(P, l, n2, mr, (P.merged && j >= 0) ? j0 : -1);
+  const WGeom g = w_geom(P, l, ncol_all, mr, (P.merged && j >= 0) ? ns : -1, cend - ns);
   const int tg = w_tg(l);
   const int nq = (l + tg - 1) / tg;
   if (tg == 1) {
-    trail_w_body<1, 1, TC>(P, smw, l, ns, j0, mr, g, cend);
+    trail_w_body<1, 1, TC>(P, smw, l, ns, wc, mr, g, ncol_all);
   } else if (tg == 2) {
-    if (nq == 1) trail_w_body<2, 1, TC>(P, smw, l, ns, j0, mr, g, cend);
-    else trail_w_body<2, 2, TC>(P, smw, l, ns, j0, mr, g, cend);
+    if (nq == 1) trail_w_body<2, 1, TC>(P, smw, l, ns, wc, mr, g, ncol_all);
+    else trail_w_body<2, 2, TC>(P, smw, l, ns, wc, mr, g, ncol_all);
   } else if (tg == 4) {
-    if (nq == 1) trail_w_body<4, 1, TC>(P, smw, l, ns, j0, mr, g, cend);
-    else trail_w_body<4, 2, TC>(P, smw, l, ns, j0, mr, g, cend);
+    if (nq == 1) trail_w_body<4, 1, TC>(P, smw, l, ns, wc, mr, g, ncol_all);
+    else trail_w_body<4, 2, TC>(P, smw, l, ns, wc, mr, g, ncol_all);
   } else {
     switch (nq) {
-      case 1: trail_w_body<8, 1, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 2: trail_w_body<8, 2, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 3: trail_w_body<8, 3, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 4: trail_w_body<8, 4, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 5: trail_w_body<8, 5, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 6: trail_w_body<8, 6, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 7: trail_w_body<8, 7, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 8: trail_w_body<8, 8, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 9: trail_w_body<8, 9, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 10: trail_w_body<8, 10, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 11: trail_w_body<8, 11, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 12: trail_w_body<8, 12, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 13: trail_w_body<8, 13, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 14: trail_w_body<8, 14, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      case 15: trail_w_body<8, 15, TC>(P, smw, l, ns, j0, mr, g, cend); break;
-      default: trail_w_body<8, 16, TC>(P, smw, l, ns, j0, mr, g, cend); break;
+      case 1: trail_w_body<8, 1, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 2: trail_w_body<8, 2, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 3: trail_w_body<8, 3, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 4: trail_w_body<8, 4, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 5: trail_w_body<8, 5, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 6: trail_w_body<8, 6, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 7: trail_w_body<8, 7, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 8: trail_w_body<8, 8, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 9: trail_w_body<8, 9, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 10: trail_w_body<8, 10, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 11: trail_w_body<8, 11, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 12: trail_w_body<8, 12, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 13: trail_w_body<8, 13, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 14: trail_w_body<8, 14, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      case 15: trail_w_body<8, 15, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
+      default: trail_w_body<8, 16, TC>(P, smw, l, ns, wc, mr, g, ncol_all); break;
     }
   }
 }
 
 __global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P, int j) { trail_w_kernel<double>(P, j); }
 
+// W = T^T sum(partials), the partials of k_trail_w's row chunks.  For a
+// sub-panel (j >= 0, every form but the FP32-class one) T is not formed:
+// with S = V^T V from the W pass, T^-1 = strict_upper(S) + diag(1/htau)
+// (Schreiber & Van Loan's compact WY in the inverse form of Puglisi), so
+// W solves (T^-1)^T W = V^T A by forward substitution,
+//   W_t = htau_t (P_t - sum_{q<t} S_qt W_q),
+// which a zero htau_t (H_t = I) turns into W_t = 0 as T's zero column would.
 __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j) {
   DevState* st = P.st;
   if (st->done) return;
@@ -1316,31 +1358,58 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j)
   const int64_t cend = trail_end(P, st, j);
   const int64_t n2 = cend - j0, mr = P.m - sg.r0;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  const bool use_s = w_has_s(P, j);
+  const int nsx = use_s ? l : 0;
   const int64_t nct = (n2 + TW_COLS - 1) / TW_COLS;
-  const WGeom g = w_geom(P, l, n2, mr, (P.merged && j >= 0) ? j0 : -1);  // row chunks of k_trail_w
+  // the row chunks of k_trail_w (k_trail_w32 in the FP32-class form)
+  const WGeom g = w_geom(P, l, nsx + n2, mr, (P.merged && j >= 0) ? sg.r0 : -1, cend - sg.r0);
   const int64_t nrc = g.nrc;
   if (blockIdx.x == 0 && threadIdx.x == 0)
     add_flops(st, KID_TRAIL_WREDUCE, (double)n2 * l * ((double)(nrc - 1) + (l + 1.0)));
   __shared__ double s_w[KMAX][TW_COLS + 1];
+  __shared__ double s_S[PB][PB + 1];
+  __shared__ double s_tau[PB];
   const int tid = threadIdx.x;
   const int c = tid % TW_COLS, tg = tid / TW_COLS, TG = GEMM_THREADS / TW_COLS;
+  if (use_s) {  // S_qt = v_q^T v_t (q < t < l <= PB) and htau, once per CTA
+    for (int e = tid; e < l * l; e += GEMM_THREADS) {
+      const int q = e / l, t = e % l;
+      double sv = 0.0;
+      if (q < t)
+        for (int64_t ch = 0; ch < nrc; ++ch) sv += P.Wp[ch * g.qstride + (int64_t)q * g.tstride + sg.r0 + t - g.cofs];
+      s_S[q][t] = sv;
+    }
+    if (tid < l) s_tau[tid] = P.htau[sg.r0 + tid];
+  }
   for (int64_t ct = blockIdx.x; ct < nct; ct += gridDim.x) {
     const int64_t cbase = j0 + ct * TW_COLS;
     const bool ok = (cbase + c) < cend;
     __syncthreads();
     for (int t = tg; t < l; t += TG) {
-      double s = 0.0;
+      double sv = 0.0;
       if (ok)
-        for (int64_t q = 0; q < nrc; ++q) s += P.Wp[q * g.qstride + (int64_t)t * g.tstride + cbase + c - g.cofs];
-      s_w[t][c] = s;
+        for (int64_t q = 0; q < nrc; ++q) sv += P.Wp[q * g.qstride + (int64_t)t * g.tstride + cbase + c - g.cofs];
+      s_w[t][c] = sv;
     }
     __syncthreads();
-    for (int t = tg; t < l; t += TG) {
-      // (T^T W)_t = sum_{q <= t} T(q, t) W_q
-      double s = 0.0;
-      const double* Tc = P.T + (int64_t)t * KMAX;
-      for (int q = 0; q <= t; ++q) s = fma(Tc[q], s_w[q][c], s);
-      if (ok) P.W[(int64_t)t * P.n + cbase + c] = s;
+    if (use_s) {
+      if (tg == 0) {  // one thread per column, t ascending
+        for (int t = 0; t < l; ++t) {
+          double sv = s_w[t][c];
+          for (int q = 0; q < t; ++q) sv = fma(-s_S[q][t], s_w[q][c], sv);
+          sv *= s_tau[t];
+          s_w[t][c] = sv;
+          if (ok) P.W[(int64_t)t * P.n + cbase + c] = sv;
+        }
+      }
+    } else {
+      for (int t = tg; t < l; t += TG) {
+        // (T^T W)_t = sum_{q <= t} T(q, t) W_q
+        double sv = 0.0;
+        const double* Tc = P.T + (int64_t)t * KMAX;
+        for (int q = 0; q <= t; ++q) sv = fma(Tc[q], s_w[q][c], sv);
+        if (ok) P.W[(int64_t)t * P.n + cbase + c] = sv;
+      }
     }
   }
 }
