@@ -94,6 +94,33 @@ struct DeviceConfig {
 thread_local DeviceConfig g_cfg;
 thread_local std::vector<cudaEvent_t> g_events;
 
+// Look-ahead of the FP64 form: a second stream that takes the bulk of each
+// sub-panel's trailing update while the next sub-panel's panel runs, and the
+// events that order the two; per host thread and device, created on first use.
+constexpr int LA_MAX_DEV = 64;
+constexpr int LA_SUB = KMAX / PB;
+struct LookAhead {
+  cudaStream_t side = nullptr;
+  cudaEvent_t ready[LA_SUB] = {};  // sub-panel j's W is reduced (main stream)
+  cudaEvent_t done[LA_SUB] = {};   // sub-panel j's bulk update has finished (side stream)
+};
+thread_local LookAhead g_la[LA_MAX_DEV];
+
+cudaError_t lookahead_resources(int dev, LookAhead** out) {
+  if (dev < 0 || dev >= LA_MAX_DEV) return cudaErrorInvalidDevice;
+  LookAhead& la = g_la[dev];
+  if (!la.side) {
+    cudaError_t e = cudaStreamCreateWithFlags(&la.side, cudaStreamNonBlocking);
+    for (int q = 0; q < LA_SUB && e == cudaSuccess; ++q) {
+      e = cudaEventCreateWithFlags(&la.ready[q], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&la.done[q], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  *out = &la;
+  return cudaSuccess;
+}
+
 int configure(DeviceConfig* cfg) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -329,9 +356,16 @@ int qrdm_workspace_size(int64_t m, int64_t n, int32_t k_max, size_t* bytes) {
   return 0;
 }
 
-int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, double delta, int32_t k_max,
+}  // extern "C"
+
+namespace qrdm {
+
+// qrdm_factor; allow_side = false keeps every launch on the caller's stream
+// (no second stream or events are created)
+int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, double delta, int32_t k_max,
                 double* d_htau, int32_t* d_perm, qrdm_info* info, const qrdm_opts* opts, void* d_work,
-                size_t work_bytes, void* stream_, qrdm_step_record* d_trace, int32_t* d_trace_J, int64_t trace_cap) {
+                size_t work_bytes, void* stream_, qrdm_step_record* d_trace, int32_t* d_trace_J, int64_t trace_cap,
+                bool allow_side) {
   qrdm_opts o;
   {
     const int rc = validate_factor(m, n, dA, lda, tau, delta, k_max, d_htau, d_perm, info, opts, &o);
@@ -454,7 +488,7 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   P.gram_chunks = sms < GRAM_CHUNKS_MAX ? sms : GRAM_CHUNKS_MAX;
   P.wchunks = WCHUNKS;
   const int gemm_grid = 2 * sms;
-  P.w_units = 4 * gemm_grid;
+  P.w_grid = gemm_grid;
   P.trace = (StepRecord*)d_trace;
   P.traceJ = d_trace_J;
   P.trace_cap = d_trace ? trace_cap : 0;
@@ -519,7 +553,7 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   // events for profiling: two pools (the previous batch is read while the
   // next one runs), each with a start/end pair per launch
   constexpr int MAX_BATCH = 16;
-  const int per_step = 11 + 4 * nsub_full;  // select..permute, 4 per sub-panel, 4 merged, downdate, step end
+  const int per_step = 11 + 5 * nsub_full;  // select..permute, 5 per sub-panel, 4 merged, downdate, step end
   const int pool = MAX_BATCH * per_step;
   if (prof && (int)g_events.size() < 2 * 2 * pool) {
     while ((int)g_events.size() < 2 * 2 * pool) {
@@ -535,22 +569,23 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   };
   std::vector<Rec> recs[2];
   int cur = 0;
-  auto run = [&](int kid, auto&& launch) -> cudaError_t {
+  auto run_on = [&](int kid, cudaStream_t s, auto&& launch) -> cudaError_t {
     int evi = -1;
     if (prof) {
       evi = 2 * pool * cur + 2 * (int)recs[cur].size();
-      cudaError_t e = cudaEventRecord(g_events[evi], stream);
+      cudaError_t e = cudaEventRecord(g_events[evi], s);
       if (e != cudaSuccess) return e;
     }
     launch();
     ++launches;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && prof) {
-      e = cudaEventRecord(g_events[evi + 1], stream);
+      e = cudaEventRecord(g_events[evi + 1], s);
       recs[cur].push_back({kid, evi});
     }
     return e;
   };
+  auto run = [&](int kid, auto&& launch) -> cudaError_t { return run_on(kid, stream, launch); };
   auto harvest = [&](int which) -> cudaError_t {
     for (const Rec& r : recs[which]) {
       float msk = 0.f;
@@ -562,6 +597,13 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     recs[which].clear();
     return cudaSuccess;
   };
+  // look-ahead (FP64 form only): the side stream takes each sub-panel's bulk update
+  LookAhead* la = nullptr;
+  bool la_ok = false;
+  if (allow_side && o.precision == 0 && nsub_full > 1) {
+    CK(lookahead_resources(cfg.device, &la));
+    la_ok = true;
+  }
   const unsigned tcv_grid = (unsigned)std::min<int64_t>(TCV_CHUNKS, (m + TCV_ROWS_MIN - 1) / TCV_ROWS_MIN);
   const dim3 tcw_grid((unsigned)((n + TCW_COLS - 1) / TCW_COLS), (unsigned)P.tc_nseg);
   // persistent update: at most one CTA per tile of the first step's trailing block
@@ -571,6 +613,8 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   const int tcu_grid2 = (int)std::min<int64_t>(tcu_tiles, (int64_t)sms * cfg.tcu_occ[1]);
   auto enqueue_step = [&](int nsub) -> cudaError_t {
     cudaError_t e;
+    const bool use_la = (la_ok && nsub > 1);
+    int pending = -1;  // sub-panel whose bulk update the side stream may still run
     if ((e = run(QRDM_K_SELECT, [&] { k_select<<<1, SEL_THREADS, 0, stream>>>(P); })) != cudaSuccess) return e;
     if ((e = run(QRDM_K_GRAM, [&] {
            if (merged && !merged64) {  // the tensor-core forms: the Gram on tcgen05 too
@@ -598,6 +642,10 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
                cudaLaunchKernelEx(&pc, k_panel_g, P, j);
            })) != cudaSuccess)
         return e;
+      if (pending >= 0) {  // the previous sub-panel's bulk update
+        if ((e = cudaStreamWaitEvent(stream, la->done[pending], 0)) != cudaSuccess) return e;
+        pending = -1;
+      }
       if ((e = run(QRDM_K_TRAIL_W, [&] {
              if (mixed)
                k_trail_w32<<<gemm_grid, GEMM_THREADS, S32_SMEM, stream>>>(P, j);
@@ -608,13 +656,28 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
       if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] { k_trail_wreduce<<<sms, GEMM_THREADS, 0, stream>>>(P, j); })) !=
           cudaSuccess)
         return e;
-      if ((e = run(QRDM_K_TRAIL_UPDATE, [&] {
-             if (mixed)
-               k_trail_update32<<<gemm_grid, GEMM_THREADS, S32_SMEM, stream>>>(P, j);
-             else
-               k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P, j);
-           })) != cudaSuccess)
+      if (use_la && j + 1 < nsub) {
+        // the next sub-panel's columns on this stream (its panel needs them),
+        // the rest on the side stream beside that panel; the next W pass
+        // waits for the rest
+        if ((e = cudaEventRecord(la->ready[j], stream)) != cudaSuccess) return e;
+        if ((e = run(QRDM_K_TRAIL_UPDATE,
+                     [&] { k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P, j, 1); })) != cudaSuccess)
+          return e;
+        if ((e = cudaStreamWaitEvent(la->side, la->ready[j], 0)) != cudaSuccess) return e;
+        if ((e = run_on(QRDM_K_TRAIL_UPDATE, la->side,
+                        [&] { k_trail_update<<<gemm_grid, GEMM_THREADS, 0, la->side>>>(P, j, 2); })) != cudaSuccess)
+          return e;
+        if ((e = cudaEventRecord(la->done[j], la->side)) != cudaSuccess) return e;
+        pending = j;
+      } else if ((e = run(QRDM_K_TRAIL_UPDATE, [&] {
+                    if (mixed)
+                      k_trail_update32<<<gemm_grid, GEMM_THREADS, S32_SMEM, stream>>>(P, j);
+                    else
+                      k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P, j, 0);
+                  })) != cudaSuccess) {
         return e;
+      }
     }
     if (merged) {
       // one update of the trailing block with all of the step's reflectors
@@ -642,7 +705,7 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
             cudaSuccess)
           return e;
         if ((e = run(QRDM_K_TRAIL_UPDATE, [&] {
-               k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P, -1);
+               k_trail_update<<<gemm_grid, GEMM_THREADS, 0, stream>>>(P, -1, 0);
              })) != cudaSuccess)
           return e;
       } else {
@@ -669,6 +732,7 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
           return e;
       }
     }
+    if (pending >= 0 && (e = cudaStreamWaitEvent(stream, la->done[pending], 0)) != cudaSuccess) return e;
     if ((e = run(QRDM_K_DOWNDATE, [&] { k_downdate<<<dd_grid, 256, 0, stream>>>(P); })) != cudaSuccess) return e;
     return run(QRDM_K_STEP_END, [&] { k_step_end<<<1, 1, 0, stream>>>(P); });
   };
@@ -732,6 +796,17 @@ int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   info->rank_colmax = hs.rank_colmax >= 0 ? hs.rank_colmax : (hs.ns >= kmin ? kmin : hs.ns);
   info->nsteps = hs.step;
   return QRDM_OK;
+}
+
+}  // namespace qrdm
+
+extern "C" {
+
+int qrdm_factor(double* dA, int64_t m, int64_t n, int64_t lda, double tau, double delta, int32_t k_max,
+                double* d_htau, int32_t* d_perm, qrdm_info* info, const qrdm_opts* opts, void* d_work,
+                size_t work_bytes, void* stream, qrdm_step_record* d_trace, int32_t* d_trace_J, int64_t trace_cap) {
+  return factor_impl(dA, m, n, lda, tau, delta, k_max, d_htau, d_perm, info, opts, d_work, work_bytes, stream,
+                     d_trace, d_trace_J, trace_cap, true);
 }
 
 

@@ -50,6 +50,11 @@ struct alignas(128) DevState {
   int32_t pbreak;   // 1 once the panel's break test fired in this step
   int32_t cur_lj;   // reflectors accepted by the current sub-panel (0: inactive)
   int32_t pad[3];
+  // per sub-panel of the current step: reflectors accepted, and whether
+  // another sub-panel follows; the trailing kernels of sub-panel j read these,
+  // not the fields above, because sub-panel j + 1 may run beside them
+  int32_t sub_l[KMAX / PB];
+  int32_t sub_next[KMAX / PB];
   double flops[16]; // algorithmic FP64 flops per kernel id (profile)
   // grid barrier of the fused single-column kernel and its diagnostics
   unsigned int gbar;     // arrivals (monotonic within one launch)
@@ -94,7 +99,7 @@ struct Params {
   double* W;       // [kmax][n] T^T V^T A22
   int32_t gram_chunks;  // CTAs of k_gram (= partial Gram matrices)
   int32_t wchunks;      // most row chunks of the W phase
-  int32_t w_units;      // target work units of the W phase (same in k_trail_w and k_trail_wreduce)
+  int32_t w_grid;       // CTAs of k_trail_w (its row chunks are chosen for this grid; k_trail_wreduce agrees)
   int32_t mixed;        // 1: FP32-class trailing update and Gram (geometry of k_trail_w32)
   int32_t merged;       // 1: sub-panel updates stop at the panel's end; one merged trailing update per step
   float* Wt;            // tensor-core forms: V^T A22 of row segment s at Wt + (s + 1) n 64, [column][64] (aliases Wp)
@@ -340,6 +345,10 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
       st->l = 0;
       st->pbreak = 0;
       st->cur_lj = 0;
+      for (int q = 0; q < KMAX / PB; ++q) {
+        st->sub_l[q] = 0;
+        st->sub_next[q] = 0;
+      }
     }
     s_ctl[0] = go;
   }
@@ -926,7 +935,11 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
   const int crank = (int)cluster.block_rank();
   const int tid = threadIdx.x;
   if (jb >= k || st->pbreak) {  // sub-panel beyond the panel, or the panel stopped
-    if (crank == 0 && tid == 0) st->cur_lj = 0;
+    if (crank == 0 && tid == 0) {
+      st->cur_lj = 0;
+      st->sub_l[j] = 0;
+      st->sub_next[j] = 0;
+    }
     return;
   }
   const int cs = (int)cluster.num_blocks();
@@ -1091,6 +1104,8 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
       }
     if (tid == 0) {
       st->cur_lj = lacc;
+      st->sub_l[j] = lacc;
+      st->sub_next[j] = (!broke && jb + PB < k) ? 1 : 0;
       st->l += lacc;
       if (lacc > 0) st->pol_minb = fmin(st->pol_minb, minb);
       if (broke) st->pbreak = 1;
@@ -1138,7 +1153,7 @@ __device__ __forceinline__ SubGeom sub_geom(const DevState* st, int j) {
   }
   g.r0 = st->ns + (int64_t)j * PB;
   g.c0 = st->ns + min((j + 1) * PB, k);
-  g.l = st->cur_lj;
+  g.l = st->sub_l[j];
   return g;
 }
 constexpr int TW_COLS = 32;   // columns per W work unit
@@ -1155,14 +1170,26 @@ __device__ __forceinline__ double vget(const double* A, int64_t lda, int64_t ns,
 }
 
 // number of row chunks for the W phase (same on every CTA)
-__device__ __forceinline__ int64_t wchunk_rows(int64_t mr, int64_t ncoltiles, int wchunks, int target_units) {
-  int64_t want = (target_units + ncoltiles - 1) / ncoltiles;
-  if (want > wchunks) want = wchunks;
-  if (want < 1) want = 1;
-  int64_t rows = (mr + want - 1) / want;
-  rows = (rows + TW_SUB - 1) / TW_SUB * TW_SUB;
-  if (rows < TW_SUB) rows = TW_SUB;
-  return rows;
+// Rows per chunk: the chunk count q (at most wchunks) that minimizes the W
+// pass's time on `grid` CTAs, ceil(ncoltiles q / grid) waves of units of
+// rows(q) rows each, rows(q) = mr / q rounded up to TW_SUB; ties go to the
+// smaller q (fewer partials to sum).  A fixed q left the last wave mostly
+// empty at some shapes (125 tiles x 10 chunks on 304 CTAs: 4.1 waves).
+__device__ __forceinline__ int64_t wchunk_rows(int64_t mr, int64_t ncoltiles, int wchunks, int grid) {
+  int64_t best_rows = (mr + TW_SUB - 1) / TW_SUB * TW_SUB, best_cost = -1;
+  for (int q = 1; q <= wchunks; ++q) {
+    int64_t rows = (mr + q - 1) / q;
+    rows = (rows + TW_SUB - 1) / TW_SUB * TW_SUB;
+    if (rows < TW_SUB) rows = TW_SUB;
+    const int64_t nq = (mr + rows - 1) / rows;  // chunks these rows make
+    const int64_t waves = (ncoltiles * nq + grid - 1) / grid;
+    const int64_t cost = waves * rows;
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best_rows = rows;
+    }
+  }
+  return best_rows;
 }
 
 // Thread layout of the W phase: TG reflector groups x (256/TG) columns; each
@@ -1224,7 +1251,7 @@ __device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int6
     g.tstride = NARROW_COLS;
     g.cofs = narrow_c0;
   }
-  g.rows_per = wchunk_rows(mr, g.nct, cap, P.w_units);
+  g.rows_per = wchunk_rows(mr, g.nct, cap, P.w_grid);
   g.nrc = (mr + g.rows_per - 1) / g.rows_per;
   return g;
 }
@@ -1414,34 +1441,44 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j)
   }
 }
 
-template <typename TC>
-__device__ __forceinline__ void trail_update_kernel(Params& P, int j) {
-  DevState* st = P.st;
-  if (st->done) return;
+// part (sub-panels, j >= 0): 0 every column right of the sub-panel; 1 only
+// the next sub-panel's columns (what its panel needs first); 2 the others.
+// Parts 1 and 2 together make part 0, so part 2 may run beside the next
+// sub-panel's panel.
+__device__ __forceinline__ void update_range(const Params& P, const DevState* st, int j, int part, int64_t* c0,
+                                             int64_t* cend) {
   const SubGeom sg = sub_geom(st, j);
-  const int l = sg.l;
-  const int64_t ns = sg.r0, m = P.m, lda = P.lda;
-  const int64_t j0 = sg.c0;
-  const int64_t cend = trail_end(P, st, j);
-  const int64_t n2 = cend - j0, mr = m - ns;
-  if (l <= 0 || n2 <= 0 || mr <= 0) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_UPDATE, 2.0 * (double)mr * (double)n2 * l);
+  *c0 = sg.c0;
+  *cend = trail_end(P, st, j);
+  if (part == 0 || j < 0) return;
+  // the next sub-panel's columns, when one follows
+  const int64_t split = st->sub_next[j] ? min(*cend, st->ns + min((int64_t)(j + 2) * PB, (int64_t)st->k)) : *c0;
+  if (part == 1) *cend = split;
+  else *c0 = split;
+}
+
+// A[rows, cols] -= V W in tiles of TU_ROWS x TCN (TCN = 64 or 32), 16 x 16
+// threads with 4 x (TCN / 16) outputs each, reflectors staged TU_KC at a time
+template <typename TC, int TCN>
+__device__ __forceinline__ void trail_update_tiles(Params& P, int l, int64_t ns, int64_t j0, int64_t cend,
+                                                   int64_t mr, TC (*s_v)[TU_ROWS], TC (*s_w)[TU_COLS]) {
+  constexpr int NJ = TCN / 16;
+  const int64_t lda = P.lda;
+  const int64_t n2 = cend - j0;
   const int64_t nrt = (mr + TU_ROWS - 1) / TU_ROWS;
-  const int64_t nct = (n2 + TU_COLS - 1) / TU_COLS;
+  const int64_t nct = (n2 + TCN - 1) / TCN;
   const int64_t units = nrt * nct;
-  __shared__ TC s_v[TU_KC][TU_ROWS];
-  __shared__ TC s_w[TU_KC][TU_COLS];
   const int tid = threadIdx.x;
-  const int tr = tid % 16, tc = tid / 16;  // 16 x 16 threads, 4 x 4 outputs each
+  const int tr = tid % 16, tc = tid / 16;  // 16 x 16 threads
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int64_t rt = u % nrt, ct = u / nrt;
     const int64_t rbase = rt * TU_ROWS;  // relative to ns
-    const int64_t cbase = j0 + ct * TU_COLS;
-    TC acc[4][4];
+    const int64_t cbase = j0 + ct * TCN;
+    TC acc[4][NJ];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = (TC)0;
+      for (int jj = 0; jj < NJ; ++jj) acc[i][jj] = (TC)0;
     for (int t0 = 0; t0 < l; t0 += TU_KC) {
       const int kcnt = min(TU_KC, l - t0);
       __syncthreads();
@@ -1451,40 +1488,68 @@ __device__ __forceinline__ void trail_update_kernel(Params& P, int j) {
         if (t < kcnt && rbase + r < mr) v = vget(P.A, lda, ns, rbase + r, t0 + t);
         s_v[t][r] = (TC)v;
       }
-      for (int e = tid; e < TU_KC * TU_COLS; e += GEMM_THREADS) {
-        int t = e / TU_COLS, c = e % TU_COLS;
+      for (int e = tid; e < TU_KC * TCN; e += GEMM_THREADS) {
+        int t = e / TCN, c = e % TCN;
         double v = 0.0;
         if (t < kcnt && cbase + c < cend) v = P.W[(int64_t)(t0 + t) * P.n + cbase + c];
         s_w[t][c] = (TC)v;
       }
       __syncthreads();
       for (int t = 0; t < kcnt; ++t) {
-        TC vv[4], ww[4];
+        TC vv[4], ww[NJ];
 #pragma unroll
         for (int i = 0; i < 4; ++i) vv[i] = s_v[t][tr + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) ww[j] = s_w[t][tc + 16 * j];
+        for (int jj = 0; jj < NJ; ++jj) ww[jj] = s_w[t][tc + 16 * jj];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmat(vv[i], ww[j], acc[i][j]);
+          for (int jj = 0; jj < NJ; ++jj) acc[i][jj] = fmat(vv[i], ww[jj], acc[i][jj]);
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t col = cbase + tc + 16 * j;
+    for (int jj = 0; jj < NJ; ++jj) {
+      const int64_t col = cbase + tc + 16 * jj;
       if (col >= cend) continue;
       double* a = P.A + col * lda + ns;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int64_t r = rbase + tr + 16 * i;
-        if (r < mr) a[r] -= (double)acc[i][j];
+        if (r < mr) a[r] -= (double)acc[i][jj];
       }
     }
   }
 }
 
-__global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P, int j) { trail_update_kernel<double>(P, j); }
+template <typename TC>
+__device__ __forceinline__ void trail_update_kernel(Params& P, int j, int part) {
+  DevState* st = P.st;
+  if (st->done) return;
+  const SubGeom sg = sub_geom(st, j);
+  const int l = sg.l;
+  const int64_t ns = sg.r0, m = P.m;
+  int64_t j0, cend;
+  update_range(P, st, j, part, &j0, &cend);
+  const int64_t n2 = cend - j0, mr = m - ns;
+  if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_UPDATE, 2.0 * (double)mr * (double)n2 * l);
+  // tile width: the one with fewer tile-waves times tile size on this grid
+  // (the same choice in every CTA)
+  const int64_t nrt = (mr + TU_ROWS - 1) / TU_ROWS;
+  const int64_t G = gridDim.x;
+  const int64_t c64 = ((nrt * ((n2 + 63) / 64) + G - 1) / G) * 64;
+  const int64_t c32 = ((nrt * ((n2 + 31) / 32) + G - 1) / G) * 32;
+  __shared__ TC s_v[TU_KC][TU_ROWS];
+  __shared__ TC s_w[TU_KC][TU_COLS];
+  if (c32 < c64)
+    trail_update_tiles<TC, 32>(P, l, ns, j0, cend, mr, s_v, s_w);
+  else
+    trail_update_tiles<TC, 64>(P, l, ns, j0, cend, mr, s_v, s_w);
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P, int j, int part) {
+  trail_update_kernel<double>(P, j, part);
+}
 
 // ---------------------------------------------------------------------------
 // a9, FP32-class form.  With l <= PB = 16 reflectors per pass the update moves
@@ -2062,6 +2127,10 @@ __global__ void k_state_init(Params P) {
   st->npairs = 0;
   st->pbreak = 0;
   st->cur_lj = 0;
+  for (int q = 0; q < KMAX / PB; ++q) {
+    st->sub_l[q] = 0;
+    st->sub_next[q] = 0;
+  }
   for (int i = 0; i < 16; ++i) st->flops[i] = 0.0;
   st->gbar = 0u;
   st->abort_flag = 0;

@@ -9,6 +9,15 @@
 
 #include "../../include/qrdm.h"
 
+namespace qrdm {
+// qrdm_factor with every launch on the caller's stream (no second stream or
+// events are created: this entry point creates nothing)
+int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, double delta, int32_t k_max,
+                double* d_htau, int32_t* d_perm, qrdm_info* info, const qrdm_opts* opts, void* d_work,
+                size_t work_bytes, void* stream, qrdm_step_record* d_trace, int32_t* d_trace_J, int64_t trace_cap,
+                bool allow_side);
+}  // namespace qrdm
+
 namespace {
 
 // The shared scratch.  In host code `g_scratch` only names the symbol; its
@@ -50,8 +59,8 @@ extern "C" int qrdm_factor_noalloc(double* dA, int64_t m, int64_t n, int64_t lda
                                    int32_t* d_trace_J, int64_t trace_cap) {
   if (opts && opts->profile) return QRDM_ERR_UNSUPPORTED;  // profiling creates CUDA events
   if (m == 0 || n == 0)  // nothing to factor: qrdm_factor checks every argument and needs no workspace
-    return qrdm_factor(dA, m, n, lda, tau, delta, k_max, d_htau, d_perm, info, opts, nullptr, 0, stream, d_trace,
-                       d_trace_J, trace_cap);
+    return qrdm::factor_impl(dA, m, n, lda, tau, delta, k_max, d_htau, d_perm, info, opts, nullptr, 0, stream,
+                             d_trace, d_trace_J, trace_cap, false);
   size_t need = 0;
   if (m >= 0 && n >= 0 && n <= INT32_MAX && k_max >= 1 && k_max <= QRDM_KMAX_LIMIT) {
     if (qrdm_workspace_size(m, n, k_max, &need) == 0 && need > (size_t)QRDM_NOALLOC_SCRATCH_BYTES)
@@ -66,6 +75,6 @@ extern "C" int qrdm_factor_noalloc(double* dA, int64_t m, int64_t n, int64_t lda
   }
   // qrdm_factor validates every argument and re-initializes the whole step
   // state in the workspace, so the previous call's contents do not matter.
-  return qrdm_factor(dA, m, n, lda, tau, delta, k_max, d_htau, d_perm, info, opts, scratch,
-                     (size_t)QRDM_NOALLOC_SCRATCH_BYTES, stream, d_trace, d_trace_J, trace_cap);
+  return qrdm::factor_impl(dA, m, n, lda, tau, delta, k_max, d_htau, d_perm, info, opts, scratch,
+                           (size_t)QRDM_NOALLOC_SCRATCH_BYTES, stream, d_trace, d_trace_J, trace_cap, false);
 }
