@@ -356,7 +356,8 @@ def measure_c3(q, inputs, torch, stream, hbm_gbs: float | None = None) -> dict:
                 "trailing_elements_over_steps": elems,
                 "w_pass_ms": kms["k_trail_w"], "w_pass_GBps": w_gbs,
                 "update_pass_ms": kms["k_trail_update"], "update_pass_GBps": u_gbs,
-                "t_build_and_w_sum_ms": kms["k_trail_wreduce"],
+                "t_build_ms": kms["k_tc_vtv+k_tc_tbuild"], "v_images_ms": kms["k_tc_vimg"],
+                "w_sum_ms": kms["k_tc_wsum"], "subpanel_w_reduce_ms": kms["k_trail_wreduce"],
                 "hbm_frac_of_measured": {"w_pass": w_gbs / hbm_gbs if hbm_gbs else None,
                                          "update_pass": u_gbs / hbm_gbs if hbm_gbs else None},
                 "note": "the k_trail_w / k_trail_update slots also hold the FP64 sub-panel updates of the panel "
@@ -609,6 +610,57 @@ def forms_summary(c3, c4, c5) -> dict:
     return out
 
 
+def run_fp64_probe() -> int:
+    """The FP64 rates of this GPU (FFMA64 chains, DMMA mma.sync m8n8k4, and a
+    cuBLAS DGEMM through torch), with the SM clocks sampled meanwhile: the
+    measured counterpart of the derived FP64 peak the roofline divides by."""
+    import torch
+
+    import paper_2106_03138_gb300 as q
+    from paper_2106_03138_gb300 import _binding as b
+
+    q.load()
+    dev = torch.device("cuda", 0)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    blocks = sms * 8
+    out = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    res = {}
+    with ClockSampler(0) as clk:
+        for which, name, iters in ((0, "ffma64", 200000), (1, "dmma_m8n8k4", 50000)):
+            b.qrdm_fp64_probe(which, blocks, max(1, iters // 20), out.data_ptr(), out.numel() * 8, stream)  # warm
+            best = None
+            for _ in range(3):
+                rc, fl, ms = b.qrdm_fp64_probe(which, blocks, iters, out.data_ptr(), out.numel() * 8, stream)
+                assert rc == 0, rc
+                best = ms if best is None else min(best, ms)
+            res[name] = {"TFLOP/s": fl / (best * 1e-3) / 1e12, "ms": best, "blocks": blocks, "iters": iters}
+        n = 8192
+        x = torch.randn(n, n, dtype=torch.float64, device=dev)
+        y = torch.randn(n, n, dtype=torch.float64, device=dev)
+        torch.matmul(x, y)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(x, y)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        res["cublas_dgemm_8192"] = {"TFLOP/s": 2.0 * n ** 3 / (best * 1e-3) / 1e12, "ms": best}
+    csum = clk.summary()
+    smax = csum.get("sm_max_mhz") or 2070.0
+    derived = FP64_FLOP_PER_CLK_PER_SM * sms * smax * 1e6 / 1e12
+    print(json.dumps({"fp64_probe": res, "derived_peak_TFLOP/s": derived,
+                      "derived_peak": f"{FP64_FLOP_PER_CLK_PER_SM:g} flop/clk/SM x {sms} SMs x {smax:g} MHz",
+                      "clocks": csum, "gpu": props.name}), flush=True)
+    return 0
+
+
 def config_dict(world: int) -> dict:
     return {"workload": WORKLOAD_DESC, "matrices": list(WORKLOAD), "tau": TAU, "delta": DELTA, "k_max": KMAX,
             "global_batch": 3 * world, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -630,9 +682,12 @@ def main() -> int:
                     help="factor one named matrix once at the benchmark's parameters and exit (profiler target)")
     ap.add_argument("--max-steps", type=int, default=0, help="with --profile-case: stop after this many block steps")
     ap.add_argument("--precision", type=int, default=0, help="with --profile-case: 0 FP64, 1 FP32-class mixed")
+    ap.add_argument("--fp64-probe", action="store_true", help="measure this GPU's FP64 rates and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.fp64_probe:
+        return run_fp64_probe()
     if args.profile_case:
         return run_profile_case(args.profile_case, args.max_steps, args.precision)
 

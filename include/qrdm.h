@@ -65,7 +65,10 @@ extern "C" {
 #define QRDM_K_DOWNDATE 10     /* a10: partial norm update */
 #define QRDM_K_STEP_END 11     /* a11: n_s += l */
 #define QRDM_K_QRP_TAIL 12     /* a2..a11 fused for single-column steps (DM off or k_max = 1) */
-#define QRDM_NKERNELS 13
+#define QRDM_K_WY_T 13         /* a8, merged forms: V^T V of the step and its compact-WY T */
+#define QRDM_K_TC_VIMG 14      /* a9, tensor-core forms: V's operand images */
+#define QRDM_K_TC_WSUM 15      /* a9, tensor-core forms: W = T^T (sum of segments) and W's image */
+#define QRDM_NKERNELS 16
 
 /* Optional per-kernel timing (host struct, filled when opts->profile is set):
    every launch is bracketed by CUDA events on the caller's stream; ms[] sums
@@ -493,6 +496,22 @@ int qrdm_ls_solve(const double* dA, int64_t lda, const double* dQR, int64_t ldqr
 int qrdm_qp3_workspace_size(int64_t m, int64_t n, int32_t nb, size_t* bytes);
 int qrdm_qp3_factor(double* dA, int64_t m, int64_t n, int64_t lda, int32_t nb, double* d_htau, int32_t* d_perm,
                     qrdm_info* info, int32_t eps1_mode, void* d_work, size_t work_bytes, void* stream);
+
+/*
+ * FP64 rate probe (not part of the factorization): times one launch of
+ * `blocks` x 256 threads that run `iters` rounds of FP64 arithmetic, so that
+ * the FP64 kernels' roofline can be read against a measured rate.
+ *   which 0: FFMA64, eight independent fma chains per thread (16 flops per
+ *            thread and round);
+ *   which 1: DMMA, mma.sync m8n8k4 FP64 with four independent accumulators
+ *            per warp (2048 flops per warp and round).
+ * d_out: device scratch of blocks x 256 doubles (the chains' sums land
+ * there); *flops (host) the flops performed, *ms (host) the launch's time by
+ * CUDA events on `stream`.  Synchronizes the stream.  Errors: -i for an
+ * invalid i-th argument, QRDM_ERR_CUDA.
+ */
+int qrdm_fp64_probe(int32_t which, int32_t blocks, int32_t iters, void* d_out, size_t out_bytes, double* flops,
+                    float* ms, void* stream);
 
 /* Static description of an error code. */
 const char* qrdm_strerror(int code);

@@ -31,7 +31,8 @@ QRDM_KMAX_LIMIT = 128
 
 
 KERNEL_NAMES = ("k_colnorm_init", "k_select", "k_gram", "k_gram_reduce", "k_pick", "k_permute", "k_panel",
-                "k_trail_w", "k_trail_wreduce", "k_trail_update", "k_downdate", "k_step_end", "k_qrp_tail")
+                "k_trail_w", "k_trail_wreduce", "k_trail_update", "k_downdate", "k_step_end", "k_qrp_tail",
+                "k_tc_vtv+k_tc_tbuild", "k_tc_vimg", "k_tc_wsum")
 
 
 class qrdm_profile(ctypes.Structure):
@@ -89,7 +90,7 @@ EXPORTS = ("qrdm_workspace_size", "qrdm_factor", "qrdm_factor_noalloc", "qrdm_st
            "qrdm_factor_batched", "qrdm_factor_batched_graph", "qrdm_batch_results", "qrdm_mlp_workspace_size",
            "qrdm_mlp_init", "qrdm_mlp_to_bf16", "qrdm_mlp_forward", "qrdm_mlp_loss_grad", "qrdm_mlp_adam_step",
            "qrdm_mlp_train", "qrdm_ls_workspace_size", "qrdm_ls_solve", "qrdm_qp3_workspace_size",
-           "qrdm_qp3_factor")
+           "qrdm_qp3_factor", "qrdm_fp64_probe")
 QRDM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 _lock = threading.Lock()
@@ -120,6 +121,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.qrdm_factor_noalloc.argtypes = [c_p, c_i64, c_i64, c_i64, c_f64, c_f64, c_i32, c_p, c_p,
                                             ctypes.POINTER(qrdm_info), ctypes.POINTER(qrdm_opts), c_p, c_p, c_p,
                                             c_i64]
+        lib.qrdm_fp64_probe.restype = ctypes.c_int
+        lib.qrdm_fp64_probe.argtypes = [c_i32, c_i32, c_i32, c_p, c_sz, ctypes.POINTER(c_f64),
+                                        ctypes.POINTER(ctypes.c_float), c_p]
         lib.qrdm_strerror.restype = ctypes.c_char_p
         lib.qrdm_strerror.argtypes = [ctypes.c_int]
         lib.qrdm_last_cuda_error.restype = ctypes.c_int
@@ -271,3 +275,11 @@ def qrdm_mlp_workspace_size(batch: int) -> int:
     if rc != 0:
         raise ValueError(f"qrdm_mlp_workspace_size: invalid argument {-rc}")
     return int(out.value)
+
+
+def qrdm_fp64_probe(which: int, blocks: int, iters: int, d_out: int, out_bytes: int, stream: int) -> tuple[int, float, float]:
+    """FP64 rate probe: (rc, flops, ms) of one timed launch (include/qrdm.h)."""
+    fl = c_f64(0.0)
+    ms = ctypes.c_float(0.0)
+    rc = load().qrdm_fp64_probe(which, blocks, iters, d_out, out_bytes, ctypes.byref(fl), ctypes.byref(ms), stream)
+    return rc, float(fl.value), float(ms.value)

@@ -8,7 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqrdm.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("qrdm.cu", "qrdm_noalloc.cu", "qrdm_mlp.cu", "qrdm_ls.cu", "qrdm_qp3.cu")]
+SOURCES = [os.path.join(CSRC, f)
+           for f in ("qrdm.cu", "qrdm_noalloc.cu", "qrdm_mlp.cu", "qrdm_ls.cu", "qrdm_qp3.cu", "qrdm_probe.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(os.path.dirname(HERE), "include", "qrdm.h")
 ]

@@ -1,5 +1,6 @@
 // C ABI of the GB300 QRDM library: argument checks, workspace layout, and the
 // host loop that enqueues one block step (Algorithm 4) at a time.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -147,6 +148,12 @@ int configure(DeviceConfig* cfg) {
     return e;
   if ((e = cudaFuncSetAttribute(k_tc_w<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCW_SMEM)) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(k_tc_w_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcwTma<1>::SMEM)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_tc_w_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcwTma<2>::SMEM)) !=
+      cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(k_tc_update<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcu_smem<1>())) !=
       cudaSuccess)
     return e;
@@ -235,6 +242,38 @@ int configure(DeviceConfig* cfg) {
   g_cfg = c;
   *cfg = c;
   return 0;
+}
+
+// cuTensorMapEncodeTiled, reached through the runtime (the library links only
+// the CUDA runtime); null when the driver does not offer it
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    cudaGetLastError();
+    return (EncodeTiledFn)p;
+  }();
+  return fn;
+}
+
+// tensor map of the FP64 matrix (rows inner) with boxes of `rows` rows x 128
+// columns; false when it cannot be made
+bool encode_a_map(CUtensorMap* map, double* dA, int64_t m, int64_t n, int64_t lda, int rows) {
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)lda * sizeof(double)};
+  const cuuint32_t box[2] = {(cuuint32_t)rows, (cuuint32_t)TCW_COLS};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, dA, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool policy_valid(const qrdm_policy* p) {
@@ -488,7 +527,7 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   P.gram_chunks = sms < GRAM_CHUNKS_MAX ? sms : GRAM_CHUNKS_MAX;
   P.wchunks = WCHUNKS;
   const int gemm_grid = 2 * sms;
-  P.w_grid = gemm_grid;
+  P.w_units = 4 * gemm_grid;
   P.trace = (StepRecord*)d_trace;
   P.traceJ = d_trace_J;
   P.trace_cap = d_trace ? trace_cap : 0;
@@ -553,7 +592,7 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   // events for profiling: two pools (the previous batch is read while the
   // next one runs), each with a start/end pair per launch
   constexpr int MAX_BATCH = 16;
-  const int per_step = 11 + 5 * nsub_full;  // select..permute, 5 per sub-panel, 4 merged, downdate, step end
+  const int per_step = 12 + 5 * nsub_full;  // select..permute, 5 per sub-panel, 5 merged, downdate, step end
   const int pool = MAX_BATCH * per_step;
   if (prof && (int)g_events.size() < 2 * 2 * pool) {
     while ((int)g_events.size() < 2 * 2 * pool) {
@@ -604,6 +643,11 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     CK(lookahead_resources(cfg.device, &la));
     la_ok = true;
   }
+  // the tensor-core W pass reads A by TMA when A allows 16-byte rows
+  CUtensorMap tmA;
+  memset(&tmA, 0, sizeof(tmA));
+  const bool use_tma = merged && !merged64 && P.tc_al &&
+                       encode_a_map(&tmA, dA, m, n, lda, tf32 ? TcwTma<2>::KA : TcwTma<1>::KA);
   const unsigned tcv_grid = (unsigned)std::min<int64_t>(TCV_CHUNKS, (m + TCV_ROWS_MIN - 1) / TCV_ROWS_MIN);
   const dim3 tcw_grid((unsigned)((n + TCW_COLS - 1) / TCW_COLS), (unsigned)P.tc_nseg);
   // persistent update: at most one CTA per tile of the first step's trailing block
@@ -681,19 +725,22 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     }
     if (merged) {
       // one update of the trailing block with all of the step's reflectors
-      if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] {
-             if (merged64)
+      if ((e = run(QRDM_K_WY_T, [&] {
+             if (merged64) {  // T in FP64 for the exact merged form
                k_tc_vtv<double><<<tcv_grid, TC_THREADS, 0, stream>>>(P);
-             else
+               k_tc_tbuild<<<1, TC_THREADS, TCB_SMEM, stream>>>(P);
+             } else {  // S = V^T V only: W is solved for by forward substitution
                k_tc_vtv<float><<<tcv_grid, TC_THREADS, 0, stream>>>(P);
-             k_tc_tbuild<<<1, TC_THREADS, TCB_SMEM, stream>>>(P);
-             if (!merged64) {
-               if (tf32)
-                 k_tc_vimg<2><<<tcvi_grid, TC_THREADS, 0, stream>>>(P);
-               else
-                 k_tc_vimg<1><<<tcvi_grid, TC_THREADS, 0, stream>>>(P);
+               k_tc_sred<<<(TC_LMAX * (TC_LMAX - 1) / 2 + TC_THREADS - 1) / TC_THREADS, TC_THREADS, 0, stream>>>(P);
              }
            })) != cudaSuccess)
+        return e;
+      if (!merged64 && (e = run(QRDM_K_TC_VIMG, [&] {
+                          if (tf32)
+                            k_tc_vimg<2><<<tcvi_grid, TC_THREADS, 0, stream>>>(P);
+                          else
+                            k_tc_vimg<1><<<tcvi_grid, TC_THREADS, 0, stream>>>(P);
+                        })) != cudaSuccess)
         return e;
       if (merged64) {
         // the same merged update in FP64 on the CUDA cores (exact form)
@@ -710,13 +757,19 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
           return e;
       } else {
         if ((e = run(QRDM_K_TRAIL_W, [&] {
-               if (tf32)
+               if (use_tma) {
+                 if (tf32)
+                   k_tc_w_tma<2><<<tcw_grid, TCW_THREADS, TcwTma<2>::SMEM, stream>>>(tmA, P);
+                 else
+                   k_tc_w_tma<1><<<tcw_grid, TCW_THREADS, TcwTma<1>::SMEM, stream>>>(tmA, P);
+               } else if (tf32) {
                  k_tc_w<2><<<tcw_grid, TCW_THREADS, TCW_SMEM, stream>>>(P);
-               else
+               } else {
                  k_tc_w<1><<<tcw_grid, TCW_THREADS, TCW_SMEM, stream>>>(P);
+               }
              })) != cudaSuccess)
           return e;
-        if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] {
+        if ((e = run(QRDM_K_TC_WSUM, [&] {
                if (tf32)
                  k_tc_wsum<2><<<2 * sms, TC_THREADS, 0, stream>>>(P);
                else

@@ -99,7 +99,7 @@ struct Params {
   double* W;       // [kmax][n] T^T V^T A22
   int32_t gram_chunks;  // CTAs of k_gram (= partial Gram matrices)
   int32_t wchunks;      // most row chunks of the W phase
-  int32_t w_grid;       // CTAs of k_trail_w (its row chunks are chosen for this grid; k_trail_wreduce agrees)
+  int32_t w_units;      // target work units of the W phase (same in k_trail_w and k_trail_wreduce)
   int32_t mixed;        // 1: FP32-class trailing update and Gram (geometry of k_trail_w32)
   int32_t merged;       // 1: sub-panel updates stop at the panel's end; one merged trailing update per step
   float* Wt;            // tensor-core forms: V^T A22 of row segment s at Wt + (s + 1) n 64, [column][64] (aliases Wp)
@@ -121,7 +121,7 @@ struct Params {
 // kernel ids (same numbering as QRDM_K_* in the C header)
 enum KernelId {
   KID_COLNORM = 0, KID_SELECT, KID_GRAM, KID_GRAM_REDUCE, KID_PICK, KID_PERMUTE, KID_PANEL, KID_TRAIL_W,
-  KID_TRAIL_WREDUCE, KID_TRAIL_UPDATE, KID_DOWNDATE, KID_STEP_END, KID_QRP_TAIL
+  KID_TRAIL_WREDUCE, KID_TRAIL_UPDATE, KID_DOWNDATE, KID_STEP_END, KID_QRP_TAIL, KID_WY_T, KID_TC_VIMG, KID_TC_WSUM
 };
 
 __device__ __forceinline__ void add_flops(DevState* st, int kid, double f) { atomicAdd(&st->flops[kid], f); }
@@ -1170,26 +1170,14 @@ __device__ __forceinline__ double vget(const double* A, int64_t lda, int64_t ns,
 }
 
 // number of row chunks for the W phase (same on every CTA)
-// Rows per chunk: the chunk count q (at most wchunks) that minimizes the W
-// pass's time on `grid` CTAs, ceil(ncoltiles q / grid) waves of units of
-// rows(q) rows each, rows(q) = mr / q rounded up to TW_SUB; ties go to the
-// smaller q (fewer partials to sum).  A fixed q left the last wave mostly
-// empty at some shapes (125 tiles x 10 chunks on 304 CTAs: 4.1 waves).
-__device__ __forceinline__ int64_t wchunk_rows(int64_t mr, int64_t ncoltiles, int wchunks, int grid) {
-  int64_t best_rows = (mr + TW_SUB - 1) / TW_SUB * TW_SUB, best_cost = -1;
-  for (int q = 1; q <= wchunks; ++q) {
-    int64_t rows = (mr + q - 1) / q;
-    rows = (rows + TW_SUB - 1) / TW_SUB * TW_SUB;
-    if (rows < TW_SUB) rows = TW_SUB;
-    const int64_t nq = (mr + rows - 1) / rows;  // chunks these rows make
-    const int64_t waves = (ncoltiles * nq + grid - 1) / grid;
-    const int64_t cost = waves * rows;
-    if (best_cost < 0 || cost < best_cost) {
-      best_cost = cost;
-      best_rows = rows;
-    }
-  }
-  return best_rows;
+__device__ __forceinline__ int64_t wchunk_rows(int64_t mr, int64_t ncoltiles, int wchunks, int target_units) {
+  int64_t want = (target_units + ncoltiles - 1) / ncoltiles;
+  if (want > wchunks) want = wchunks;
+  if (want < 1) want = 1;
+  int64_t rows = (mr + want - 1) / want;
+  rows = (rows + TW_SUB - 1) / TW_SUB * TW_SUB;
+  if (rows < TW_SUB) rows = TW_SUB;
+  return rows;
 }
 
 // Thread layout of the W phase: TG reflector groups x (256/TG) columns; each
@@ -1251,7 +1239,7 @@ __device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int6
     g.tstride = NARROW_COLS;
     g.cofs = narrow_c0;
   }
-  g.rows_per = wchunk_rows(mr, g.nct, cap, P.w_grid);
+  g.rows_per = wchunk_rows(mr, g.nct, cap, P.w_units);
   g.nrc = (mr + g.rows_per - 1) / g.rows_per;
   return g;
 }
@@ -1533,18 +1521,9 @@ __device__ __forceinline__ void trail_update_kernel(Params& P, int j, int part) 
   const int64_t n2 = cend - j0, mr = m - ns;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_UPDATE, 2.0 * (double)mr * (double)n2 * l);
-  // tile width: the one with fewer tile-waves times tile size on this grid
-  // (the same choice in every CTA)
-  const int64_t nrt = (mr + TU_ROWS - 1) / TU_ROWS;
-  const int64_t G = gridDim.x;
-  const int64_t c64 = ((nrt * ((n2 + 63) / 64) + G - 1) / G) * 64;
-  const int64_t c32 = ((nrt * ((n2 + 31) / 32) + G - 1) / G) * 32;
   __shared__ TC s_v[TU_KC][TU_ROWS];
   __shared__ TC s_w[TU_KC][TU_COLS];
-  if (c32 < c64)
-    trail_update_tiles<TC, 32>(P, l, ns, j0, cend, mr, s_v, s_w);
-  else
-    trail_update_tiles<TC, 64>(P, l, ns, j0, cend, mr, s_v, s_w);
+  trail_update_tiles<TC, 64>(P, l, ns, j0, cend, mr, s_v, s_w);
 }
 
 __global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P, int j, int part) {

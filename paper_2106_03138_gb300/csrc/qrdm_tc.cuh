@@ -161,6 +161,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// one thread: tiled 2-D tensor copy (TMA) of the box at element coordinates
+// (x, y) of the tensor map into this CTA's shared memory, completing on the
+// mbarrier; x * element size must be a multiple of 16 bytes
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int32_t x, int32_t y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // round FP32 to TF32 (nearest, ties away), returned as an FP32 bit pattern
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;

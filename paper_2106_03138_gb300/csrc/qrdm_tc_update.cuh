@@ -25,6 +25,8 @@
 // accumulation truncates.
 #pragma once
 
+#include <cuda.h>
+
 #include "qrdm_kernels.cuh"
 #include "qrdm_tc.cuh"
 
@@ -199,6 +201,26 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_tbuild(Params P) {
   for (int e = tid; e < l * l; e += TC_THREADS) {
     const int r = e % l, c = e / l;
     P.T[(int64_t)c * KMAX + r] = (r <= c) ? s_t[r][c] : 0.0;
+  }
+}
+
+// S = V^T V of the step (pairs i < j), the chunk partials of k_tc_vtv summed
+// in FP64 in chunk order, into P.G (packed, pair e = j (j - 1) / 2 + i): the
+// tensor-core forms apply the step's block reflector through S (k_tc_wsum)
+// instead of forming T.
+__global__ void __launch_bounds__(TC_THREADS) k_tc_sred(Params P) {
+  DevState* st = P.st;
+  if (st->done) return;
+  const int l = st->l;
+  const int64_t ns = st->ns, mr = P.m - ns;
+  if (l <= 1 || st->k >= P.n - ns || mr <= 0) return;
+  const int64_t per = max((int64_t)TCV_ROWS_MIN, (mr + TCV_CHUNKS - 1) / TCV_CHUNKS);
+  const int64_t nch = (mr + per - 1) / per;
+  const int npair = l * (l - 1) / 2;
+  for (int e = blockIdx.x * TC_THREADS + threadIdx.x; e < npair; e += gridDim.x * TC_THREADS) {
+    double acc = 0.0;
+    for (int64_t c = 0; c < nch; ++c) acc += P.Gp[c * (int64_t)P.kmax * P.kmax + e];
+    P.G[e] = acc;
   }
 }
 
@@ -501,6 +523,218 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w(Params P) {
   if (wp == 0) tc::tmem_dealloc(taddr, 2 * TC_LMAX);
 }
 
+// The W pass with TMA (when A is 16-byte aligned and lda even, P.tc_al): the
+// FP64 tile of each K chunk, KA rows x 128 columns, arrives by one tiled
+// tensor copy into a ring of NST FP64 stages, NST chunks ahead of the
+// conversion, so the loads need no thread and no load-queue slot.  The
+// threads convert from shared memory: 8 lanes per column read 16-byte pieces
+// (two rows) side by side, and each lane writes its rows' hi and lo parts
+// straight into the split operand tile (two BF16 in 4 bytes, or two TF32 in
+// 8).  V's chunk, the accumulators per chunk and the MMAs are those of
+// k_tc_w.
+template <int FMT>
+struct TcwTma {
+  static constexpr int KA = TcFmt<FMT>::KA;
+  static constexpr int NST = (FMT == 1) ? 2 : 3;          // FP64 stages
+  static constexpr int F64_STAGE = KA * TCW_COLS * 8;      // 64 KB (BF16), 32 KB (TF32)
+  static constexpr int PPL = KA / 16;                      // 16-byte pieces per lane and column
+  static constexpr int SMEM = 1024 + 2 * TCW_STAGE + NST * F64_STAGE + 128;
+};
+
+template <int FMT>
+__global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w_tma(const __grid_constant__ CUtensorMap tmA, Params P) {
+  using G = TcwTma<FMT>;
+  constexpr int KA = G::KA, NST = G::NST, ESZ = TcFmt<FMT>::ESZ;
+  constexpr int NWQ = TCW_THREADS / 128;
+  constexpr int PART = TC_LMAX / NWQ;
+  constexpr int VPT = TcwLoad<FMT>::VPT;
+  static_assert(PART % 16 == 0, "TMEM loads of 16 columns");
+  DevState* st = P.st;
+  if (st->done) return;
+  const int l = st->l;
+  const int64_t j0 = st->ns + st->k, n2 = P.n - j0;
+  if (l <= 0 || n2 <= 0 || P.m - st->ns <= 0) return;
+  const int o = tc_shift(P, st->ns);
+  const int64_t ns = st->ns - o, mr = P.m - ns;
+  const int64_t c0 = j0 + (int64_t)blockIdx.x * TCW_COLS;
+  int64_t nseg, seg_rows;
+  tc_segments(mr, P.tc_nseg, TC_SEG_ALIGN, &nseg, &seg_rows);
+  const int64_t seg = blockIdx.y;
+  if (c0 >= P.n || seg >= nseg) return;
+  if (blockIdx.x == 0 && seg == 0 && threadIdx.x == 0)
+    add_flops(st, KID_TRAIL_W, 2.0 * (double)(mr - o) * (double)n2 * l);
+  const int64_t rbeg = seg * seg_rows, rend = min(mr, rbeg + seg_rows);
+  extern __shared__ unsigned char tcwt_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)tcwt_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* f64s = base + 2 * TCW_STAGE;                                    // FP64 ring
+  uint64_t* bar = reinterpret_cast<uint64_t*>(f64s + NST * G::F64_STAGE);       // [0,1] MMA, [2..] ring
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2 + NST);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(tslot + 1);
+  const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
+  if (wp == 0) tc::tmem_alloc(tslot, 2 * TC_LMAX);
+  const int64_t nchunks = (rend - rbeg + KA - 1) / KA;
+  int64_t tma_issued = 0;  // thread 0: chunks whose tensor copy was issued
+  if (tid == 0) {
+    for (int b = 0; b < 2 + NST; ++b) tc::mbar_init(&bar[b], 1);
+    *s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (; tma_issued < NST && tma_issued < nchunks; ++tma_issued) {
+      tc::mbar_expect_tx(&bar[2 + tma_issued], G::F64_STAGE);
+      tc::tma_load_2d(f64s + tma_issued * G::F64_STAGE, &tmA, (int32_t)(ns + rbeg + tma_issued * KA), (int32_t)c0,
+                      &bar[2 + tma_issued]);
+    }
+  }
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = *tslot;
+  const uint32_t tview = taddr + ((uint32_t)((wp & 3) * 32) << 16) + (uint32_t)((wp >> 2) * PART);
+  float wsum[PART];
+#pragma unroll
+  for (int t = 0; t < PART; ++t) wsum[t] = 0.0f;
+  // conversion units: column cq + 64 q of the tile, lane j of its 8
+  const int j = tid & 7, cq = tid >> 3;
+  const uint4* vsrc = reinterpret_cast<const uint4*>(P.tc_vw + (rbeg / KA) * (2 * TCW_TILE_V));
+  const uint32_t idesc = tc::idesc_f32acc(TCW_COLS, TC_LMAX, FMT);
+  uint4 vreg[2][VPT];
+#pragma unroll
+  for (int q = 0; q < VPT; ++q) vreg[0][q] = vsrc[tid + q * TCW_THREADS];
+  int64_t issued = -1, waited = 0;
+  for (int64_t i0 = 0; i0 < nchunks; i0 += 2) {
+#pragma unroll
+    for (int par = 0; par < 2; ++par) {
+      const int64_t i = i0 + par;
+      if (i < nchunks) {
+        const int s = par;  // = i & 1, split stage and accumulator
+        const int f = (int)(i % NST);
+        if (i + 1 < nchunks) {
+#pragma unroll
+          for (int q = 0; q < VPT; ++q)
+            vreg[1 - par][q] = vsrc[(i + 1) * (2 * TCW_TILE_V / 16) + tid + q * TCW_THREADS];
+        }
+        if (tid == 0) {
+          // chunk i - 2 has left this split stage and accumulator; chunk i has landed
+          if (i >= 2 && !tc::mbar_wait(&bar[s], (uint32_t)(((i >> 1) - 1) & 1), P.wait_ns)) *s_fail = 1;
+          if (!*s_fail && !tc::mbar_wait(&bar[2 + f], (uint32_t)((i / NST) & 1), P.wait_ns)) *s_fail = 1;
+          if (!*s_fail) waited = i + 1;
+        }
+        __syncthreads();
+        if (*s_fail) break;
+        tc::fence_after_sync();
+        if (i >= 2) {
+#pragma unroll
+          for (int q = 0; q < PART / 16; ++q) {
+            float g[16];
+            tc::tmem_ld16(tview + (uint32_t)(s * TC_LMAX + q * 16), g);
+#pragma unroll
+            for (int v = 0; v < 16; ++v) wsum[q * 16 + v] += g[v];
+          }
+        }
+        // FP64 stage f -> split stage s
+        unsigned char* stage = base + s * TCW_STAGE;
+        unsigned char* aH = stage;
+        unsigned char* aL = aH + TCW_TILE_A;
+        unsigned char* vH = aL + TCW_TILE_A;
+        const unsigned char* src = f64s + f * G::F64_STAGE;
+#pragma unroll
+        for (int u = 0; u < TCW_COLS * 8 / TCW_THREADS; ++u) {
+          const int c = cq + (TCW_THREADS / 8) * u;
+#pragma unroll
+          for (int e = 0; e < G::PPL; ++e) {
+            const int h = e * 8 + j;  // 16-byte piece: rows 2h, 2h + 1 of column c
+            const double2 d = *reinterpret_cast<const double2*>(src + (size_t)c * (KA * 8) + h * 16);
+            const float x0 = f64_to_f32_rn(d.x), x1 = f64_to_f32_rn(d.y);
+            const uint32_t off = tc::sw128_off_e<ESZ>(c, 2 * h);
+            if (FMT == 1) {
+              __nv_bfloat16 h0, l0, h1, l1;
+              tc::split_bf16(x0, &h0, &l0);
+              tc::split_bf16(x1, &h1, &l1);
+              __nv_bfloat162 hh, ll;
+              hh.x = h0;
+              hh.y = h1;
+              ll.x = l0;
+              ll.y = l1;
+              *reinterpret_cast<__nv_bfloat162*>(aH + off) = hh;
+              *reinterpret_cast<__nv_bfloat162*>(aL + off) = ll;
+            } else {
+              const float h0 = tc::tf32_rna(x0), h1 = tc::tf32_rna(x1);
+              *reinterpret_cast<float2*>(aH + off) = make_float2(h0, h1);
+              *reinterpret_cast<float2*>(aL + off) = make_float2(tc::tf32_rna(x0 - h0), tc::tf32_rna(x1 - h1));
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) reinterpret_cast<uint4*>(vH)[tid + q * TCW_THREADS] = vreg[par][q];
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          // FP64 stage f is free: the chunk NST ahead goes there
+          if (tma_issued < nchunks) {
+            tc::mbar_expect_tx(&bar[2 + f], G::F64_STAGE);
+            tc::tma_load_2d(f64s + f * G::F64_STAGE, &tmA, (int32_t)(ns + rbeg + tma_issued * KA), (int32_t)c0,
+                            &bar[2 + f]);
+            ++tma_issued;
+          }
+          const uint32_t a_h = tc::smem_u32(stage), a_l = a_h + TCW_TILE_A;
+          const uint32_t v_h = a_l + TCW_TILE_A, v_l = v_h + TCW_TILE_V;
+          const uint32_t d = taddr + (uint32_t)(s * TC_LMAX);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t oo = kk * 32;
+            tc_mma<FMT>(d, tc::sw128_desc(a_h + oo), tc::sw128_desc(v_l + oo), idesc, kk > 0 ? 1u : 0u);
+            tc_mma<FMT>(d, tc::sw128_desc(a_l + oo), tc::sw128_desc(v_h + oo), idesc, 1u);
+          }
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t oo = kk * 32;
+            tc_mma<FMT>(d, tc::sw128_desc(a_h + oo), tc::sw128_desc(v_h + oo), idesc, 1u);
+          }
+          tc::mma_commit(&bar[s]);
+        }
+        issued = i;
+      }
+    }
+    if (*s_fail) break;
+  }
+  const int64_t last = nchunks - 1;
+  if (tid == 0 && !*s_fail && !tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), P.wait_ns)) *s_fail = 1;
+  __syncthreads();
+  tc::fence_after_sync();
+  if (*s_fail) {
+    // leave no copy or MMA in flight: bounded waits for the last MMA issued
+    // and for every tensor copy issued but not yet waited for
+    if (tid == 0) {
+      if (issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), P.wait_ns);
+      for (int64_t c = waited; c < tma_issued; ++c)
+        if (!tc::mbar_wait(&bar[2 + (int)(c % NST)], (uint32_t)((c / NST) & 1), P.wait_ns)) break;
+      record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TRAIL_W);
+    }
+  } else {
+    for (int64_t i = max((int64_t)0, last - 1); i <= last; ++i) {
+#pragma unroll
+      for (int q = 0; q < PART / 16; ++q) {
+        float g[16];
+        tc::tmem_ld16(tview + (uint32_t)((int)(i & 1) * TC_LMAX + q * 16), g);
+#pragma unroll
+        for (int v = 0; v < 16; ++v) wsum[q * 16 + v] += g[v];
+      }
+    }
+    const int64_t col = c0 + (wp & 3) * 32 + lane;
+    if (col < P.n) {
+      float4* o4 = reinterpret_cast<float4*>(P.Wt + ((seg + 1) * P.n + col) * TC_LMAX + (wp >> 2) * PART);
+#pragma unroll
+      for (int v = 0; v < PART / 4; ++v)
+        o4[v] = make_float4(wsum[4 * v], wsum[4 * v + 1], wsum[4 * v + 2], wsum[4 * v + 3]);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (wp == 0) tc::tmem_dealloc(taddr, 2 * TC_LMAX);
+}
+
 // The candidate Gram matrix G = C^T C of the tensor-core forms (C: the kc <=
 // 64 candidate columns of rows ns..m-1, gathered through P.cols).  CTA c
 // takes the 64-row chunks c, c + gridDim.x, ... as the FP64/FP32 Gram kernels
@@ -658,8 +892,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gram(Params P) {
 }
 
 // W = T^T (sum of the segments' V^T A22) per trailing column: one warp per
-// column; lanes t and t + 32 sum their reflector's segments in FP64, apply T
-// (upper, from P.T) in FP32 and write W's hi/lo operand image for the update
+// column; lanes t and t + 32 sum their reflector's segments in FP64 into
+// P_t.  T is not formed: with S = V^T V (k_tc_sred), T^-1 = strict_upper(S) +
+// diag(1/htau), so W solves (T^-1)^T W = P by forward substitution,
+// W_t = htau_t (P_t - sum_{q<t} S_qt W_q), right-looking across the lanes in
+// FP32 (W_t from its lane by a shuffle, then every later lane subtracts its
+// S_tu W_t); then W's hi/lo operand image for the update is written
 // (128-column tiles from column ns + k; padding columns of the last tile are
 // zero).
 template <int FMT>
@@ -671,13 +909,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_wsum(Params P) {
   const int64_t ns = st->ns, j0 = ns + st->k;
   const int64_t n2 = P.n - j0, mr = P.m - ns;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
-  __shared__ float s_T[TC_LMAX][TC_LMAX + 1];
-  __shared__ float s_g[TC_THREADS / 32][TC_LMAX];
+  __shared__ float s_S[TC_LMAX][TC_LMAX + 1];  // S_qt, q < t
+  __shared__ float s_tau[TC_LMAX];
   const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
   for (int e = tid; e < TC_LMAX * TC_LMAX; e += TC_THREADS) {
     const int q = e / TC_LMAX, t = e % TC_LMAX;
-    s_T[q][t] = (q < l && t < l && q <= t) ? (float)P.T[(int64_t)t * KMAX + q] : 0.0f;
+    s_S[q][t] = (q < t && t < l) ? (float)P.G[t * (t - 1) / 2 + q] : 0.0f;
   }
+  if (tid < TC_LMAX) s_tau[tid] = (tid < l) ? (float)P.htau[st->ns + tid] : 0.0f;
   __syncthreads();
   int64_t nseg, seg_rows;
   tc_segments(mr + tc_shift(P, ns), P.tc_nseg, TC_SEG_ALIGN, &nseg, &seg_rows);  // the W pass's segments
@@ -695,12 +934,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_wsum(Params P) {
         g0 += (double)part[lane];
         g1 += (double)part[lane + 32];
       }
-      s_g[wp][lane] = (float)g0;
-      s_g[wp][lane + 32] = (float)g1;
-      __syncwarp();
-      for (int q = 0; q <= lane; ++q) w0 = fmaf(s_T[q][lane], s_g[wp][q], w0);
-      for (int q = 0; q <= lane + 32; ++q) w1 = fmaf(s_T[q][lane + 32], s_g[wp][q], w1);
-      __syncwarp();
+      float p0 = (float)g0, p1 = (float)g1;  // P_lane, P_{lane + 32}
+      for (int t = 0; t < l; ++t) {
+        const float pt = __shfl_sync(0xffffffffu, t < 32 ? p0 : p1, t & 31);
+        const float wt = s_tau[t] * pt;
+        if (lane > t) p0 = fmaf(-s_S[t][lane], wt, p0);
+        if (lane + 32 > t) p1 = fmaf(-s_S[t][lane + 32], wt, p1);
+        if (lane == (t & 31)) {
+          if (t < 32) p0 = wt;
+          else p1 = wt;
+        }
+      }
+      w0 = (lane < l) ? p0 : 0.0f;
+      w1 = (lane + 32 < l) ? p1 : 0.0f;
     }
     unsigned char* img = P.tc_wi + (c / TCU_COLS) * (2 * NA * TC_ATOM);
     const int cc = (int)(c % TCU_COLS);

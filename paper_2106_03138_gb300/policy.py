@@ -121,6 +121,15 @@ class Policy:
         self._check(_b.load().qrdm_mlp_to_bf16(self.w32.data_ptr(), self.w16.data_ptr(), self._s()),
                     "qrdm_mlp_to_bf16")
 
+    @classmethod
+    def load(cls, path: str, device="cuda") -> "Policy":
+        """A policy from the weights train_policy stored (FP32 master copy)."""
+        with np.load(path) as z:
+            w = z["w32"]
+        pol = cls(device=device)
+        pol.load_weights(w)
+        return pol
+
     def struct(self, *, weights: bool = True, feat_log=None, act_log=None) -> _b.qrdm_policy:
         """qrdm_policy for the C calls (keep the returned object alive)."""
         p = _b.qrdm_policy()
