@@ -105,6 +105,20 @@ def time_oracle_sample(mats, parallel: bool = False) -> tuple[float, float]:
     return time.perf_counter() - t0, fl
 
 
+def time_dgeqp3_sample(mats) -> tuple[float, float]:
+    """(seconds, metric flops) of LAPACK's column-pivoting QR (xGEQP3 through
+    scipy, its own BLAS threads on the host cores) on the sample: the
+    comparator the paper measures QRDM against (Sec. 5)."""
+    import scipy.linalg
+
+    t0 = time.perf_counter()
+    fl = 0.0
+    for A in mats:
+        scipy.linalg.qr(A, mode="raw", pivoting=True, check_finite=False)
+        fl += metric_flops(*A.shape)
+    return time.perf_counter() - t0, fl
+
+
 def oracle_parallel_available() -> bool:
     from oracle import oracle as orc
 
@@ -350,18 +364,20 @@ def measure_c3(q, inputs, torch, stream, hbm_gbs: float | None = None) -> dict:
             kk = np.asarray(t["k"], dtype=np.float64)
             elems = float(np.sum((n - ns) * np.maximum(n - ns - kk, 0.0)))
             kms = {q.KERNEL_NAMES[i]: float(pr.ms[i]) for i in range(len(q.KERNEL_NAMES))}
-            w_gbs = 8.0 * elems / (kms["k_trail_w"] * 1e-3) / 1e9
-            u_gbs = 16.0 * elems / (kms["k_trail_update"] * 1e-3) / 1e9
+            w_gbs = 8.0 * elems / (kms["k_tc_w"] * 1e-3) / 1e9
+            u_gbs = 16.0 * elems / (kms["k_tc_update"] * 1e-3) / 1e9
             out[key]["merged_update"] = {
                 "trailing_elements_over_steps": elems,
-                "w_pass_ms": kms["k_trail_w"], "w_pass_GBps": w_gbs,
-                "update_pass_ms": kms["k_trail_update"], "update_pass_GBps": u_gbs,
+                "w_pass_ms": kms["k_tc_w"], "w_pass_GBps": w_gbs,
+                "update_pass_ms": kms["k_tc_update"], "update_pass_GBps": u_gbs,
+                "subpanel_w_ms": kms["k_trail_w"], "subpanel_update_ms": kms["k_trail_update"],
                 "t_build_ms": kms["k_tc_vtv+k_tc_tbuild"], "v_images_ms": kms["k_tc_vimg"],
                 "w_sum_ms": kms["k_tc_wsum"], "subpanel_w_reduce_ms": kms["k_trail_wreduce"],
                 "hbm_frac_of_measured": {"w_pass": w_gbs / hbm_gbs if hbm_gbs else None,
                                          "update_pass": u_gbs / hbm_gbs if hbm_gbs else None},
-                "note": "the k_trail_w / k_trail_update slots also hold the FP64 sub-panel updates of the panel "
-                        "columns (a small share); profiled run, events around every launch",
+                "note": "k_tc_w / k_tc_update: the merged tensor-core passes over the trailing block; the "
+                        "subpanel_* entries are the FP64 updates of the panel's own columns; profiled run, "
+                        "events around every launch",
                 "kernel_ms": {k: round(v, 2) for k, v in kms.items() if v > 0},
             }
         if prec == 1:
@@ -571,7 +587,44 @@ def measure_c5(q, torch, stream, n_train: int = 150, n_held: int = 60, big: int 
                                single["fixed_0.9_0.9"]["sigma_min_R11_over_sigma_r"])
     out["held_out_single"] = {"matrix": f"{n}x{n}, sigma geometric 1->1e-12 over {r} values then 1e-15, seed 1000",
                               "k_max": KMAX, **single}
-    del A0, ws
+    del A0
+    # the policy trained at scale (paper_2106_03138_gb300/train_policy.py; weights stored beside it), on
+    # the held-out 4096^2 seeds 1000..1009 against fixed (0.9, 0.9); quality sigma_min(R11) / sigma_r
+    # with sigma_min exact (singular values of the r x r block)
+    wpath = os.path.join(ROOT, "paper_2106_03138_gb300", "policy_weights.npz")
+    if os.path.exists(wpath):
+        big = P.Policy.load(wpath)
+        with np.load(wpath) as z:
+            tsum = json.loads(str(z["summary"]))
+        rows = []
+        for sd in range(1000, 1010):
+            A0 = inputs.from_spectrum_gpu(n, n, sig, sd)
+            res = {}
+            for key, kw in (("fixed_0.9_0.9", {}), ("learned", {"policy": big.struct()})):
+                for rep in range(2):
+                    dA = A0.clone()
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    f = q.factor(dA, 0.9, 0.9, KMAX, workspace=ws, stream=stream, **kw)
+                    e1.record(stream)
+                    e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                smin = float(torch.linalg.svdvals(torch.triu(dA[:r, :r]))[-1])
+                res[key] = {"ms": ms, "block_steps": f.nsteps, "quality": smin / float(sig[r - 1])}
+                del dA
+            rows.append({"seed": sd, **res, "speedup": res["fixed_0.9_0.9"]["ms"] / res["learned"]["ms"],
+                         "quality_ratio": res["learned"]["quality"] / res["fixed_0.9_0.9"]["quality"]})
+            del A0
+        sp = np.array([x["speedup"] for x in rows])
+        qr = np.array([x["quality_ratio"] for x in rows])
+        out["held_out_seeds"] = {
+            "matrix": f"{n}x{n}, sigma geometric 1->1e-12 over {r} values then 1e-15, seeds 1000..1009",
+            "weights": "paper_2106_03138_gb300/policy_weights.npz", "training": tsum, "seeds": len(rows),
+            "speedup_median": float(np.median(sp)), "speedup_min": float(sp.min()),
+            "quality_ratio_median": float(np.median(qr)), "quality_ratio_min": float(qr.min()),
+            "within_2x": int(np.sum(qr >= 0.5)), "per_seed": rows,
+            "quality": "sigma_min(R11)/sigma_r, sigma_min exact (torch.linalg.svdvals of the r x r block)"}
+    del ws
     torch.cuda.empty_cache()
     return out
 
@@ -902,6 +955,13 @@ def main() -> int:
             cpu = {"value": single["value"], "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                    "sample": single["sample"], "seconds": secs1, **host,
                    "all_cores": "unavailable: the C compiler has no OpenMP"}
+        try:
+            secs_q, fl_q = time_dgeqp3_sample(mats)
+            cpu["lapack_dgeqp3"] = {"value": fl_q / secs_q / 1e9, "unit": "GFLOP/s", "seconds": secs_q,
+                                    "what": "scipy.linalg.qr(pivoting=True), LAPACK xGEQP3 with the host BLAS "
+                                            "threads, same sample, metric flops (4mn^2-4n^3/3)"}
+        except Exception as exc:  # noqa: BLE001 - context only
+            cpu["lapack_dgeqp3"] = {"unavailable": str(exc)[:200]}
 
     if rank == 0:
         per = [{"matrix": nm, "m": m, "n": n, "rank": f.rank, "rank_colmax": f.rank_colmax, "steps": f.nsteps}

@@ -35,7 +35,7 @@ def main() -> int:
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--batch", type=int, default=2048)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--quality-factor", type=float, default=P.QUALITY_FACTOR)
+    ap.add_argument("--quality-factor", type=float, default=0.75)
     ap.add_argument("--out", required=True)
     args = ap.parse_args()
     load()
@@ -46,7 +46,7 @@ def main() -> int:
     for c in range(0, len(entries), args.chunk):
         part = entries[c:c + args.chunk]
         pristine = [e.build_gpu() for e in part]
-        X, T, info = P.collect(part, pristine, quality_factor=args.quality_factor)
+        X, T, info = P.collect(part, pristine, quality_factor=args.quality_factor, grid_tau=P.GRID_TAU_FINE)
         Xs.append(X)
         Ts.append(T)
         for k, v in info["label_counts"].items():
@@ -69,7 +69,7 @@ def main() -> int:
                "train_steps": args.steps, "batch": args.batch, "lr": args.lr, "train_s": train_s,
                "quality_factor": args.quality_factor,
                "loss_first50": float(loss[:50].mean()), "loss_last50": float(loss[-50:].mean()),
-               "grid_tau": list(P.GRID_TAU), "grid_delta": list(P.GRID_DELTA)}
+               "grid_tau": list(P.GRID_TAU_FINE), "grid_delta": list(P.GRID_DELTA)}
     np.savez(args.out, w32=pol.w32.cpu().numpy(), summary=json.dumps(summary))
     print(json.dumps(summary), flush=True)
     return 0
