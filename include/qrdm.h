@@ -68,18 +68,23 @@ extern "C" {
 #define QRDM_K_WY_T 13         /* a8, merged forms: V^T V of the step and its compact-WY T */
 #define QRDM_K_TC_VIMG 14      /* a9, tensor-core forms: V's operand images */
 #define QRDM_K_TC_WSUM 15      /* a9, tensor-core forms: W = T^T (sum of segments) and W's image */
-#define QRDM_NKERNELS 16
+#define QRDM_K_TC_W 16         /* a9, tensor-core forms: the merged W = V^T A22 (tcgen05) */
+#define QRDM_K_TC_UPDATE 17    /* a9, tensor-core forms: the merged A22 -= V W (tcgen05) */
+#define QRDM_NKERNELS 18
 
 /* Optional per-kernel timing (host struct, filled when opts->profile is set):
-   every launch is bracketed by CUDA events on the caller's stream; ms[] sums
+   every launch is bracketed by CUDA events on the caller's stream (and the
+   FP64 form's look-ahead, which runs part of each trailing update on a second
+   stream beside the next panel, is off, so that each kernel's time is its
+   own); ms[] sums
    the device time per kernel, flops[] the algorithmic FP64 flops its
    launches performed (for the trailing update 4 m' n'' l + 2 l^2 n''), and
    launches[] counts them.  Values accumulate across calls; zero the struct to
    reset it. */
 typedef struct qrdm_profile {
-  double ms[16];
-  double flops[16];
-  int64_t launches[16];
+  double ms[24];
+  double flops[24];
+  int64_t launches[24];
 } qrdm_profile;
 
 /* Options; a NULL pointer means all zero (the defaults). */

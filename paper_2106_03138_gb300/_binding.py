@@ -32,11 +32,11 @@ QRDM_KMAX_LIMIT = 128
 
 KERNEL_NAMES = ("k_colnorm_init", "k_select", "k_gram", "k_gram_reduce", "k_pick", "k_permute", "k_panel",
                 "k_trail_w", "k_trail_wreduce", "k_trail_update", "k_downdate", "k_step_end", "k_qrp_tail",
-                "k_tc_vtv+k_tc_tbuild", "k_tc_vimg", "k_tc_wsum")
+                "k_tc_vtv+k_tc_tbuild", "k_tc_vimg", "k_tc_wsum", "k_tc_w", "k_tc_update")
 
 
 class qrdm_profile(ctypes.Structure):
-    _fields_ = [("ms", c_f64 * 16), ("flops", c_f64 * 16), ("launches", c_i64 * 16)]
+    _fields_ = [("ms", c_f64 * 24), ("flops", c_f64 * 24), ("launches", c_i64 * 24)]
 
 
 class qrdm_policy(ctypes.Structure):

@@ -220,10 +220,10 @@ int configure(DeviceConfig* cfg) {
       if ((e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
         return (int)e;
     int o1 = 0, o2 = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_tc_update<1>, TC_THREADS, tcu_smem<1>())) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_tc_update<1>, tcu_threads<1>(), tcu_smem<1>())) !=
         cudaSuccess)
       return (int)e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_tc_update<2>, TC_THREADS, tcu_smem<2>())) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_tc_update<2>, tcu_threads<2>(), tcu_smem<2>())) !=
         cudaSuccess)
       return (int)e;
     // each CTA holds 2 x TCU_COLS TMEM columns of the 512
@@ -639,7 +639,8 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   // look-ahead (FP64 form only): the side stream takes each sub-panel's bulk update
   LookAhead* la = nullptr;
   bool la_ok = false;
-  if (allow_side && o.precision == 0 && nsub_full > 1) {
+  // (not under opts.profile: there every kernel's event time must be its own)
+  if (allow_side && o.precision == 0 && nsub_full > 1 && !o.profile) {
     CK(lookahead_resources(cfg.device, &la));
     la_ok = true;
   }
@@ -756,7 +757,7 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
              })) != cudaSuccess)
           return e;
       } else {
-        if ((e = run(QRDM_K_TRAIL_W, [&] {
+        if ((e = run(QRDM_K_TC_W, [&] {
                if (use_tma) {
                  if (tf32)
                    k_tc_w_tma<2><<<tcw_grid, TCW_THREADS, TcwTma<2>::SMEM, stream>>>(tmA, P);
@@ -776,11 +777,11 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
                  k_tc_wsum<1><<<2 * sms, TC_THREADS, 0, stream>>>(P);
              })) != cudaSuccess)
           return e;
-        if ((e = run(QRDM_K_TRAIL_UPDATE, [&] {
+        if ((e = run(QRDM_K_TC_UPDATE, [&] {
                if (tf32)
-                 k_tc_update<2><<<tcu_grid2, TC_THREADS, tcu_smem<2>(), stream>>>(P);
+                 k_tc_update<2><<<tcu_grid2, tcu_threads<2>(), tcu_smem<2>(), stream>>>(P);
                else
-                 k_tc_update<1><<<tcu_grid1, TC_THREADS, tcu_smem<1>(), stream>>>(P);
+                 k_tc_update<1><<<tcu_grid1, tcu_threads<1>(), tcu_smem<1>(), stream>>>(P);
              })) != cudaSuccess)
           return e;
       }

@@ -55,7 +55,7 @@ struct alignas(128) DevState {
   // not the fields above, because sub-panel j + 1 may run beside them
   int32_t sub_l[KMAX / PB];
   int32_t sub_next[KMAX / PB];
-  double flops[16]; // algorithmic FP64 flops per kernel id (profile)
+  double flops[24]; // algorithmic flops per kernel id (profile)
   // grid barrier of the fused single-column kernel and its diagnostics
   unsigned int gbar;     // arrivals (monotonic within one launch)
   int32_t abort_flag;    // set when a bounded wait gave up or a check failed; every kernel then stops
@@ -121,7 +121,8 @@ struct Params {
 // kernel ids (same numbering as QRDM_K_* in the C header)
 enum KernelId {
   KID_COLNORM = 0, KID_SELECT, KID_GRAM, KID_GRAM_REDUCE, KID_PICK, KID_PERMUTE, KID_PANEL, KID_TRAIL_W,
-  KID_TRAIL_WREDUCE, KID_TRAIL_UPDATE, KID_DOWNDATE, KID_STEP_END, KID_QRP_TAIL, KID_WY_T, KID_TC_VIMG, KID_TC_WSUM
+  KID_TRAIL_WREDUCE, KID_TRAIL_UPDATE, KID_DOWNDATE, KID_STEP_END, KID_QRP_TAIL, KID_WY_T, KID_TC_VIMG, KID_TC_WSUM,
+  KID_TC_W, KID_TC_UPDATE
 };
 
 __device__ __forceinline__ void add_flops(DevState* st, int kid, double f) { atomicAdd(&st->flops[kid], f); }
@@ -1264,23 +1265,66 @@ __device__ __forceinline__ void trail_w_body(const Params& P, double* smem, int 
     TC acc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = (TC)0;
-    for (int64_t r0 = rbeg; r0 < rend; r0 += TW_SUB) {
-      const int rows = (int)min((int64_t)TW_SUB, rend - r0);
-      __syncthreads();
-      for (int e = tid; e < TW_SUB * COLS; e += GEMM_THREADS) {
+    // Software pipeline (l >= 4, TG >= 4): the elements of pass r0 + TW_SUB
+    // are loaded into registers while pass r0 is computed from shared memory,
+    // so the global load latency hides behind the FMAs (each thread holds AE
+    // elements of A and VE of V).  Tiny blocks (TG < 4) stage directly.
+    constexpr bool PIPE = TG >= 4 && NQ <= 4;  // the sub-panel updates (l <= 16)
+    constexpr int AE = PIPE ? TW_SUB * COLS / GEMM_THREADS : 1;                          // 32 / TG
+    constexpr int VE = PIPE ? (TW_SUB * TG * NQ + GEMM_THREADS - 1) / GEMM_THREADS : 1;  // l <= TG NQ
+    double ra[AE], rv[VE];
+    auto load_pass = [&](int64_t p0) {
+      const int prow = (int)min((int64_t)TW_SUB, rend - p0);
+#pragma unroll
+      for (int k = 0; k < AE; ++k) {
+        const int e = tid + k * GEMM_THREADS;
         const int cc = e / TW_SUB, rr = e % TW_SUB;
         double v = 0.0;
-        if (rr < rows && cc < ncols) {
+        if (rr < prow && cc < ncols) {
           const int64_t cl = cbase + cc;
-          v = (cl < wc.ns) ? vget(P.A, lda, ns, r0 + rr, (int)cl) : P.A[wc.phys(cl) * lda + ns + r0 + rr];
+          v = (cl < wc.ns) ? vget(P.A, lda, ns, p0 + rr, (int)cl) : P.A[wc.phys(cl) * lda + ns + p0 + rr];
         }
-        s_a[rr * LDA_S + cc] = (TC)v;
+        ra[k] = v;
       }
-      for (int e = tid; e < TW_SUB * l; e += GEMM_THREADS) {
+#pragma unroll
+      for (int k = 0; k < VE; ++k) {
+        const int e = tid + k * GEMM_THREADS;
         const int t = e / TW_SUB, rr = e % TW_SUB;
-        s_v[rr * LDV_S + t] = (TC)((rr < rows) ? vget(P.A, lda, ns, r0 + rr, t) : 0.0);
+        rv[k] = (t < l && rr < prow) ? vget(P.A, lda, ns, p0 + rr, t) : 0.0;
+      }
+    };
+    if (PIPE) load_pass(rbeg);
+    for (int64_t r0 = rbeg; r0 < rend; r0 += TW_SUB) {
+      const int rows = (int)min((int64_t)TW_SUB, rend - r0);
+      __syncthreads();  // the previous pass is done with shared memory
+      if (PIPE) {
+#pragma unroll
+        for (int k = 0; k < AE; ++k) {
+          const int e = tid + k * GEMM_THREADS;
+          s_a[(e % TW_SUB) * LDA_S + e / TW_SUB] = (TC)ra[k];
+        }
+#pragma unroll
+        for (int k = 0; k < VE; ++k) {
+          const int e = tid + k * GEMM_THREADS;
+          if (e / TW_SUB < l) s_v[(e % TW_SUB) * LDV_S + e / TW_SUB] = (TC)rv[k];
+        }
+      } else {
+        for (int e = tid; e < TW_SUB * COLS; e += GEMM_THREADS) {
+          const int cc = e / TW_SUB, rr = e % TW_SUB;
+          double v = 0.0;
+          if (rr < rows && cc < ncols) {
+            const int64_t cl = cbase + cc;
+            v = (cl < wc.ns) ? vget(P.A, lda, ns, r0 + rr, (int)cl) : P.A[wc.phys(cl) * lda + ns + r0 + rr];
+          }
+          s_a[rr * LDA_S + cc] = (TC)v;
+        }
+        for (int e = tid; e < TW_SUB * l; e += GEMM_THREADS) {
+          const int t = e / TW_SUB, rr = e % TW_SUB;
+          s_v[rr * LDV_S + t] = (TC)((rr < rows) ? vget(P.A, lda, ns, r0 + rr, t) : 0.0);
+        }
       }
       __syncthreads();
+      if (PIPE && r0 + TW_SUB < rend) load_pass(r0 + TW_SUB);
       for (int rr = 0; rr < rows; ++rr) {
         const TC a = s_a[rr * LDA_S + c];
         const TC* vr = s_v + rr * LDV_S + tg;
@@ -1927,20 +1971,18 @@ __global__ void __launch_bounds__(QRP_THREADS) k_qrp_tail(Params P) {
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if (lane == 0) s_red[wp] = part;
     __syncthreads();
-    if (tid == 0) {
+    if (wp == 0) {  // warp 0: beta, then the two quotients at once in lanes 0 and 1
       double s2 = 0.0;
       for (int q = 0; q < QRP_THREADS / 32; ++q) s2 += s_red[q];
       const double alpha = s_x[0];
-      if (s2 == 0.0) {
-        s_sc[0] = alpha;
-        s_sc[1] = 0.0;
-        s_sc[2] = 0.0;
-      } else {
-        const double nrm = sqrt(alpha * alpha + s2);
-        const double beta = (alpha >= 0.0) ? -nrm : nrm;
+      const double nrm = sqrt(alpha * alpha + s2);
+      const double beta = (s2 == 0.0) ? alpha : ((alpha >= 0.0) ? -nrm : nrm);
+      const double qv = ((lane == 0) ? (beta - alpha) : 1.0) / ((lane == 0) ? beta : (alpha - beta));
+      const double q1 = __shfl_sync(0xffffffffu, qv, 1);
+      if (lane == 0) {
         s_sc[0] = beta;
-        s_sc[1] = (beta - alpha) / beta;
-        s_sc[2] = 1.0 / (alpha - beta);
+        s_sc[1] = (s2 == 0.0) ? 0.0 : qv;
+        s_sc[2] = (s2 == 0.0) ? 0.0 : q1;
       }
     }
     __syncthreads();
@@ -2110,7 +2152,7 @@ __global__ void k_state_init(Params P) {
     st->sub_l[q] = 0;
     st->sub_next[q] = 0;
   }
-  for (int i = 0; i < 16; ++i) st->flops[i] = 0.0;
+  for (int i = 0; i < 24; ++i) st->flops[i] = 0.0;
   st->gbar = 0u;
   st->abort_flag = 0;
   st->diag_code = 0;

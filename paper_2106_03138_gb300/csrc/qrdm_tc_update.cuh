@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w(Params P) {
   const int64_t seg = blockIdx.y;
   if (c0 >= P.n || seg >= nseg) return;
   if (blockIdx.x == 0 && seg == 0 && threadIdx.x == 0)
-    add_flops(st, KID_TRAIL_W, 2.0 * (double)(mr - o) * (double)n2 * l);
+    add_flops(st, KID_TC_W, 2.0 * (double)(mr - o) * (double)n2 * l);
   const int64_t rbeg = seg * seg_rows, rend = min(mr, rbeg + seg_rows);
   const bool al = P.tc_al != 0;
   extern __shared__ unsigned char tcw_raw[];
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w(Params P) {
   if (*s_fail) {
     // leave no MMA writing TMEM behind: a bounded wait for the last one issued
     if (tid == 0 && issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), P.wait_ns);
-    if (tid == 0) record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TRAIL_W);
+    if (tid == 0) record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TC_W);
   } else {
     for (int64_t i = max((int64_t)0, last - 1); i <= last; ++i) {
 #pragma unroll
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w_tma(const __grid_consta
   const int64_t seg = blockIdx.y;
   if (c0 >= P.n || seg >= nseg) return;
   if (blockIdx.x == 0 && seg == 0 && threadIdx.x == 0)
-    add_flops(st, KID_TRAIL_W, 2.0 * (double)(mr - o) * (double)n2 * l);
+    add_flops(st, KID_TC_W, 2.0 * (double)(mr - o) * (double)n2 * l);
   const int64_t rbeg = seg * seg_rows, rend = min(mr, rbeg + seg_rows);
   extern __shared__ unsigned char tcwt_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tcwt_raw + 1023) & ~(uintptr_t)1023);
@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w_tma(const __grid_consta
       if (issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), P.wait_ns);
       for (int64_t c = waited; c < tma_issued; ++c)
         if (!tc::mbar_wait(&bar[2 + (int)(c % NST)], (uint32_t)((c / NST) & 1), P.wait_ns)) break;
-      record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TRAIL_W);
+      record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TC_W);
     }
   } else {
     for (int64_t i = max((int64_t)0, last - 1); i <= last; ++i) {
@@ -964,9 +964,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_wsum(Params P) {
 // buffers, two tiles ahead) and issues the MMAs into one of two TMEM
 // accumulators (2 x 128 columns); meanwhile all warps stream the previous
 // tile through HBM (load A, subtract, store), 32 loads per thread in flight.
+// threads of k_tc_update: the BF16 form fits two CTAs of 8 warps per SM; the
+// 3xTF32 form's operand buffers allow one CTA per SM, which gets 16 warps so
+// that as many loads of A stay in flight
 template <int FMT>
-__global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
+__host__ __device__ constexpr int tcu_threads() {
+  return FMT == 1 ? 256 : 512;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(tcu_threads<FMT>(), FMT == 1 ? 2 : 1) k_tc_update(Params P) {
   constexpr int NA = TcFmt<FMT>::NA;
+  constexpr int NT = tcu_threads<FMT>();
+  constexpr int CPW = TCU_COLS / (NT / 128);  // columns of a tile per warp (its lane quarter's rows)
   constexpr int OPB = 2 * NA * TC_ATOM;  // bytes of one operand tile, hi and lo
   static_assert(TCU_ROWS == 128 && TCU_COLS == 128, "tiles of 128 rows / columns");
   DevState* st = P.st;
@@ -975,7 +985,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
   const int64_t ns = st->ns, j0 = ns + st->k;
   const int64_t n2 = P.n - j0, mr = P.m - ns, lda = P.lda;
   if (l <= 0 || n2 <= 0 || mr <= 0) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_UPDATE, 2.0 * (double)mr * (double)n2 * l);
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TC_UPDATE, 2.0 * (double)mr * (double)n2 * l);
   const int64_t nct = (n2 + TCU_COLS - 1) / TCU_COLS;
   const int64_t ntiles = ((mr + TCU_ROWS - 1) / TCU_ROWS) * nct;
   const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
@@ -1014,7 +1024,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
   tc::fence_after_sync();
   const uint32_t taddr = *tslot;
   const uint32_t idesc = tc::idesc_f32acc(TCU_ROWS, TCU_COLS, FMT);
-  const int q4 = wp & 3, half = wp >> 2;  // TMEM lane quarter and column half of this warp
+  const int q4 = wp & 3, part = wp >> 2;  // TMEM lane quarter and column part of this warp
   int64_t cur_rb = -1, issued = -1;
   for (int64_t i = 0; i <= nloc; ++i) {
     if (i < nloc) {
@@ -1073,6 +1083,15 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
     }
     if (i >= 1) {  // epilogue of tile i - 1
       const int64_t pi = i - 1, t = t0 + pi, rb = t / nct, ct = t % nct;
+      const int64_t rr = rb * TCU_ROWS + q4 * 32 + lane;
+      const bool rok = rr < mr;
+      double* arow = P.A + ns + rr;
+      const int64_t cb0 = j0 + ct * TCU_COLS + part * CPW;
+      // A of the first 32 columns does not depend on the MMAs: its loads go
+      // out before the wait for them
+      double x[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) x[u] = (rok && cb0 + u < P.n) ? arow[(cb0 + u) * lda] : 0.0;
       if (tid == 0 && !*s_fail) {
         if (!tc::mbar_wait(&bar[pi & 1], (uint32_t)((pi >> 1) & 1), P.wait_ns)) {
           *s_fail = 1;
@@ -1085,17 +1104,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
       __syncthreads();
       if (*s_fail) break;
       tc::fence_after_sync();
-      const int64_t rr = rb * TCU_ROWS + q4 * 32 + lane;
-      const bool rok = rr < mr;
-      double* arow = P.A + ns + rr;
-      const uint32_t tb =
-          taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((pi & 1) * TCU_COLS + half * (TCU_COLS / 2));
+      const uint32_t tb = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((pi & 1) * TCU_COLS + part * CPW);
 #pragma unroll 1
-      for (int c = 0; c < TCU_COLS / 2; c += 32) {
-        const int64_t cb = j0 + ct * TCU_COLS + half * (TCU_COLS / 2) + c;
-        double x[32];
+      for (int c = 0; c < CPW; c += 32) {
+        const int64_t cb = cb0 + c;
+        if (c > 0) {
 #pragma unroll
-        for (int u = 0; u < 32; ++u) x[u] = (rok && cb + u < P.n) ? arow[(cb + u) * lda] : 0.0;
+          for (int u = 0; u < 32; ++u) x[u] = (rok && cb + u < P.n) ? arow[(cb + u) * lda] : 0.0;
+        }
         float v[32];
         tc::tmem_ld16(tb + c, v);
         tc::tmem_ld16(tb + c + 16, v + 16);
@@ -1120,7 +1136,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_tc_update(Params P) {
       for (; v_done < v_iss; ++v_done)
         if (!tc::mbar_wait(&bar[4], v_done & 1u, P.wait_ns)) break;
     }
-    if (tid == 0) record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TRAIL_UPDATE);
+    if (tid == 0) record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TC_UPDATE);
   }
   tc::fence_before_sync();
   __syncthreads();

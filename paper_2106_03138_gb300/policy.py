@@ -123,10 +123,15 @@ class Policy:
 
     @classmethod
     def load(cls, path: str, device="cuda") -> "Policy":
-        """A policy from the weights train_policy stored (FP32 master copy)."""
+        """A policy from the weights train_policy stored (FP32 master copy and
+        the output ranges it was trained for)."""
+        import json
+
         with np.load(path) as z:
             w = z["w32"]
-        pol = cls(device=device)
+            meta = json.loads(str(z["summary"]))
+        pol = cls(device=device, tau_range=tuple(meta.get("tau_range", TAU_RANGE)),
+                  delta_range=tuple(meta.get("delta_range", DELTA_RANGE)), rho_min=meta.get("rho_min", RHO_MIN))
         pol.load_weights(w)
         return pol
 
@@ -303,7 +308,7 @@ GRID_TAU_FINE = (0.25, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9)
 
 
 def collect(entries, pristine, k_max=64, stream=None, quality_factor: float = QUALITY_FACTOR,
-            grid_tau=GRID_TAU, grid_delta=GRID_DELTA) -> tuple[np.ndarray, np.ndarray, dict]:
+            grid_tau=GRID_TAU, grid_delta=GRID_DELTA, tau_range=TAU_RANGE) -> tuple[np.ndarray, np.ndarray, dict]:
     """Sweep the (tau, delta) grid with plain QRDM and build (X, T).  A grid
     point is admissible for a matrix when its sigma_min(R11) / sigma_r is at
     least quality_factor times the fixed (0.9, 0.9) run's.  Returns (X, T,
@@ -342,7 +347,7 @@ def collect(entries, pristine, k_max=64, stream=None, quality_factor: float = QU
                     continue
                 tau_l, delta_l = best[int(ph[s])]
                 X.append(f[s])
-                T.append(normalize(tau_l, delta_l))
+                T.append(normalize(tau_l, delta_l, tau_range=tau_range))
                 label_hist[(tau_l, delta_l)] = label_hist.get((tau_l, delta_l), 0) + 1
     info = {"grid": [list(g) for g in sweeps], "sweep_ms": {f"{g[0]},{g[1]}": sw.ms for g, sw in sweeps.items()},
             "label_counts": {f"{k[0]},{k[1]}": v for k, v in sorted(label_hist.items())},
