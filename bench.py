@@ -201,9 +201,9 @@ def traffic_for(kernel: str):
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    if rec.get("kernel") != kernel or rec.get("source_sha256") != kernel_source_hash():
+    if rec.get("source_sha256") != kernel_source_hash():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec.get("kernels", {}).get(kernel, {}).get("dram_bytes_per_launch")
 
 
 def kernel_source_hash() -> str:

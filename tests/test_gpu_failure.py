@@ -30,7 +30,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 import paper_2106_03138_gb300 as q  # noqa: E402
 
 QRDM_K_PICK = 4
-QRDM_K_TRAIL_UPDATE = 9
+QRDM_K_TC_UPDATE = 17
 
 
 def _gpu_dict(dA, f):
@@ -77,7 +77,7 @@ def test_tensor_core_update_wait_runs_out_and_frees_its_tensor_memory(precision)
     e = ei.value
     assert e.code == q.QRDM_ERR_TIMEOUT
     assert e.info.fail_code == q.QRDM_FAIL_MMA_WAIT
-    assert e.info.fail_value == QRDM_K_TRAIL_UPDATE
+    assert e.info.fail_value == QRDM_K_TC_UPDATE
     assert e.info.fail_step == 0
     for _ in range(2):
         dA = q.colmajor(A)
