@@ -20,17 +20,19 @@ import time
 import numpy as np
 
 
-VALIDATION_SEEDS = (2000, 2001, 2002, 2003)  # 4096^2 validation matrices, apart from the held-out 1000..1009
+VALIDATION_SEEDS = tuple(range(2000, 2010))  # 4096^2 validation matrices, apart from the held-out 1000..1009
 RHO_GRID = (0.5, 0.6, 0.7, 0.8, 0.9)
 
 
 def calibrate_rho(path: str, bar: float = 0.6, n: int = 4096) -> dict:
     """Choose the guard threshold rho_min of stored weights on validation
     matrices (n x n, sigma geometric 1 -> 1e-12 over 3n/4 values then 1e-15,
-    seeds VALIDATION_SEEDS): the smallest rho in RHO_GRID for which every
-    validation matrix keeps sigma_min(R11) / sigma_r at least `bar` times
-    that of fixed (0.9, 0.9) (exact sigma_min of the r x r block).  Writes it
-    into the file's summary and returns the calibration record."""
+    seeds VALIDATION_SEEDS): every rho in RHO_GRID is tried, and the smallest
+    one for which every validation matrix keeps sigma_min(R11) / sigma_r at
+    least `bar` times that of fixed (0.9, 0.9) (exact sigma_min of the r x r
+    block) is taken; the largest rho when none does.  Writes it into the
+    file's summary and returns the calibration record (per rho: the worst and
+    median quality ratio and the median time ratio against fixed)."""
     import torch
 
     from . import factor, inputs, qrdm_workspace_size
@@ -42,33 +44,40 @@ def calibrate_rho(path: str, bar: float = 0.6, n: int = 4096) -> dict:
     pol = P.Policy.load(path)
 
     def run(A0, kw):
-        dA = A0.clone()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        f = factor(dA, 0.9, 0.9, 64, workspace=ws, **kw)
-        torch.cuda.synchronize()
-        ms = 1e3 * (time.perf_counter() - t0)
+        best = None
+        for _ in range(2):  # the second run is timed warm
+            dA = A0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            f = factor(dA, 0.9, 0.9, 64, workspace=ws, **kw)
+            torch.cuda.synchronize()
+            best = 1e3 * (time.perf_counter() - t0)
         q = float(torch.linalg.svdvals(torch.triu(dA[:r, :r]))[-1]) / float(sig[r - 1])
-        return ms, f.nsteps, q
+        return best, f.nsteps, q
 
-    mats = [inputs.from_spectrum_gpu(n, n, sig, sd) for sd in VALIDATION_SEEDS]
-    ref = [run(A0, {}) for A0 in mats]
     record = {"seeds": list(VALIDATION_SEEDS), "bar": bar, "trials": []}
-    chosen = RHO_GRID[-1]
+    ref, got = [], {rho: [] for rho in RHO_GRID}
+    for sd in VALIDATION_SEEDS:
+        A0 = inputs.from_spectrum_gpu(n, n, sig, sd)
+        ref.append(run(A0, {}))
+        for rho in RHO_GRID:
+            pol.rho_min = rho
+            got[rho].append(run(A0, {"policy": pol.struct()}))
+        del A0
+    chosen = None
     for rho in RHO_GRID:
-        pol.rho_min = rho
-        got = [run(A0, {"policy": pol.struct()}) for A0 in mats]
-        ratios = [g[2] / rf[2] for g, rf in zip(got, ref)]
-        steps = [g[1] / rf[1] for g, rf in zip(got, ref)]
-        record["trials"].append({"rho_min": rho, "quality_ratio_min": min(ratios), "step_ratio_max": max(steps)})
-        if min(ratios) >= bar:
+        ratios = [g[2] / rf[2] for g, rf in zip(got[rho], ref)]
+        times = [g[0] / rf[0] for g, rf in zip(got[rho], ref)]
+        record["trials"].append({"rho_min": rho, "quality_ratio_min": min(ratios),
+                                 "quality_ratio_median": float(np.median(ratios)),
+                                 "time_ratio_median": float(np.median(times))})
+        if chosen is None and min(ratios) >= bar:
             chosen = rho
-            break
-    record["rho_min"] = chosen
+    record["rho_min"] = chosen if chosen is not None else RHO_GRID[-1]
     with np.load(path) as z:
         w = z["w32"]
         summary = json.loads(str(z["summary"]))
-    summary["rho_min"] = chosen
+    summary["rho_min"] = record["rho_min"]
     summary["rho_calibration"] = record
     np.savez(path, w32=w, summary=json.dumps(summary))
     return record
