@@ -160,6 +160,12 @@ int configure(DeviceConfig* cfg) {
   if ((e = cudaFuncSetAttribute(k_tc_update<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcu_smem<2>())) !=
       cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(k_tc_update_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcuTma<1>::SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_tc_update_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcuTma<2>::SMEM)) != cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(k_trail_w32, cudaFuncAttributeMaxDynamicSharedMemorySize, S32_SMEM)) != cudaSuccess)
     return (int)e;
   if ((e = cudaFuncSetAttribute(k_trail_update32, cudaFuncAttributeMaxDynamicSharedMemorySize, S32_SMEM)) !=
@@ -262,14 +268,14 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// tensor map of the FP64 matrix (rows inner) with boxes of `rows` rows x 128
-// columns; false when it cannot be made
-bool encode_a_map(CUtensorMap* map, double* dA, int64_t m, int64_t n, int64_t lda, int rows) {
+// tensor map of the FP64 matrix (rows inner) with boxes of `rows` rows x
+// `cols` columns; false when it cannot be made
+bool encode_a_map(CUtensorMap* map, double* dA, int64_t m, int64_t n, int64_t lda, int rows, int cols) {
   const EncodeTiledFn enc = encode_tiled();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
   const cuuint64_t strides[1] = {(cuuint64_t)lda * sizeof(double)};
-  const cuuint32_t box[2] = {(cuuint32_t)rows, (cuuint32_t)TCW_COLS};
+  const cuuint32_t box[2] = {(cuuint32_t)rows, (cuuint32_t)cols};
   const cuuint32_t es[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, dA, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -648,7 +654,12 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   CUtensorMap tmA;
   memset(&tmA, 0, sizeof(tmA));
   const bool use_tma = merged && !merged64 && P.tc_al &&
-                       encode_a_map(&tmA, dA, m, n, lda, tf32 ? TcwTma<2>::KA : TcwTma<1>::KA);
+                       encode_a_map(&tmA, dA, m, n, lda, tf32 ? TcwTma<2>::KA : TcwTma<1>::KA, TCW_COLS);
+  // and the update streams it by tensor copies in sub-tiles of 128 rows x 32 columns
+  CUtensorMap tmU;
+  memset(&tmU, 0, sizeof(tmU));
+  const bool use_tcu_tma = use_tma && encode_a_map(&tmU, dA, m, n, lda, TCU_ROWS, TcuTma<1>::SUBC);
+  P.tcu_tma = use_tcu_tma ? 1 : 0;
   const unsigned tcv_grid = (unsigned)std::min<int64_t>(TCV_CHUNKS, (m + TCV_ROWS_MIN - 1) / TCV_ROWS_MIN);
   const dim3 tcw_grid((unsigned)((n + TCW_COLS - 1) / TCW_COLS), (unsigned)P.tc_nseg);
   // persistent update: at most one CTA per tile of the first step's trailing block
@@ -656,6 +667,9 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   const int tcvi_grid = (int)std::min<int64_t>((int64_t)sms * 4, ((m + 127) / 128 * 128 * TC_LMAX + TC_THREADS - 1) / TC_THREADS);
   const int tcu_grid1 = (int)std::min<int64_t>(tcu_tiles, (int64_t)sms * cfg.tcu_occ[0]);
   const int tcu_grid2 = (int)std::min<int64_t>(tcu_tiles, (int64_t)sms * cfg.tcu_occ[1]);
+  // the streamed update: one CTA per SM (its rows may start one row higher)
+  const int tcu_grid_tma =
+      (int)std::min<int64_t>(((m + 1 + TCU_ROWS - 1) / TCU_ROWS) * ((n + TCU_COLS - 1) / TCU_COLS), (int64_t)sms);
   auto enqueue_step = [&](int nsub) -> cudaError_t {
     cudaError_t e;
     const bool use_la = (la_ok && nsub > 1);
@@ -778,10 +792,16 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
              })) != cudaSuccess)
           return e;
         if ((e = run(QRDM_K_TC_UPDATE, [&] {
-               if (tf32)
+               if (use_tcu_tma) {
+                 if (tf32)
+                   k_tc_update_tma<2><<<tcu_grid_tma, TcuTma<2>::THREADS, TcuTma<2>::SMEM, stream>>>(tmU, P);
+                 else
+                   k_tc_update_tma<1><<<tcu_grid_tma, TcuTma<1>::THREADS, TcuTma<1>::SMEM, stream>>>(tmU, P);
+               } else if (tf32) {
                  k_tc_update<2><<<tcu_grid2, tcu_threads<2>(), tcu_smem<2>(), stream>>>(P);
-               else
+               } else {
                  k_tc_update<1><<<tcu_grid1, tcu_threads<1>(), tcu_smem<1>(), stream>>>(P);
+               }
              })) != cudaSuccess)
           return e;
       }

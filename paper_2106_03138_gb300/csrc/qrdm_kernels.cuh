@@ -108,6 +108,7 @@ struct Params {
   unsigned char* tc_vu; // V's operand image for the update
   unsigned char* tc_wi; // W's operand image for the update
   int32_t tc_al;        // 1: A and lda allow 16-byte loads from an even row (the W pass starts its rows there)
+  int32_t tcu_tma;      // 1: the update streams A by tensor copies from that even row (V's update image shifted too)
   int32_t checked;      // 1: range-check every device-derived index before use (opts.checked)
   int32_t test_fault;   // test hook of opts.test_fault (0: none)
   int64_t wait_ns;      // limit of every bounded device-side wait, in global-timer nanoseconds

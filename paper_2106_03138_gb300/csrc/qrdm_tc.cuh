@@ -171,6 +171,30 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int32_t
       : "memory");
 }
 
+// one thread: tiled 2-D tensor copy (TMA) of the box at element coordinates
+// (x, y) from this CTA's shared memory to global memory (elements outside the
+// tensor are not written); completes in the thread's current bulk group.
+// x * element size must be a multiple of 16 bytes and x, y >= 0
+__device__ __forceinline__ void tma_store_2d(const void* tmap, int32_t x, int32_t y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(tmap), "r"(x),
+               "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+
+// close the bulk group of the stores issued so far
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// wait until every committed bulk store has read its shared-memory source
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// wait until every committed bulk store has written global memory
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// one arrival on the mbarrier (release at CTA scope)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // round FP32 to TF32 (nearest, ties away), returned as an FP32 bit pattern
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;

@@ -247,7 +247,8 @@ __device__ __forceinline__ int tc_shift(const Params& P, int64_t ns) { return (P
 // V's operand images, one element per thread (rows padded with zeros to the
 // next 128): Vw for the W pass (chunk of KA rows: reflector t is the tile's
 // row, the chunk's rows its K) and Vu for the update (block of 128 rows: row
-// r is the tile's row, the reflectors its K, in NA atoms)
+// r is the tile's row, the reflectors its K, in NA atoms; shifted by o rows
+// like Vw when the update streams A by tensor copies)
 template <int FMT>
 __global__ void __launch_bounds__(TC_THREADS) k_tc_vimg(Params P) {
   constexpr int ESZ = TcFmt<FMT>::ESZ, KA = TcFmt<FMT>::KA, NA = TcFmt<FMT>::NA;
@@ -262,8 +263,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_vimg(Params P) {
   for (int64_t e = (int64_t)blockIdx.x * TC_THREADS + threadIdx.x; e < total; e += (int64_t)gridDim.x * TC_THREADS) {
     const int t = (int)(e / pad);
     const int64_t r = e % pad;
-    const double vu = (t < l && r < mr) ? vget(P.A, P.lda, ns, r, t) : 0.0;
-    const double vw = (o == 0) ? vu : ((t < l && r >= 1 && r - 1 < mr) ? vget(P.A, P.lda, ns, r - 1, t) : 0.0);
+    const double v0 = (t < l && r < mr) ? vget(P.A, P.lda, ns, r, t) : 0.0;
+    const double vw = (o == 0) ? v0 : ((t < l && r >= 1 && r - 1 < mr) ? vget(P.A, P.lda, ns, r - 1, t) : 0.0);
+    const double vu = P.tcu_tma ? vw : v0;  // the streamed update's tiles start at the same even row
     unsigned char* w = P.tc_vw + (r / KA) * (2 * TC_LMAX * 128);
     tc_put<FMT>(w, w + TC_LMAX * 128, tc::sw128_off_e<ESZ>(t, (int)(r % KA)), f64_to_f32_rn(vw));
     unsigned char* u = P.tc_vu + (r / 128) * (2 * NA * TC_ATOM) + (t / KA) * TC_ATOM;
@@ -1141,6 +1143,225 @@ __global__ void __launch_bounds__(tcu_threads<FMT>(), FMT == 1 ? 2 : 1) k_tc_upd
   tc::fence_before_sync();
   __syncthreads();
   if (wp == 0) tc::tmem_dealloc(taddr, 2 * TCU_COLS);
+}
+
+
+// The update with A streamed by tensor copies (TMA), when A is 16-byte
+// aligned with an even lda (P.tc_al): the tiles of k_tc_update start at the
+// even row ns - o (o = ns mod 2; V's image then holds a zero row on top, so
+// row ns - 1 is rewritten with its own bits), and each tile passes through
+// shared memory in four sub-tiles of 32 columns (32 KB of FP64).  A ring of
+// NS stages: a tiled tensor copy brings a sub-tile in, the epilogue warps
+// subtract the accumulator in place, a tiled tensor copy writes it back, and
+// the stage takes the sub-tile NS ahead.  Loads and stores need no thread and
+// no load-queue slot, so the ring keeps NS - 1 sub-tiles in flight while one
+// is converted.  Warp 8 issues every copy and MMA (one thread); warps 0-7 are
+// the epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (the tile's
+// rows) and 16 of each sub-tile's columns.  One CTA per SM (persistent, the
+// same balanced tile ranges as k_tc_update); the BF16 form double-buffers W,
+// the 3xTF32 form (operand tiles twice as large) has one W buffer, reloaded
+// as soon as the tile's MMAs are done.
+template <int FMT>
+struct TcuTma {
+  static constexpr int NA = TcFmt<FMT>::NA;
+  static constexpr int OPB = 2 * NA * TC_ATOM;  // one operand tile, hi and lo
+  static constexpr int NWB = (FMT == 1) ? 2 : 1;  // W buffers
+  static constexpr int NS = (FMT == 1) ? 4 : 3;   // FP64 sub-tile stages
+  static constexpr int SUBC = 32;                 // columns of a sub-tile
+  static constexpr int NSUB = TCU_COLS / SUBC;
+  static constexpr int STAGE = TCU_ROWS * SUBC * 8;
+  static constexpr int THREADS = 288;  // 8 epilogue warps and the copy / MMA warp
+  static constexpr int SMEM = 1024 + (1 + NWB) * OPB + NS * STAGE + 256;
+};
+
+template <int FMT>
+__global__ void __launch_bounds__(TcuTma<FMT>::THREADS, 1)
+    k_tc_update_tma(const __grid_constant__ CUtensorMap tmU, Params P) {
+  using G = TcuTma<FMT>;
+  constexpr int NA = G::NA, OPB = G::OPB, NWB = G::NWB, NS = G::NS, NSUB = G::NSUB;
+  static_assert(TCU_ROWS == 128 && TCU_COLS == 128, "tiles of 128 rows / columns");
+  DevState* st = P.st;
+  if (st->done) return;
+  const int l = st->l;
+  const int64_t j0 = st->ns + st->k, n2 = P.n - j0;
+  if (l <= 0 || n2 <= 0 || P.m - st->ns <= 0) return;
+  const int o = tc_shift(P, st->ns);
+  const int64_t r0 = st->ns - o, mr = P.m - r0;  // tile rows start at the even row r0
+  if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TC_UPDATE, 2.0 * (double)(mr - o) * (double)n2 * l);
+  const int64_t nct = (n2 + TCU_COLS - 1) / TCU_COLS;
+  const int64_t ntiles = ((mr + TCU_ROWS - 1) / TCU_ROWS) * nct;
+  const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+  if (t0 >= t1) return;
+  const int64_t nloc = t1 - t0, nsub = nloc * NSUB;
+  extern __shared__ unsigned char tcut_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)tcut_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* vbuf = base;                      // V hi atoms, then lo atoms
+  unsigned char* wbuf = base + OPB;                // NWB buffers of W
+  unsigned char* ring = base + (1 + NWB) * OPB;    // NS FP64 stages
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ring + NS * G::STAGE);
+  uint64_t* b_mma = bar;             // [2] MMAs of accumulator 0 / 1 done
+  uint64_t* b_w = bar + 2;           // [NWB] W landed
+  uint64_t* b_v = bar + 4;           // V landed
+  uint64_t* b_hook = bar + 5;        // never arrived on (test hook 3)
+  uint64_t* b_full = bar + 6;        // [NS] sub-tile landed
+  uint64_t* b_done = bar + 6 + NS;   // [NS] sub-tile subtracted (8 arrivals)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 6 + 2 * NS);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(tslot + 1);
+  const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
+  if (wp == 8) tc::tmem_alloc(tslot, 2 * TCU_COLS);
+  if (tid == 256) {
+    for (int b = 0; b < 6 + NS; ++b) tc::mbar_init(&bar[b], 1);
+    for (int b = 0; b < NS; ++b) tc::mbar_init(&b_done[b], 8);
+    *s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = *tslot;
+  if (wp == 8) {
+    if (lane == 0) {
+      const long long lim = P.wait_ns;
+      auto rb_of = [&](int64_t i) { return (t0 + i) / nct; };
+      auto ct_of = [&](int64_t i) { return (t0 + i) % nct; };
+      auto sx = [&](int64_t g) { return (int32_t)(r0 + rb_of(g / NSUB) * TCU_ROWS); };
+      auto sy = [&](int64_t g) { return (int32_t)(j0 + ct_of(g / NSUB) * TCU_COLS + (g % NSUB) * G::SUBC); };
+      int64_t loads = 0, w_iss = 0, w_wait = 0, mma_iss = -1, cur_rb = -1;
+      uint32_t v_iss = 0, v_wait = 0;
+      bool ok = true;
+      auto issue_w = [&](int64_t i) {
+        tc::mbar_expect_tx(&b_w[i % NWB], OPB);
+        tc::bulk_g2s(wbuf + (i % NWB) * OPB, P.tc_wi + ct_of(i) * OPB, OPB, &b_w[i % NWB]);
+        w_iss = i + 1;
+      };
+      auto issue_load = [&](int64_t g) {
+        const int s = (int)(g % NS);
+        tc::mbar_expect_tx(&b_full[s], G::STAGE);
+        tc::tma_load_2d(ring + s * G::STAGE, &tmU, sx(g), sy(g), &b_full[s]);
+        loads = g + 1;
+      };
+      // MMAs of tile i into accumulator i & 1 (its previous tile's epilogue is done)
+      auto issue_mma = [&](int64_t i) -> bool {
+        const int64_t rb = rb_of(i);
+        if (rb != cur_rb) {  // a new row block: the MMAs issued so far still read V
+          if (i > 0 && !tc::mbar_wait(&b_mma[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1), lim)) return false;
+          tc::mbar_expect_tx(b_v, OPB);
+          tc::bulk_g2s(vbuf, P.tc_vu + rb * OPB, OPB, b_v);
+          ++v_iss;
+          if (!tc::mbar_wait(b_v, v_wait & 1u, lim)) return false;
+          ++v_wait;
+          cur_rb = rb;
+        }
+        if (!tc::mbar_wait(&b_w[i % NWB], (uint32_t)((i / NWB) & 1), lim)) return false;
+        w_wait = i + 1;
+        if (i == 0 && P.test_fault == 3 && !tc::mbar_wait(b_hook, 0u, lim)) return false;
+        tc::fence_after_sync();
+        const uint32_t idesc = tc::idesc_f32acc(TCU_ROWS, TCU_COLS, FMT);
+        const uint32_t d = taddr + (uint32_t)((i & 1) * TCU_COLS);
+        const uint32_t vh = tc::smem_u32(vbuf), vl = vh + NA * TC_ATOM;
+        const uint32_t wh = tc::smem_u32(wbuf + (i % NWB) * OPB), wl = wh + NA * TC_ATOM;
+        // cross terms first, then hi*hi (only those truncate at the scale of the sum)
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t off = a * TC_ATOM + kk * 32;
+            tc_mma<FMT>(d, tc::sw128_desc(vh + off), tc::sw128_desc(wl + off), idesc, (a > 0 || kk > 0) ? 1u : 0u);
+            tc_mma<FMT>(d, tc::sw128_desc(vl + off), tc::sw128_desc(wh + off), idesc, 1u);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t off = a * TC_ATOM + kk * 32;
+            tc_mma<FMT>(d, tc::sw128_desc(vh + off), tc::sw128_desc(wh + off), idesc, 1u);
+          }
+        }
+        tc::mma_commit(&b_mma[i & 1]);
+        mma_iss = i;
+        return true;
+      };
+      issue_w(0);
+      if (NWB == 2 && nloc > 1) issue_w(1);
+      for (int64_t g = 0; g < NS && g < nsub; ++g) issue_load(g);
+      ok = issue_mma(0);
+      if (ok && NWB == 1 && nloc > 1) {  // the one W buffer is free once tile 0's MMAs are done
+        ok = tc::mbar_wait(&b_mma[0], 0u, lim);
+        if (ok) issue_w(1);
+      }
+      for (int64_t g = 0; ok && g < nsub; ++g) {
+        const int s = (int)(g % NS);
+        const int64_t i = g / NSUB;
+        const int sub = (int)(g % NSUB);
+        if (*s_fail || !tc::mbar_wait(&b_done[s], (uint32_t)((g / NS) & 1), lim)) {
+          ok = false;
+          break;
+        }
+        // (a sub-tile wholly right of the last column was loaded as zeros and is not stored)
+        if (sy(g) < P.n) tc::tma_store_2d(&tmU, sx(g), sy(g), ring + s * G::STAGE);
+        tc::bulk_commit();
+        if (sub == 0 && i + 1 < nloc) {
+          // tile i's epilogue has begun, so its MMAs are done: W buffer (i mod 2)
+          // takes tile i + 2 (BF16 form), and tile i + 1's MMAs go out
+          if (NWB == 2 && i + 2 < nloc) issue_w(i + 2);
+          if (!(ok = issue_mma(i + 1))) break;
+        }
+        if (NWB == 1 && sub == 1 && i + 2 < nloc) {
+          if (!(ok = tc::mbar_wait(&b_mma[(i + 1) & 1], (uint32_t)(((i + 1) >> 1) & 1), lim))) break;
+          issue_w(i + 2);
+        }
+        if (g + NS < nsub) {  // the stage takes the sub-tile NS ahead once the store has read it
+          tc::bulk_wait_read_all();
+          issue_load(g + NS);
+        }
+      }
+      tc::bulk_wait_all();
+      if (!ok) {
+        *s_fail = 1;
+        // leave no copy or MMA in flight: bounded waits for the last of each
+        if (mma_iss >= 0) (void)tc::mbar_wait(&b_mma[mma_iss & 1], (uint32_t)((mma_iss >> 1) & 1), lim);
+        for (int64_t i = w_wait; i < w_iss; ++i)
+          if (!tc::mbar_wait(&b_w[i % NWB], (uint32_t)((i / NWB) & 1), lim)) break;
+        if (v_wait < v_iss) (void)tc::mbar_wait(b_v, v_wait & 1u, lim);
+        for (int64_t g = (loads > NS ? loads - NS : 0); g < loads; ++g)
+          if (!tc::mbar_wait(&b_full[g % NS], (uint32_t)((g / NS) & 1), lim)) break;
+        record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TC_UPDATE);
+      }
+    }
+    __syncwarp();
+  } else {
+    const int q4 = wp & 3, half = wp >> 2;
+    const int row = q4 * 32 + lane;  // the tile's row this thread subtracts
+    for (int64_t i = 0; i < nloc && !*s_fail; ++i) {
+      if (!tc::mbar_wait(&b_mma[i & 1], (uint32_t)((i >> 1) & 1), P.wait_ns)) {
+        *s_fail = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t tb = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((i & 1) * TCU_COLS + half * 16);
+      for (int sub = 0; sub < NSUB; ++sub) {
+        const int64_t g = i * NSUB + sub;
+        const int s = (int)(g % NS);
+        float v[16];
+        tc::tmem_ld16(tb + (uint32_t)(sub * G::SUBC), v);
+        if (!tc::mbar_wait(&b_full[s], (uint32_t)((g / NS) & 1), P.wait_ns)) *s_fail = 1;
+        if (*s_fail) break;
+        double* col = reinterpret_cast<double*>(ring + s * G::STAGE) + (half * 16) * TCU_ROWS + row;
+        // FP32 -> FP64 on the integer pipe (exact); the FP64 pipe does the subtraction
+#pragma unroll
+        for (int u = 0; u < 16; ++u) col[u * TCU_ROWS] = col[u * TCU_ROWS] - f32_to_f64(v[u]);
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&b_done[s]);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (wp == 8) tc::tmem_dealloc(taddr, 2 * TCU_COLS);
 }
 
 }  // namespace qrdm
