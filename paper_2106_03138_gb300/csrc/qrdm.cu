@@ -654,7 +654,7 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   CUtensorMap tmA;
   memset(&tmA, 0, sizeof(tmA));
   const bool use_tma = merged && !merged64 && P.tc_al &&
-                       encode_a_map(&tmA, dA, m, n, lda, tf32 ? TcwTma<2>::KA : TcwTma<1>::KA, TCW_COLS);
+                       encode_a_map(&tmA, dA, m, n, lda, TcwTma<1>::BOXR, TCW_COLS);
   // and the update streams it by tensor copies in sub-tiles of 128 rows x 32 columns
   CUtensorMap tmU;
   memset(&tmU, 0, sizeof(tmU));
@@ -774,9 +774,9 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
         if ((e = run(QRDM_K_TC_W, [&] {
                if (use_tma) {
                  if (tf32)
-                   k_tc_w_tma<2><<<tcw_grid, TCW_THREADS, TcwTma<2>::SMEM, stream>>>(tmA, P);
+                   k_tc_w_tma<2><<<tcw_grid, TcwTma<2>::THREADS, TcwTma<2>::SMEM, stream>>>(tmA, P);
                  else
-                   k_tc_w_tma<1><<<tcw_grid, TCW_THREADS, TcwTma<1>::SMEM, stream>>>(tmA, P);
+                   k_tc_w_tma<1><<<tcw_grid, TcwTma<1>::THREADS, TcwTma<1>::SMEM, stream>>>(tmA, P);
                } else if (tf32) {
                  k_tc_w<2><<<tcw_grid, TCW_THREADS, TCW_SMEM, stream>>>(P);
                } else {

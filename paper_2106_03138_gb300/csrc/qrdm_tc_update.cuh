@@ -525,32 +525,37 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w(Params P) {
   if (wp == 0) tc::tmem_dealloc(taddr, 2 * TC_LMAX);
 }
 
-// The W pass with TMA (when A is 16-byte aligned and lda even, P.tc_al): the
-// FP64 tile of each K chunk, KA rows x 128 columns, arrives by one tiled
-// tensor copy into a ring of NST FP64 stages, NST chunks ahead of the
-// conversion, so the loads need no thread and no load-queue slot.  The
-// threads convert from shared memory: 8 lanes per column read 16-byte pieces
-// (two rows) side by side, and each lane writes its rows' hi and lo parts
+// The W pass with TMA (when A is 16-byte aligned and lda even, P.tc_al),
+// warp-specialized.  The FP64 rows of each K chunk arrive by tiled tensor
+// copies of 32 rows x 128 columns (32 KB) into a ring of NST boxes, filled as
+// soon as the converters release a box, so NST - 1 boxes stay in flight while
+// one is converted.  Warps 0-7 convert: 8 lanes per column read 16-byte
+// pieces (two rows) side by side and write each pair of rows' hi and lo parts
 // straight into the split operand tile (two BF16 in 4 bytes, or two TF32 in
-// 8).  V's chunk, the accumulators per chunk and the MMAs are those of
-// k_tc_w.
+// 8); they also add each finished chunk's accumulator into FP32 registers
+// (warp w: TMEM lanes 32 (w mod 4) .. + 31, the tile's columns, and 32 of
+// the 64 reflectors).  Warp 8 (one thread) issues the tensor copies, V's
+// chunk (one bulk copy from its image), and the MMAs.  Two split stages and
+// two accumulators alternate, and the MMAs, their order and the chunk order
+// of the sums are those of k_tc_w.
 template <int FMT>
 struct TcwTma {
   static constexpr int KA = TcFmt<FMT>::KA;
-  static constexpr int NST = (FMT == 1) ? 2 : 3;          // FP64 stages
-  static constexpr int F64_STAGE = KA * TCW_COLS * 8;      // 64 KB (BF16), 32 KB (TF32)
-  static constexpr int PPL = KA / 16;                      // 16-byte pieces per lane and column
-  static constexpr int SMEM = 1024 + 2 * TCW_STAGE + NST * F64_STAGE + 128;
+  static constexpr int BOXR = 32;                        // rows of one tensor copy
+  static constexpr int BPC = KA / BOXR;                  // boxes per K chunk (2 BF16, 1 TF32)
+  static constexpr int NST = 4;                          // FP64 boxes in the ring
+  static constexpr int BOX = BOXR * TCW_COLS * 8;        // 32 KB
+  static constexpr int THREADS = 288;                    // 8 converter warps and the copy / MMA warp
+  static constexpr int SMEM = 1024 + 2 * TCW_STAGE + NST * BOX + 256;
 };
 
 template <int FMT>
-__global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w_tma(const __grid_constant__ CUtensorMap tmA, Params P) {
+__global__ void __launch_bounds__(TcwTma<FMT>::THREADS, 1)
+    k_tc_w_tma(const __grid_constant__ CUtensorMap tmA, Params P) {
   using G = TcwTma<FMT>;
-  constexpr int KA = G::KA, NST = G::NST, ESZ = TcFmt<FMT>::ESZ;
-  constexpr int NWQ = TCW_THREADS / 128;
-  constexpr int PART = TC_LMAX / NWQ;
-  constexpr int VPT = TcwLoad<FMT>::VPT;
-  static_assert(PART % 16 == 0, "TMEM loads of 16 columns");
+  constexpr int KA = G::KA, NST = G::NST, BPC = G::BPC, ESZ = TcFmt<FMT>::ESZ;
+  constexpr int PART = TC_LMAX / 2;  // reflector sums each converter thread keeps
+  static_assert(KA % G::BOXR == 0 && PART % 16 == 0, "whole boxes per chunk, TMEM loads of 16 columns");
   DevState* st = P.st;
   if (st->done) return;
   const int l = st->l;
@@ -566,88 +571,156 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w_tma(const __grid_consta
   if (blockIdx.x == 0 && seg == 0 && threadIdx.x == 0)
     add_flops(st, KID_TC_W, 2.0 * (double)(mr - o) * (double)n2 * l);
   const int64_t rbeg = seg * seg_rows, rend = min(mr, rbeg + seg_rows);
+  const int64_t nchunks = (rend - rbeg + KA - 1) / KA, nbox = nchunks * BPC;
   extern __shared__ unsigned char tcwt_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tcwt_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* f64s = base + 2 * TCW_STAGE;                                    // FP64 ring
-  uint64_t* bar = reinterpret_cast<uint64_t*>(f64s + NST * G::F64_STAGE);       // [0,1] MMA, [2..] ring
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2 + NST);
+  unsigned char* ring = base + 2 * TCW_STAGE;  // FP64 boxes
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ring + NST * G::BOX);
+  uint64_t* b_mma = bar;              // [2] MMAs of split stage / accumulator s done
+  uint64_t* b_vt = bar + 2;           // [2] V's chunk landed in split stage s
+  uint64_t* b_conv = bar + 4;         // [2] A's chunk converted into split stage s (8 arrivals)
+  uint64_t* b_acc = bar + 6;          // [2] accumulator s read (8 arrivals)
+  uint64_t* b_full = bar + 8;         // [NST] box landed
+  uint64_t* b_free = bar + 8 + NST;   // [NST] box converted (8 arrivals)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 8 + 2 * NST);
   volatile int* s_fail = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
-  if (wp == 0) tc::tmem_alloc(tslot, 2 * TC_LMAX);
-  const int64_t nchunks = (rend - rbeg + KA - 1) / KA;
-  int64_t tma_issued = 0;  // thread 0: chunks whose tensor copy was issued
-  if (tid == 0) {
-    for (int b = 0; b < 2 + NST; ++b) tc::mbar_init(&bar[b], 1);
+  if (wp == 8) tc::tmem_alloc(tslot, 2 * TC_LMAX);
+  if (tid == 256) {
+    for (int b = 0; b < 8 + 2 * NST; ++b) tc::mbar_init(&bar[b], 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&b_conv[b], 8);
+      tc::mbar_init(&b_acc[b], 8);
+    }
+    for (int b = 0; b < NST; ++b) tc::mbar_init(&b_free[b], 8);
     *s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (; tma_issued < NST && tma_issued < nchunks; ++tma_issued) {
-      tc::mbar_expect_tx(&bar[2 + tma_issued], G::F64_STAGE);
-      tc::tma_load_2d(f64s + tma_issued * G::F64_STAGE, &tmA, (int32_t)(ns + rbeg + tma_issued * KA), (int32_t)c0,
-                      &bar[2 + tma_issued]);
-    }
   }
-  tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = *tslot;
-  const uint32_t tview = taddr + ((uint32_t)((wp & 3) * 32) << 16) + (uint32_t)((wp >> 2) * PART);
-  float wsum[PART];
-#pragma unroll
-  for (int t = 0; t < PART; ++t) wsum[t] = 0.0f;
-  // conversion units: column cq + 64 q of the tile, lane j of its 8
-  const int j = tid & 7, cq = tid >> 3;
-  const uint4* vsrc = reinterpret_cast<const uint4*>(P.tc_vw + (rbeg / KA) * (2 * TCW_TILE_V));
-  const uint32_t idesc = tc::idesc_f32acc(TCW_COLS, TC_LMAX, FMT);
-  uint4 vreg[2][VPT];
-#pragma unroll
-  for (int q = 0; q < VPT; ++q) vreg[0][q] = vsrc[tid + q * TCW_THREADS];
-  int64_t issued = -1, waited = 0;
-  for (int64_t i0 = 0; i0 < nchunks; i0 += 2) {
-#pragma unroll
-    for (int par = 0; par < 2; ++par) {
-      const int64_t i = i0 + par;
-      if (i < nchunks) {
-        const int s = par;  // = i & 1, split stage and accumulator
-        const int f = (int)(i % NST);
-        if (i + 1 < nchunks) {
-#pragma unroll
-          for (int q = 0; q < VPT; ++q)
-            vreg[1 - par][q] = vsrc[(i + 1) * (2 * TCW_TILE_V / 16) + tid + q * TCW_THREADS];
-        }
-        if (tid == 0) {
-          // chunk i - 2 has left this split stage and accumulator; chunk i has landed
-          if (i >= 2 && !tc::mbar_wait(&bar[s], (uint32_t)(((i >> 1) - 1) & 1), P.wait_ns)) *s_fail = 1;
-          if (!*s_fail && !tc::mbar_wait(&bar[2 + f], (uint32_t)((i / NST) & 1), P.wait_ns)) *s_fail = 1;
-          if (!*s_fail) waited = i + 1;
-        }
-        __syncthreads();
-        if (*s_fail) break;
-        tc::fence_after_sync();
-        if (i >= 2) {
-#pragma unroll
-          for (int q = 0; q < PART / 16; ++q) {
-            float g[16];
-            tc::tmem_ld16(tview + (uint32_t)(s * TC_LMAX + q * 16), g);
-#pragma unroll
-            for (int v = 0; v < 16; ++v) wsum[q * 16 + v] += g[v];
+  const unsigned char* vimg = P.tc_vw + (rbeg / KA) * (2 * TCW_TILE_V);
+  const long long lim = P.wait_ns;
+  int64_t loads = 0, v_iss = 0, v_wait = 0, mma_iss = -1;  // thread 256: copies and MMAs issued / waited
+  if (wp == 8) {
+    if (lane == 0) {
+      bool ok = true;
+      auto issue_box = [&](int64_t bx) {
+        const int f = (int)(bx % NST);
+        tc::mbar_expect_tx(&b_full[f], G::BOX);
+        tc::tma_load_2d(ring + f * G::BOX, &tmA, (int32_t)(ns + rbeg + bx * G::BOXR), (int32_t)c0, &b_full[f]);
+        loads = bx + 1;
+      };
+      auto issue_v = [&](int64_t i) {  // V's chunk i into split stage i & 1 (after its A tiles)
+        unsigned char* vH = base + (i & 1) * TCW_STAGE + 2 * TCW_TILE_A;
+        tc::mbar_expect_tx(&b_vt[i & 1], 2 * TCW_TILE_V);
+        tc::bulk_g2s(vH, vimg + i * (2 * TCW_TILE_V), 2 * TCW_TILE_V, &b_vt[i & 1]);
+        v_iss = i + 1;
+      };
+      for (int64_t bx = 0; bx < NST && bx < nbox; ++bx) issue_box(bx);
+      issue_v(0);
+      if (nchunks > 1) issue_v(1);
+      const uint32_t idesc = tc::idesc_f32acc(TCW_COLS, TC_LMAX, FMT);
+      for (int64_t i = 0; ok && i < nchunks; ++i) {
+        const int s = (int)(i & 1);
+        // the chunk's boxes are converted: the ring takes the boxes NST ahead
+        for (int b = 0; ok && b < BPC; ++b) {
+          const int64_t bx = i * BPC + b;
+          if (*s_fail || !tc::mbar_wait(&b_free[bx % NST], (uint32_t)((bx / NST) & 1), lim)) {
+            ok = false;
+            break;
           }
+          if (bx + NST < nbox) issue_box(bx + NST);
         }
-        // FP64 stage f -> split stage s
+        if (!ok) break;
+        // split stage s holds chunk i (A converted, V landed) and accumulator s was read
+        if (!tc::mbar_wait(&b_conv[s], (uint32_t)((i >> 1) & 1), lim) ||
+            !tc::mbar_wait(&b_vt[s], (uint32_t)((i >> 1) & 1), lim) ||
+            (i >= 2 && !tc::mbar_wait(&b_acc[s], (uint32_t)(((i - 2) >> 1) & 1), lim))) {
+          ok = false;
+          break;
+        }
+        v_wait = i + 1;
+        tc::fence_after_sync();
         unsigned char* stage = base + s * TCW_STAGE;
-        unsigned char* aH = stage;
-        unsigned char* aL = aH + TCW_TILE_A;
-        unsigned char* vH = aL + TCW_TILE_A;
-        const unsigned char* src = f64s + f * G::F64_STAGE;
+        const uint32_t a_h = tc::smem_u32(stage), a_l = a_h + TCW_TILE_A;
+        const uint32_t v_h = a_l + TCW_TILE_A, v_l = v_h + TCW_TILE_V;
+        const uint32_t d = taddr + (uint32_t)(s * TC_LMAX);
 #pragma unroll
-        for (int u = 0; u < TCW_COLS * 8 / TCW_THREADS; ++u) {
-          const int c = cq + (TCW_THREADS / 8) * u;
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t oo = kk * 32;
+          tc_mma<FMT>(d, tc::sw128_desc(a_h + oo), tc::sw128_desc(v_l + oo), idesc, kk > 0 ? 1u : 0u);
+          tc_mma<FMT>(d, tc::sw128_desc(a_l + oo), tc::sw128_desc(v_h + oo), idesc, 1u);
+        }
 #pragma unroll
-          for (int e = 0; e < G::PPL; ++e) {
-            const int h = e * 8 + j;  // 16-byte piece: rows 2h, 2h + 1 of column c
-            const double2 d = *reinterpret_cast<const double2*>(src + (size_t)c * (KA * 8) + h * 16);
-            const float x0 = f64_to_f32_rn(d.x), x1 = f64_to_f32_rn(d.y);
-            const uint32_t off = tc::sw128_off_e<ESZ>(c, 2 * h);
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t oo = kk * 32;
+          tc_mma<FMT>(d, tc::sw128_desc(a_h + oo), tc::sw128_desc(v_h + oo), idesc, 1u);
+        }
+        tc::mma_commit(&b_mma[s]);
+        mma_iss = i;
+        // split stage s^1 takes chunk i + 1's V once chunk i - 1's MMAs are done
+        if (i >= 1 && i + 1 < nchunks) {
+          if (!tc::mbar_wait(&b_mma[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1), lim)) {
+            ok = false;
+            break;
+          }
+          issue_v(i + 1);
+        }
+      }
+      if (!ok) *s_fail = 1;
+    }
+    __syncwarp();
+  } else {
+    const uint32_t tview = taddr + ((uint32_t)((wp & 3) * 32) << 16) + (uint32_t)((wp >> 2) * PART);
+    float wsum[PART];
+#pragma unroll
+    for (int t = 0; t < PART; ++t) wsum[t] = 0.0f;
+    const int j = tid & 7, cq = tid >> 3;  // lane j of the 8 of columns cq + 32 u
+    bool ok = true;
+    auto add_acc = [&](int64_t i) {  // chunk i's accumulator into the sums (its MMAs are done)
+#pragma unroll
+      for (int q = 0; q < PART / 16; ++q) {
+        float g[16];
+        tc::tmem_ld16(tview + (uint32_t)((int)(i & 1) * TC_LMAX + q * 16), g);
+#pragma unroll
+        for (int v = 0; v < 16; ++v) wsum[q * 16 + v] += g[v];
+      }
+    };
+    for (int64_t i = 0; ok && i < nchunks; ++i) {
+      const int s = (int)(i & 1);
+      if (i >= 2) {
+        // chunk i - 2 has left split stage s: add its accumulator, free both
+        if (*s_fail || !tc::mbar_wait(&b_mma[s], (uint32_t)(((i - 2) >> 1) & 1), P.wait_ns)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        add_acc(i - 2);
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&b_acc[s]);
+      }
+      unsigned char* aH = base + s * TCW_STAGE;
+      unsigned char* aL = aH + TCW_TILE_A;
+      for (int b = 0; b < BPC; ++b) {
+        const int64_t bx = i * BPC + b;
+        const int f = (int)(bx % NST);
+        if (*s_fail || !tc::mbar_wait(&b_full[f], (uint32_t)((bx / NST) & 1), P.wait_ns)) {
+          ok = false;
+          break;
+        }
+        const unsigned char* src = ring + f * G::BOX;
+#pragma unroll
+        for (int u = 0; u < TCW_COLS / 32; ++u) {
+          const int c = cq + 32 * u;
+#pragma unroll
+          for (int e = 0; e < G::BOXR / 16; ++e) {
+            const int h = e * 8 + j;  // 16-byte piece: rows 2h, 2h + 1 of the box, column c
+            const double2 dd = *reinterpret_cast<const double2*>(src + (size_t)c * (G::BOXR * 8) + h * 16);
+            const float x0 = f64_to_f32_rn(dd.x), x1 = f64_to_f32_rn(dd.y);
+            const uint32_t off = tc::sw128_off_e<ESZ>(c, b * G::BOXR + 2 * h);
             if (FMT == 1) {
               __nv_bfloat16 h0, l0, h1, l1;
               tc::split_bf16(x0, &h0, &l0);
@@ -666,75 +739,48 @@ __global__ void __launch_bounds__(TCW_THREADS, 1) k_tc_w_tma(const __grid_consta
             }
           }
         }
-#pragma unroll
-        for (int q = 0; q < VPT; ++q) reinterpret_cast<uint4*>(vH)[tid + q * TCW_THREADS] = vreg[par][q];
-        tc::fence_proxy_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        if (tid == 0) {
-          tc::fence_after_sync();
-          // FP64 stage f is free: the chunk NST ahead goes there
-          if (tma_issued < nchunks) {
-            tc::mbar_expect_tx(&bar[2 + f], G::F64_STAGE);
-            tc::tma_load_2d(f64s + f * G::F64_STAGE, &tmA, (int32_t)(ns + rbeg + tma_issued * KA), (int32_t)c0,
-                            &bar[2 + f]);
-            ++tma_issued;
-          }
-          const uint32_t a_h = tc::smem_u32(stage), a_l = a_h + TCW_TILE_A;
-          const uint32_t v_h = a_l + TCW_TILE_A, v_l = v_h + TCW_TILE_V;
-          const uint32_t d = taddr + (uint32_t)(s * TC_LMAX);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t oo = kk * 32;
-            tc_mma<FMT>(d, tc::sw128_desc(a_h + oo), tc::sw128_desc(v_l + oo), idesc, kk > 0 ? 1u : 0u);
-            tc_mma<FMT>(d, tc::sw128_desc(a_l + oo), tc::sw128_desc(v_h + oo), idesc, 1u);
-          }
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t oo = kk * 32;
-            tc_mma<FMT>(d, tc::sw128_desc(a_h + oo), tc::sw128_desc(v_h + oo), idesc, 1u);
-          }
-          tc::mma_commit(&bar[s]);
-        }
-        issued = i;
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&b_free[f]);  // the box's reads are done
       }
+      if (!ok) break;
+      tc::fence_proxy_async_smem();  // the split tile is read by the tensor core
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&b_conv[s]);
     }
-    if (*s_fail) break;
-  }
-  const int64_t last = nchunks - 1;
-  if (tid == 0 && !*s_fail && !tc::mbar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1), P.wait_ns)) *s_fail = 1;
-  __syncthreads();
-  tc::fence_after_sync();
-  if (*s_fail) {
-    // leave no copy or MMA in flight: bounded waits for the last MMA issued
-    // and for every tensor copy issued but not yet waited for
-    if (tid == 0) {
-      if (issued >= 0) (void)tc::mbar_wait(&bar[issued & 1], (uint32_t)((issued >> 1) & 1), P.wait_ns);
-      for (int64_t c = waited; c < tma_issued; ++c)
-        if (!tc::mbar_wait(&bar[2 + (int)(c % NST)], (uint32_t)((c / NST) & 1), P.wait_ns)) break;
-      record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TC_W);
-    }
-  } else {
-    for (int64_t i = max((int64_t)0, last - 1); i <= last; ++i) {
-#pragma unroll
-      for (int q = 0; q < PART / 16; ++q) {
-        float g[16];
-        tc::tmem_ld16(tview + (uint32_t)((int)(i & 1) * TC_LMAX + q * 16), g);
-#pragma unroll
-        for (int v = 0; v < 16; ++v) wsum[q * 16 + v] += g[v];
+    // the last two chunks' accumulators
+    for (int64_t i = (nchunks > 2 ? nchunks - 2 : 0); ok && i < nchunks; ++i) {
+      if (*s_fail || !tc::mbar_wait(&b_mma[i & 1], (uint32_t)((i >> 1) & 1), P.wait_ns)) {
+        ok = false;
+        break;
       }
+      tc::fence_after_sync();
+      add_acc(i);
     }
-    const int64_t col = c0 + (wp & 3) * 32 + lane;
-    if (col < P.n) {
-      float4* o4 = reinterpret_cast<float4*>(P.Wt + ((seg + 1) * P.n + col) * TC_LMAX + (wp >> 2) * PART);
+    if (!ok) *s_fail = 1;
+    if (ok) {
+      const int64_t col = c0 + (wp & 3) * 32 + lane;
+      if (col < P.n) {
+        float4* o4 = reinterpret_cast<float4*>(P.Wt + ((seg + 1) * P.n + col) * TC_LMAX + (wp >> 2) * PART);
 #pragma unroll
-      for (int v = 0; v < PART / 4; ++v)
-        o4[v] = make_float4(wsum[4 * v], wsum[4 * v + 1], wsum[4 * v + 2], wsum[4 * v + 3]);
+        for (int v = 0; v < PART / 4; ++v)
+          o4[v] = make_float4(wsum[4 * v], wsum[4 * v + 1], wsum[4 * v + 2], wsum[4 * v + 3]);
+      }
     }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (wp == 0) tc::tmem_dealloc(taddr, 2 * TC_LMAX);
+  tc::fence_after_sync();
+  if (tid == 256 && *s_fail) {
+    // leave no copy or MMA in flight: bounded waits for the last of each
+    if (mma_iss >= 0) (void)tc::mbar_wait(&b_mma[mma_iss & 1], (uint32_t)((mma_iss >> 1) & 1), lim);
+    for (int64_t i = v_wait; i < v_iss; ++i)
+      if (!tc::mbar_wait(&b_vt[i & 1], (uint32_t)((i >> 1) & 1), lim)) break;
+    for (int64_t bx = (loads > NST ? loads - NST : 0); bx < loads; ++bx)
+      if (!tc::mbar_wait(&b_full[bx % NST], (uint32_t)((bx / NST) & 1), lim)) break;
+    record_fail(st, FAIL_MMA_WAIT, (int)blockIdx.x, st->step, st->ns, KID_TC_W);
+  }
+  __syncwarp();
+  if (wp == 8) tc::tmem_dealloc(taddr, 2 * TC_LMAX);
 }
 
 // The candidate Gram matrix G = C^T C of the tensor-core forms (C: the kc <=
