@@ -138,6 +138,9 @@ int configure(DeviceConfig* cfg) {
   const int gram_smem = (int)(KMAX * (GRAM_ROWS + 1) * sizeof(double));
   if ((e = cudaFuncSetAttribute(k_trail_w, cudaFuncAttributeMaxDynamicSharedMemorySize, TRAIL_W_SMEM)) != cudaSuccess)
     return (int)e;
+  if ((e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SEL_STAGE_MAX * (int)sizeof(double))) != cudaSuccess)
+    return (int)e;
   if ((e = cudaFuncSetAttribute(k_tc_tbuild, cudaFuncAttributeMaxDynamicSharedMemorySize, TCB_SMEM)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_tc_gram<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCG_SMEM)) != cudaSuccess)
@@ -569,6 +572,9 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
 
   const int perm_smem = (int)(2 * k_max * 33 * sizeof(double));
   const int gram_smem = (int)(k_max * (GRAM_ROWS + 1) * sizeof(double));
+  // k_select stages the partial norms in shared memory when they fit
+  P.sel_stage = (n <= SEL_STAGE_MAX) ? 1 : 0;
+  const int sel_smem = P.sel_stage ? (int)(n * sizeof(double)) : 0;
   const int pick_smem = (int)((k_max * (k_max + 1) / 2) * sizeof(double));
   unsigned perm_grid = (unsigned)((m + 31) / 32);
   if (perm_grid > (unsigned)(4 * sms)) perm_grid = 4 * sms;
@@ -674,7 +680,7 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
     cudaError_t e;
     const bool use_la = (la_ok && nsub > 1);
     int pending = -1;  // sub-panel whose bulk update the side stream may still run
-    if ((e = run(QRDM_K_SELECT, [&] { k_select<<<1, SEL_THREADS, 0, stream>>>(P); })) != cudaSuccess) return e;
+    if ((e = run(QRDM_K_SELECT, [&] { k_select<<<1, SEL_THREADS, sel_smem, stream>>>(P); })) != cudaSuccess) return e;
     if ((e = run(QRDM_K_GRAM, [&] {
            if (merged && !merged64) {  // the tensor-core forms: the Gram on tcgen05 too
              if (tf32)

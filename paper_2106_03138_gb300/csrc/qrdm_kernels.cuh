@@ -109,6 +109,7 @@ struct Params {
   unsigned char* tc_wi; // W's operand image for the update
   int32_t tc_al;        // 1: A and lda allow 16-byte loads from an even row (the W pass starts its rows there)
   int32_t tcu_tma;      // 1: the update streams A by tensor copies from that even row (V's update image shifted too)
+  int32_t sel_stage;    // 1: k_select's dynamic shared memory holds u[ns..n)
   int32_t checked;      // 1: range-check every device-derived index before use (opts.checked)
   int32_t test_fault;   // test hook of opts.test_fault (0: none)
   int64_t wait_ns;      // limit of every bounded device-side wait, in global-timer nanoseconds
@@ -196,6 +197,24 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
 }
 
+// sum_{q < cnt} p[q * stride], added in q order from 0.0 (so bit for bit the
+// plain loop) with the loads issued eight at a time: the partial sums these
+// reductions read sit in L2, and a loop that waits for each load in turn is
+// latency-bound
+__device__ __forceinline__ double sum_strided(const double* p, int64_t stride, int64_t cnt) {
+  double s = 0.0;
+  int64_t q = 0;
+  for (; q + 8 <= cnt; q += 8) {
+    double x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = p[(q + u) * stride];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += x[u];
+  }
+  for (; q < cnt; ++q) s += p[q * stride];
+  return s;
+}
+
 // operand load in a kernel's compute type
 __device__ __forceinline__ double to_tc(double x, double) { return x; }
 __device__ __forceinline__ float to_tc(double x, float) { return f64_to_f32_rn(x); }
@@ -254,6 +273,7 @@ __device__ __forceinline__ bool better(double va, int64_t pa, double vb, int64_t
 // Also advances n_s by the previous step's l.
 // ---------------------------------------------------------------------------
 constexpr int SEL_THREADS = 1024;
+constexpr int SEL_STAGE_MAX = 24576;  // most partial norms k_select stages in shared memory (192 KB)
 
 __device__ int block_sum_int(int v, int* red) {
   // red: >= 32 ints of shared memory
@@ -357,12 +377,22 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
   __syncthreads();
   if (!s_ctl[0]) return;
   const int64_t ns = st->ns, n = P.n;
+  // the partial norms u[ns..n) in shared memory when the launch gave room
+  // for them (P.sel_stage): the argmax, the count, every radix pass and the
+  // gather read them there
+  extern __shared__ double s_u[];
+  const bool staged = P.sel_stage != 0;
+  if (staged) {
+    for (int64_t j = ns + tid; j < n; j += SEL_THREADS) s_u[j - ns] = P.u[j];
+    __syncthreads();
+  }
+  const double* uu = staged ? s_u - ns : P.u;  // uu[j] = u[j] for j >= ns
 
   // argmax over u[ns..n), ties to the lowest position
   double bv = -1.0;
   int64_t bp = INT64_MAX;
   for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
-    double x = P.u[j];
+    double x = uu[j];
     if (better(x, j, bv, bp)) {
       bv = x;
       bp = j;
@@ -487,7 +517,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
   int c = 0;
   if (K > 0) {
     for (int64_t j = ns + tid; j < n; j += SEL_THREADS)
-      if (j != jstar && P.u[j] >= thr) ++c;
+      if (j != jstar && uu[j] >= thr) ++c;
   }
   const int ncand_all = (K > 0) ? block_sum_int(c, s_red) : 0;
   const int keep = ncand_all < K ? ncand_all : K;
@@ -502,7 +532,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
       for (int b = tid; b < 256; b += SEL_THREADS) s_hist[b] = 0;
       __syncthreads();
       for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
-        double x = P.u[j];
+        double x = uu[j];
         if (j != jstar && x >= thr) {
           unsigned long long key = (unsigned long long)__double_as_longlong(x);
           if ((key & pmask) == prefix) atomicAdd(&s_hist[(key >> shift) & 255], 1);
@@ -519,7 +549,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
     // krem = how many with key == tkey to take (lowest positions first)
     int neq = 0;
     for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
-      double x = P.u[j];
+      double x = uu[j];
       if (j != jstar && x >= thr && (unsigned long long)__double_as_longlong(x) == tkey) ++neq;
     }
     neq = block_sum_int(neq, s_red);
@@ -531,7 +561,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
         for (int b = tid; b < 256; b += SEL_THREADS) s_hist[b] = 0;
         __syncthreads();
         for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
-          double x = P.u[j];
+          double x = uu[j];
           if (j != jstar && x >= thr && (unsigned long long)__double_as_longlong(x) == tkey) {
             uint32_t pk = (uint32_t)j;
             if ((pk & ppmask) == pprefix) atomicAdd(&s_hist[(pk >> shift) & 255], 1);
@@ -557,7 +587,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
   if (keep > 0) {
     const bool all = (ncand_all <= keep);
     for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
-      double x = P.u[j];
+      double x = uu[j];
       if (j == jstar || !(x >= thr)) continue;
       unsigned long long key = (unsigned long long)__double_as_longlong(x);
       bool take = all || key > tkey || (key == tkey && j <= tpos);
@@ -671,9 +701,7 @@ __global__ void __launch_bounds__(256) k_gram_reduce(Params P) {
   const int64_t nchunks = (mr + GRAM_ROWS - 1) / GRAM_ROWS;
   const int nparts = (int)min((int64_t)P.gram_chunks, nchunks);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npairs; e += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += P.Gp[(int64_t)c * P.kmax * P.kmax + e];
-    P.G[e] = s;
+    P.G[e] = sum_strided(P.Gp + e, (int64_t)P.kmax * P.kmax, nparts);
   }
 }
 
@@ -688,18 +716,24 @@ __device__ __forceinline__ int tri(int a, int b) {  // packed upper index, a <= 
 __global__ void __launch_bounds__(256) k_pick(Params P) {
   DevState* st = P.st;
   if (st->done) return;
+  constexpr int KW = KMAX / 32;  // 32-bit words of a row of the compatibility matrix
   __shared__ double s_d[KMAX];   // reciprocal column norms 1/sqrt(G_aa)
   __shared__ int s_col[KMAX];    // positions of the kc gathered columns
   __shared__ int s_J[KMAX];
-  __shared__ int s_k;
-  __shared__ int s_pos[2 * KMAX], s_cont[2 * KMAX];
-  __shared__ int s_np;
+  __shared__ uint32_t s_cmp[KMAX][KW];  // bit b of row a (b < a): |theta(a, b)| < delta
+  __shared__ uint32_t s_jm[KW];         // the accepted set J as a bit set
+  __shared__ int s_k, s_np, s_nm;
+  __shared__ int s_pos[2 * KMAX];  // positions the swaps touch (entry t < k: ns + t)
+  __shared__ int s_eid[KMAX];      // entry holding J_t's position at the step start
+  __shared__ int s_cid[2 * KMAX];  // entry e now holds the column that started at entry s_cid[e]
+  __shared__ int s_inv[2 * KMAX];  // inverse of s_cid
   __shared__ double s_mv[2 * KMAX][2];
   __shared__ int s_mvp[2 * KMAX];
   extern __shared__ double s_g[];  // packed upper Gram matrix, kc*(kc+1)/2
   const int kc = st->kc;
   const int64_t ns = st->ns;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  constexpr int NW = 256 / 32;
 
   if (kc > 1)
     for (int e = tid; e < kc * (kc + 1) / 2; e += blockDim.x) s_g[e] = P.G[e];
@@ -710,108 +744,134 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
     s_d[a] = (d > 0.0) ? 1.0 / d : 0.0;  // reciprocal norm; 0 marks a zero column
   }
   __syncthreads();
-  if (tid < 32) {
-    const double tau_s = st->tau_s;
-    double dlt = st->delta_s;
-    if (P.sdd && kc > 1) {
-      double dm = tau_s * tau_s / (double)((kc - 1) > 1 ? (kc - 1) : 1);
-      if (dm < dlt) dlt = dm;
+  const double tau_s = st->tau_s;
+  double dlt = st->delta_s;
+  if (P.sdd && kc > 1) {
+    const double dm = tau_s * tau_s / (double)((kc - 1) > 1 ? (kc - 1) : 1);
+    if (dm < dlt) dlt = dm;
+  }
+  if (P.pol.active && wp == 0) {
+    // |theta(j*, i)| statistics over the candidates (a feature of the next step)
+    double cs = 0.0, cm = 0.0;
+    for (int a = 1 + lane; a < kc; a += 32) {
+      const double rr = s_d[0] * s_d[a];
+      const double th = (rr > 0.0) ? fabs(s_g[tri(0, a)]) * rr : 1.0;
+      cs += th;
+      cm = fmax(cm, th);
     }
-    if (P.pol.active) {
-      // |theta(j*, i)| statistics over the candidates (a feature of the next step)
-      double cs = 0.0, cm = 0.0;
-      for (int a = 1 + lane; a < kc; a += 32) {
-        const double rr = s_d[0] * s_d[a];
-        const double th = (rr > 0.0) ? fabs(s_g[tri(0, a)]) * rr : 1.0;
-        cs += th;
-        cm = fmax(cm, th);
-      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        cs += __shfl_xor_sync(0xffffffffu, cs, o);
-        cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
-      }
-      if (lane == 0) {
-        st->pc.cos_mean = (kc > 1) ? (float)(cs / (double)(kc - 1)) : 0.0f;
-        st->pc.cos_max = (float)cm;
-      }
+    for (int o = 16; o > 0; o >>= 1) {
+      cs += __shfl_xor_sync(0xffffffffu, cs, o);
+      cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
     }
-    // greedy DM pick (Alg. 1 loop): candidates in order, accept when
-    // |theta(a, b)| = |G_ab| / (||c_a|| ||c_b||) < delta for every accepted b
-    int k = 1;
-    if (lane == 0) s_J[0] = 0;
-    __syncwarp();
-    for (int a = 1; a < kc; ++a) {
-      bool ok = true;
-      const double ra = s_d[a];
-      for (int b = lane; b < k; b += 32) {
-        const int jb = s_J[b];
-        const int lo = jb < a ? jb : a, hi = jb < a ? a : jb;
-        const double rr = ra * s_d[jb];
-        // |theta_ab| = |G_ab| / (||c_a|| ||c_b||); a zero column counts as |theta| = 1
-        const double th = (rr > 0.0) ? fabs(s_g[tri(lo, hi)]) * rr : 1.0;
-        if (!(th < dlt)) ok = false;
-      }
-      if (__all_sync(0xffffffffu, ok)) {
-        if (lane == 0) s_J[k] = a;
-        ++k;
-      }
-      __syncwarp();
-    }
-    // permutation by pairwise swaps: position ns+t <-> current position of J_t
     if (lane == 0) {
-      int np = 0;
-      for (int t = 0; t < k; ++t) {
-        s_pos[np] = (int)(ns + t);
-        s_cont[np] = (int)(ns + t);
-        ++np;
-      }
-      for (int t = 0; t < k; ++t) {
-        const int pj = s_col[s_J[t]];
-        if (pj >= ns + k) {
-          s_pos[np] = pj;
-          s_cont[np] = pj;
-          ++np;
-        }
-      }
-      s_np = np;
-      s_k = k;
+      st->pc.cos_mean = (kc > 1) ? (float)(cs / (double)(kc - 1)) : 0.0f;
+      st->pc.cos_max = (float)cm;
     }
-    __syncwarp();
-    const int np = s_np;
-    for (int t = 0; t < k; ++t) {
-      const int orig = s_col[s_J[t]];  // position of J_t at step start
-      int found = -1;
-      for (int e = lane; e < np; e += 32)
-        if (s_cont[e] == orig) found = e;
-      unsigned b = __ballot_sync(0xffffffffu, found >= 0);
-      if (b == 0u) {  // cannot happen: every selected column is in the list
-        if (lane == 0) st->nonfinite = 3;
-        continue;
+  }
+  // the cosine test of every candidate pair at once: |theta_ab| = |G_ab| /
+  // (||c_a|| ||c_b||) < delta, a zero column counting as |theta| = 1; warp w
+  // takes rows a = w, w + 8, ..., lane b mod 32 of each word
+  for (int a = wp; a < kc; a += NW) {
+    const double ra = s_d[a];
+    for (int q = 0; q < KW && 32 * q < a; ++q) {
+      const int b = 32 * q + lane;
+      bool ok = false;
+      if (b < a) {
+        const double rr = ra * s_d[b];
+        const double th = (rr > 0.0) ? fabs(s_g[tri(b, a)]) * rr : 1.0;
+        ok = th < dlt;
       }
-      const int e_p = __shfl_sync(0xffffffffu, found, __ffs(b) - 1);
-      if (lane == 0) {
-        const int tmp = s_cont[t];  // entry t is position ns+t
-        s_cont[t] = s_cont[e_p];
-        s_cont[e_p] = tmp;
-      }
-      __syncwarp();
+      const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+      if (lane == 0) s_cmp[a][q] = bal;
     }
   }
   __syncthreads();
-  const int k = s_k;
-  const int np = s_np;
-  // compact the moves and permute u, uref, perm
+  // greedy DM pick (Alg. 1 loop): candidates in order, a accepted when its
+  // test passes against every accepted b (all of them before a)
   if (tid == 0) {
-    int nm = 0;
-    for (int e = 0; e < np; ++e) {
-      if (s_cont[e] != s_pos[e]) {
-        P.mdst[nm] = s_pos[e];
-        P.msrc[nm] = s_cont[e];
-        s_mvp[nm] = e;
-        ++nm;
+    for (int q = 0; q < KW; ++q) s_jm[q] = 0u;
+    s_jm[0] = 1u;
+    s_J[0] = 0;
+    int k = 1;
+    for (int a = 1; a < kc; ++a) {
+      uint32_t bad = 0u;
+      for (int q = 0; 32 * q < a; ++q) bad |= s_jm[q] & ~s_cmp[a][q];
+      if (bad == 0u) {
+        s_jm[a >> 5] |= 1u << (a & 31);
+        s_J[k++] = a;
       }
     }
+    s_k = k;
+  }
+  __syncthreads();
+  const int k = s_k;
+  // the positions the pairwise swaps touch: ns + t for t < k, then the
+  // positions of the J_t outside the block, in t order (warp 0)
+  if (wp == 0) {
+    int napp = 0;
+    for (int t0 = 0; t0 < k; t0 += 32) {
+      const int t = t0 + lane;
+      const int pj = (t < k) ? s_col[s_J[t]] : 0;
+      const bool app = (t < k) && pj >= ns + k;
+      const uint32_t bal = __ballot_sync(0xffffffffu, app);
+      const int r = napp + __popc(bal & ((1u << lane) - 1u));
+      if (t < k) {
+        s_pos[t] = (int)(ns + t);
+        if (app) {
+          s_pos[k + r] = pj;
+          s_eid[t] = k + r;
+        } else {
+          s_eid[t] = (int)(pj - ns);
+        }
+      }
+      napp += __popc(bal);
+    }
+    if (lane == 0) s_np = k + napp;
+  }
+  __syncthreads();
+  const int np = s_np;
+  for (int e = tid; e < np; e += blockDim.x) {
+    s_cid[e] = e;
+    s_inv[e] = e;
+  }
+  __syncthreads();
+  // permutation by pairwise swaps (Sec. 4): position ns + t <-> the current
+  // position of J_t, simulated on the entries with the inverse map
+  if (tid == 0) {
+    for (int t = 0; t < k; ++t) {
+      const int e = s_inv[s_eid[t]];
+      if (e != t) {
+        const int ct = s_cid[t], ce = s_cid[e];
+        s_cid[t] = ce;
+        s_cid[e] = ct;
+        s_inv[ce] = t;
+        s_inv[ct] = e;
+      }
+    }
+  }
+  __syncthreads();
+  // the moves, in entry order: the column that started at s_pos[s_cid[e]] goes to s_pos[e]
+  if (wp == 0) {
+    int nm = 0;
+    for (int e0 = 0; e0 < np; e0 += 32) {
+      const int e = e0 + lane;
+      const int src = (e < np) ? s_pos[s_cid[e]] : 0;
+      const bool mv = (e < np) && src != s_pos[e];
+      const uint32_t bal = __ballot_sync(0xffffffffu, mv);
+      if (mv) {
+        const int r = nm + __popc(bal & ((1u << lane) - 1u));
+        P.mdst[r] = s_pos[e];
+        P.msrc[r] = src;
+        s_mvp[r] = e;
+      }
+      nm += __popc(bal);
+    }
+    if (lane == 0) s_nm = nm;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int nm = s_nm;
     if (P.checked) {
       if (P.test_fault == 2 && st->step == 0) {
         // test hook: a destination one past the last column (refused below)
@@ -830,12 +890,12 @@ __global__ void __launch_bounds__(256) k_pick(Params P) {
     }
     st->npairs = nm;
     st->k = k;
-    s_np = nm;
+    s_nm = nm;
   }
   __syncthreads();
-  const int nm = s_np;
+  const int nm = s_nm;
   for (int qq = tid; qq < nm; qq += blockDim.x) {
-    const int src = s_cont[s_mvp[qq]];
+    const int src = P.msrc[qq];
     s_mv[qq][0] = P.u[src];
     s_mv[qq][1] = P.uref[src];
     s_mvp[qq] = P.perm[src];
@@ -1209,7 +1269,7 @@ __device__ __forceinline__ bool w_has_s(const Params& P, int j) { return j >= 0 
 // sub-panel updates of the merged form reach at most 64 columns (the rest of
 // the panel): more row chunks keep the SMs busy, their partials packed 64
 // columns wide so that up to wchunks * n / 64 of them fit the buffer
-constexpr int NARROW_WCHUNKS = 64;
+constexpr int NARROW_WCHUNKS = 128;
 constexpr int NARROW_COLS = 64;
 
 // Row chunks of k_trail_w32: passes of at least S32_ROWS rows (one staged V
@@ -1434,10 +1494,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j)
   if (use_s) {  // S_qt = v_q^T v_t (q < t < l <= PB) and htau, once per CTA
     for (int e = tid; e < l * l; e += GEMM_THREADS) {
       const int q = e / l, t = e % l;
-      double sv = 0.0;
-      if (q < t)
-        for (int64_t ch = 0; ch < nrc; ++ch) sv += P.Wp[ch * g.qstride + (int64_t)q * g.tstride + sg.r0 + t - g.cofs];
-      s_S[q][t] = sv;
+      s_S[q][t] = (q < t) ? sum_strided(P.Wp + (int64_t)q * g.tstride + sg.r0 + t - g.cofs, g.qstride, nrc) : 0.0;
     }
     if (tid < l) s_tau[tid] = P.htau[sg.r0 + tid];
   }
@@ -1446,10 +1503,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j)
     const bool ok = (cbase + c) < cend;
     __syncthreads();
     for (int t = tg; t < l; t += TG) {
-      double sv = 0.0;
-      if (ok)
-        for (int64_t q = 0; q < nrc; ++q) sv += P.Wp[q * g.qstride + (int64_t)t * g.tstride + cbase + c - g.cofs];
-      s_w[t][c] = sv;
+      s_w[t][c] = ok ? sum_strided(P.Wp + (int64_t)t * g.tstride + cbase + c - g.cofs, g.qstride, nrc) : 0.0;
     }
     __syncthreads();
     if (use_s) {
@@ -1568,7 +1622,14 @@ __device__ __forceinline__ void trail_update_kernel(Params& P, int j, int part) 
   if (blockIdx.x == 0 && threadIdx.x == 0) add_flops(st, KID_TRAIL_UPDATE, 2.0 * (double)mr * (double)n2 * l);
   __shared__ TC s_v[TU_KC][TU_ROWS];
   __shared__ TC s_w[TU_KC][TU_COLS];
-  trail_update_tiles<TC, 64>(P, l, ns, j0, cend, mr, s_v, s_w);
+  // tiles 32 columns wide when 64-wide ones would not fill one wave (the
+  // narrow updates of the panel's own columns): twice the CTAs, less of each
+  // tile past the last column; every element is summed in the same order
+  const int64_t nrt = (mr + TU_ROWS - 1) / TU_ROWS;
+  if (nrt * ((n2 + 63) / 64) < (int64_t)gridDim.x)
+    trail_update_tiles<TC, 32>(P, l, ns, j0, cend, mr, s_v, s_w);
+  else
+    trail_update_tiles<TC, 64>(P, l, ns, j0, cend, mr, s_v, s_w);
 }
 
 __global__ void __launch_bounds__(GEMM_THREADS) k_trail_update(Params P, int j, int part) {

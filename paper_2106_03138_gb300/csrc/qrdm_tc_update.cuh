@@ -218,9 +218,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_sred(Params P) {
   const int64_t nch = (mr + per - 1) / per;
   const int npair = l * (l - 1) / 2;
   for (int e = blockIdx.x * TC_THREADS + threadIdx.x; e < npair; e += gridDim.x * TC_THREADS) {
-    double acc = 0.0;
-    for (int64_t c = 0; c < nch; ++c) acc += P.Gp[c * (int64_t)P.kmax * P.kmax + e];
-    P.G[e] = acc;
+    P.G[e] = sum_strided(P.Gp + e, (int64_t)P.kmax * P.kmax, nch);
   }
 }
 
@@ -976,11 +974,21 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_wsum(Params P) {
     float w0 = 0.0f, w1 = 0.0f;
     if (c < n2) {
       const int64_t col = j0 + c;
-      double g0 = 0.0, g1 = 0.0;
-      for (int64_t sg = 0; sg < nseg; ++sg) {
+      // the segments' partials, loaded all at once (nseg <= TC_NSEG_MAX), added in segment order
+      float x0[TC_NSEG_MAX], x1[TC_NSEG_MAX];
+#pragma unroll
+      for (int sg = 0; sg < TC_NSEG_MAX; ++sg) {
         const float* part = P.Wt + ((sg + 1) * P.n + col) * TC_LMAX;
-        g0 += (double)part[lane];
-        g1 += (double)part[lane + 32];
+        x0[sg] = (sg < nseg) ? part[lane] : 0.0f;
+        x1[sg] = (sg < nseg) ? part[lane + 32] : 0.0f;
+      }
+      double g0 = 0.0, g1 = 0.0;
+#pragma unroll
+      for (int sg = 0; sg < TC_NSEG_MAX; ++sg) {
+        if (sg < nseg) {
+          g0 += (double)x0[sg];
+          g1 += (double)x1[sg];
+        }
       }
       float p0 = (float)g0, p1 = (float)g1;  // P_lane, P_{lane + 32}
       for (int t = 0; t < l; ++t) {
