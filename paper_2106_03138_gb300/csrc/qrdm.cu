@@ -135,7 +135,7 @@ int configure(DeviceConfig* cfg) {
   e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return (int)e;
   const int perm_smem = (int)(2 * KMAX * 33 * sizeof(double));
-  const int gram_smem = (int)(KMAX * (GRAM_ROWS + 1) * sizeof(double));
+  const int gram_smem = (int)(KMAX * (GRAM_ROWS_CC + 1) * sizeof(double));
   if ((e = cudaFuncSetAttribute(k_trail_w, cudaFuncAttributeMaxDynamicSharedMemorySize, TRAIL_W_SMEM)) != cudaSuccess)
     return (int)e;
   if ((e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -175,7 +175,7 @@ int configure(DeviceConfig* cfg) {
       cudaSuccess)
     return (int)e;
   if ((e = cudaFuncSetAttribute(k_gram32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(KMAX * (GRAM_ROWS + 1) * sizeof(double)))) != cudaSuccess)
+                                (int)(KMAX * (GRAM_ROWS_CC + 1) * sizeof(double)))) != cudaSuccess)
     return (int)e;
   const int pick_smem_max = (int)(KMAX * (KMAX + 1) / 2 * sizeof(double));
   if ((e = cudaFuncSetAttribute(k_pick, cudaFuncAttributeMaxDynamicSharedMemorySize, pick_smem_max)) != cudaSuccess)
@@ -571,7 +571,8 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   }
 
   const int perm_smem = (int)(2 * k_max * 33 * sizeof(double));
-  const int gram_smem = (int)(k_max * (GRAM_ROWS + 1) * sizeof(double));
+  const int gram_smem = (int)(k_max * (GRAM_ROWS_CC + 1) * sizeof(double));
+  P.gram_rows = (merged && !merged64) ? GRAM_ROWS : GRAM_ROWS_CC;
   // k_select stages the partial norms in shared memory when they fit
   P.sel_stage = (n <= SEL_STAGE_MAX) ? 1 : 0;
   const int sel_smem = P.sel_stage ? (int)(n * sizeof(double)) : 0;

@@ -98,6 +98,7 @@ struct Params {
   double* Wp;      // [wchunks][kmax][n] partial V^T A22
   double* W;       // [kmax][n] T^T V^T A22
   int32_t gram_chunks;  // CTAs of k_gram (= partial Gram matrices)
+  int32_t gram_rows;    // rows of one chunk of the Gram kernel in use (GRAM_ROWS_CC, or GRAM_ROWS on tcgen05)
   int32_t wchunks;      // most row chunks of the W phase
   int32_t w_units;      // target work units of the W phase (same in k_trail_w and k_trail_wreduce)
   int32_t mixed;        // 1: FP32-class trailing update and Gram (geometry of k_trail_w32)
@@ -268,6 +269,14 @@ __device__ __forceinline__ bool better(double va, int64_t pa, double vb, int64_t
   return va > vb || (va == vb && pa < pb);
 }
 
+// The partial norms are non-negative, and non-negative doubles order like
+// their bit patterns read as int64: the selection compares keys on the
+// integer pipe (a warp-wide FP64 compare takes the FP64 pipe as long as an FMA)
+__device__ __forceinline__ long long ukey(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool kbetter_u(long long ka, int64_t pa, long long kb, int64_t pb) {
+  return ka > kb || (ka == kb && pa < pb);
+}
+
 // ---------------------------------------------------------------------------
 // a2/a3: stopping test, argmax, candidate set (one CTA of 1024 threads).
 // Also advances n_s by the previous step's l.
@@ -340,7 +349,7 @@ __device__ int hist_pick(const int* hist, int krem, bool desc, int* s_out) {
 
 __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
   DevState* st = P.st;
-  __shared__ double s_v[32];
+  __shared__ long long s_k[32];
   __shared__ int64_t s_p[32];
   __shared__ int s_red[40];
   __shared__ int s_hist[256];
@@ -348,7 +357,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
   __shared__ int s_ctl[8];
   __shared__ double s_ctld[4];
   __shared__ int s_list[KMAX];
-  __shared__ double s_lu[KMAX];
+  __shared__ long long s_lk[KMAX];
   __shared__ int s_cnt;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 
@@ -388,44 +397,44 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
   }
   const double* uu = staged ? s_u - ns : P.u;  // uu[j] = u[j] for j >= ns
 
-  // argmax over u[ns..n), ties to the lowest position
-  double bv = -1.0;
+  // argmax over u[ns..n), ties to the lowest position (integer keys)
+  long long bk = -1;
   int64_t bp = INT64_MAX;
   for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
-    double x = uu[j];
-    if (better(x, j, bv, bp)) {
-      bv = x;
+    const long long x = ukey(uu[j]);
+    if (kbetter_u(x, j, bk, bp)) {
+      bk = x;
       bp = j;
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-    int64_t op = __shfl_xor_sync(0xffffffffu, bp, o);
-    if (better(ov, op, bv, bp)) {
-      bv = ov;
+    const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+    const int64_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+    if (kbetter_u(ok, op, bk, bp)) {
+      bk = ok;
       bp = op;
     }
   }
   if (lane == 0) {
-    s_v[w] = bv;
+    s_k[w] = bk;
     s_p[w] = bp;
   }
   __syncthreads();
   if (w == 0) {
-    bv = s_v[lane];
+    bk = s_k[lane];
     bp = s_p[lane];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      int64_t op = __shfl_xor_sync(0xffffffffu, bp, o);
-      if (better(ov, op, bv, bp)) {
-        bv = ov;
+      const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      const int64_t op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (kbetter_u(ok, op, bk, bp)) {
+        bk = ok;
         bp = op;
       }
     }
     if (lane == 0) {
-      const double mu = bv;
+      const double mu = __longlong_as_double(bk);
       const int64_t jstar = bp;
       const int64_t nrem = n - ns;
       const double anorm = __longlong_as_double((long long)st->anorm_bits);
@@ -512,12 +521,13 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
     __syncthreads();
   }
   const double thr = s_ctld[0];
+  const long long tk = ukey(thr);  // u >= thr exactly when ukey(u) >= tk (both non-negative)
 
   // count candidates
   int c = 0;
   if (K > 0) {
     for (int64_t j = ns + tid; j < n; j += SEL_THREADS)
-      if (j != jstar && uu[j] >= thr) ++c;
+      if (j != jstar && ukey(uu[j]) >= tk) ++c;
   }
   const int ncand_all = (K > 0) ? block_sum_int(c, s_red) : 0;
   const int keep = ncand_all < K ? ncand_all : K;
@@ -532,9 +542,9 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
       for (int b = tid; b < 256; b += SEL_THREADS) s_hist[b] = 0;
       __syncthreads();
       for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
-        double x = uu[j];
-        if (j != jstar && x >= thr) {
-          unsigned long long key = (unsigned long long)__double_as_longlong(x);
+        const long long kx = ukey(uu[j]);
+        if (j != jstar && kx >= tk) {
+          const unsigned long long key = (unsigned long long)kx;
           if ((key & pmask) == prefix) atomicAdd(&s_hist[(key >> shift) & 255], 1);
         }
       }
@@ -549,8 +559,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
     // krem = how many with key == tkey to take (lowest positions first)
     int neq = 0;
     for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
-      double x = uu[j];
-      if (j != jstar && x >= thr && (unsigned long long)__double_as_longlong(x) == tkey) ++neq;
+      const long long kx = ukey(uu[j]);
+      if (j != jstar && kx >= tk && (unsigned long long)kx == tkey) ++neq;
     }
     neq = block_sum_int(neq, s_red);
     if (neq > krem) {
@@ -561,8 +571,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
         for (int b = tid; b < 256; b += SEL_THREADS) s_hist[b] = 0;
         __syncthreads();
         for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
-          double x = uu[j];
-          if (j != jstar && x >= thr && (unsigned long long)__double_as_longlong(x) == tkey) {
+          const long long kx = ukey(uu[j]);
+          if (j != jstar && kx >= tk && (unsigned long long)kx == tkey) {
             uint32_t pk = (uint32_t)j;
             if ((pk & ppmask) == pprefix) atomicAdd(&s_hist[(pk >> shift) & 255], 1);
           }
@@ -587,15 +597,15 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
   if (keep > 0) {
     const bool all = (ncand_all <= keep);
     for (int64_t j = ns + tid; j < n; j += SEL_THREADS) {
-      double x = uu[j];
-      if (j == jstar || !(x >= thr)) continue;
-      unsigned long long key = (unsigned long long)__double_as_longlong(x);
+      const long long kx = ukey(uu[j]);
+      if (j == jstar || kx < tk) continue;
+      const unsigned long long key = (unsigned long long)kx;
       bool take = all || key > tkey || (key == tkey && j <= tpos);
       if (take) {
         int slot = atomicAdd(&s_cnt, 1);
         if (slot < KMAX) {
           s_list[slot] = (int)j;
-          s_lu[slot] = x;
+          s_lk[slot] = kx;
         }
       }
     }
@@ -604,11 +614,11 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
   const int got = s_cnt;
   // order by (u desc, position asc): rank counting
   if (tid < got && got <= KMAX) {
-    double xv = s_lu[tid];
-    int xp = s_list[tid];
+    const long long xk = s_lk[tid];
+    const int xp = s_list[tid];
     int r = 0;
     for (int b = 0; b < got; ++b) {
-      if (better(s_lu[b], s_list[b], xv, xp)) ++r;
+      if (kbetter_u(s_lk[b], s_list[b], xk, xp)) ++r;
     }
     if (!P.checked || (in_range(P, KID_SELECT, xp, ns, n) && in_range(P, KID_SELECT, 1 + r, 1, P.kmax)))
       P.cols[1 + r] = xp;
@@ -634,7 +644,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(Params P) {
 // Each CTA owns row chunks (grid-stride) and writes a partial upper triangle;
 // k_gram_reduce sums the partials in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
-constexpr int GRAM_ROWS = 64;  // rows staged per pass
+constexpr int GRAM_ROWS = 64;     // rows of one chunk of the tensor-core Gram (whole K atoms)
+constexpr int GRAM_ROWS_CC = 16;  // rows of one chunk of the CUDA-core Gram: enough chunks for every SM
 
 template <typename TC>
 __device__ __forceinline__ void gram_body(Params& P) {
@@ -645,20 +656,20 @@ __device__ __forceinline__ void gram_body(Params& P) {
   const int64_t ns = st->ns, m = P.m;
   const int64_t mr = m - ns;
   extern __shared__ double smg_raw[];
-  TC* smg = reinterpret_cast<TC*>(smg_raw);  // [kc][GRAM_ROWS + 1]
-  const int LDS = GRAM_ROWS + 1;
+  TC* smg = reinterpret_cast<TC*>(smg_raw);  // [kc][GRAM_ROWS_CC + 1]
+  const int LDS = GRAM_ROWS_CC + 1;
   const int npairs = kc * (kc + 1) / 2;
   TC acc[(KMAX * (KMAX + 1) / 2 + 255) / 256];
   const int nper = (npairs + blockDim.x - 1) / blockDim.x;
   for (int q = 0; q < nper; ++q) acc[q] = (TC)0;
-  const int64_t nchunks = (mr + GRAM_ROWS - 1) / GRAM_ROWS;
+  const int64_t nchunks = (mr + GRAM_ROWS_CC - 1) / GRAM_ROWS_CC;
   // chunk c of this CTA: c = blockIdx.x, blockIdx.x + gridDim.x, ...
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    const int64_t r0 = ns + c * GRAM_ROWS;
-    const int rows = (int)min((int64_t)GRAM_ROWS, m - r0);
+    const int64_t r0 = ns + c * GRAM_ROWS_CC;
+    const int rows = (int)min((int64_t)GRAM_ROWS_CC, m - r0);
     __syncthreads();
-    for (int e = threadIdx.x; e < kc * GRAM_ROWS; e += blockDim.x) {
-      int a = e / GRAM_ROWS, i = e % GRAM_ROWS;
+    for (int e = threadIdx.x; e < kc * GRAM_ROWS_CC; e += blockDim.x) {
+      int a = e / GRAM_ROWS_CC, i = e % GRAM_ROWS_CC;
       double x = 0.0;
       if (i < rows) x = P.A[(int64_t)P.cols[a] * P.lda + r0 + i];
       smg[a * LDS + i] = to_tc(x, (TC)0);
@@ -668,7 +679,7 @@ __device__ __forceinline__ void gram_body(Params& P) {
       int e = threadIdx.x + q * blockDim.x;
       if (e >= npairs) break;
       // e -> (a, b) with a <= b, column-major upper triangle enumeration
-      int b = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      int b = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);  // FP32 estimate, corrected below
       while ((b + 1) * (b + 2) / 2 <= e) ++b;
       while (b * (b + 1) / 2 > e) --b;
       int a = e - b * (b + 1) / 2;
@@ -698,7 +709,7 @@ __global__ void __launch_bounds__(256) k_gram_reduce(Params P) {
   if (kc <= 1) return;
   const int npairs = kc * (kc + 1) / 2;
   const int64_t mr = P.m - st->ns;
-  const int64_t nchunks = (mr + GRAM_ROWS - 1) / GRAM_ROWS;
+  const int64_t nchunks = (mr + P.gram_rows - 1) / P.gram_rows;  // the Gram kernel's row chunks
   const int nparts = (int)min((int64_t)P.gram_chunks, nchunks);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npairs; e += gridDim.x * blockDim.x) {
     P.G[e] = sum_strided(P.Gp + e, (int64_t)P.kmax * P.kmax, nparts);
@@ -1049,8 +1060,13 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
   const bool keep_t = P.mixed != 0;
   int lacc = w;
   bool broke = false;
-  double flops = 0.0;
-  double minb = INFINITY;  // smallest accepted |R_ii| (the learned policy's guard)
+  // On this GPU a warp-wide FP64 instruction holds the SM's narrow FP64 pipe
+  // as long as an FMA of 32 lanes, whatever its lanes add: the per-reflector
+  // reductions and scalars below are laid out to issue few of them.
+  int64_t flops = 0;       // thread 0: flops of this launch (integer pipe)
+  double minb = INFINITY;  // thread 0: smallest accepted |R_ii| (the learned policy's guard)
+  __shared__ double s_hw[PB], s_hwr[PB];  // reflector l's coefficients of the columns t > l it updates
+  __shared__ int s_brk, s_app;             // reflector l: the break test fired / H_l is not the identity
   for (int l = 0; l < w; ++l) {
     const int64_t p = r0 + l;  // pivot row and column
     double* slot = s_slot[l & 1];
@@ -1058,35 +1074,82 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
     const bool own_p = (p >= rb && p < re);
     const int lo = keep_t ? 0 : l;  // first column whose dot product this reflector needs
     // partial dot products x_l^T x_t over this CTA's rows below the pivot
-    // (t = l: the squared tail norm), and the pivot-row entries
-    for (int t = lo + wp; t < w; t += nw) {
-      double acc = 0.0;
-      for (int64_t i = i0 + lane; i < re; i += 32) acc = fma(V.at(i, l), V.at(i, t), acc);
+    // (t = l: the squared tail norm), and the pivot-row entries.  Warp wp
+    // takes columns t1 = lo + wp and t2 = t1 + 8; a pair shares the first
+    // level of its lane tree (lanes 0-15 keep t1, 16-31 keep t2), the same
+    // xor 16, 8, 4, 2, 1 tree as one column alone
+    {
+      const int t1 = lo + wp, t2 = t1 + nw;
+      if (t1 < w) {
+        const bool two = t2 < w;
+        double a1 = 0.0, a2 = 0.0;
+        for (int64_t i = i0 + lane; i < re; i += 32) {
+          const double xl = V.at(i, l);
+          a1 = fma(xl, V.at(i, t1), a1);
+          if (two) a2 = fma(xl, V.at(i, t2), a2);
+        }
+        double r;
+        if (two) {
+          const bool up = lane >= 16;
+          r = (up ? a2 : a1) + __shfl_xor_sync(0xffffffffu, up ? a1 : a2, 16);
+        } else {
+          r = a1 + __shfl_xor_sync(0xffffffffu, a1, 16);
+        }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) {
-        slot[t] = acc;
-        slot[PB + t] = own_p ? V.at(p, t) : 0.0;
+        for (int o = 8; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if (lane == 0) {
+          slot[t1] = r;
+          slot[PB + t1] = own_p ? V.at(p, t1) : 0.0;
+        }
+        if (two && lane == 16) {
+          slot[t2] = r;
+          slot[PB + t2] = own_p ? V.at(p, t2) : 0.0;
+        }
       }
     }
     cluster.sync();
-    // cluster-wide sums: lane c of a warp reads CTA c's partial, a shuffle
-    // tree adds them (the same tree, so the same bits, in every CTA)
+    // cluster-wide sums of the dot products in warp 0: lanes L and L + 16
+    // read CTA L mod 16's partials of the even and odd columns, and a
+    // transposed lane tree adds them (each level keeps half of a lane's
+    // values; the lane pairs are the xor 8, 4, 2, 1 tree of every value, the
+    // same in every CTA, so all CTAs get the same bits).  The pivot-row
+    // entries come straight from the CTA holding the pivot row (warp 1).
     {
       const int nv = w - lo;
-      for (int e = wp; e < 2 * nv; e += nw) {
-        const int f = (e < nv) ? lo + e : PB + lo + (e - nv);
-        double x = 0.0;
-        if (lane < cs) x = cluster.map_shared_rank(&s_slot[l & 1][0], lane)[f];
+      if (wp == 0) {
+        const int c = lane & 15, h = lane >> 4;
+        double v[8];
+        if (c < cs) {
+          const double* rem = cluster.map_shared_rank(&s_slot[l & 1][0], c);
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) s_tot[f] = x;
+          for (int i = 0; i < 8; ++i) v[i] = (2 * i + h < nv) ? rem[lo + 2 * i + h] : 0.0;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = 0.0;
+        }
+        bool up = (c & 8) != 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          v[i] = (up ? v[i + 4] : v[i]) + __shfl_xor_sync(0xffffffffu, up ? v[i] : v[i + 4], 8);
+        up = (c & 4) != 0;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+          v[i] = (up ? v[i + 2] : v[i]) + __shfl_xor_sync(0xffffffffu, up ? v[i] : v[i + 2], 4);
+        up = (c & 2) != 0;
+        v[0] = (up ? v[1] : v[0]) + __shfl_xor_sync(0xffffffffu, up ? v[0] : v[1], 2);
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+        const int e = 2 * (c >> 1) + h;  // the column this lane pair now holds
+        if ((c & 1) == 0 && e < nv) s_tot[lo + e] = v[0];
+      } else if (wp == 1) {
+        const int own = (int)((p - r0) / rpc);
+        if (lane < nv) s_tot[PB + lo + lane] = cluster.map_shared_rank(&s_slot[l & 1][0], own)[PB + lo + lane];
       }
     }
     __syncthreads();
     // the reflector's scalars in warp 0: beta from the norm, then the two
     // quotients htau = (beta - alpha) / beta and 1 / (alpha - beta) at once in
-    // lanes 0 and 1 (FP64 division is a long instruction sequence here)
+    // lanes 0 and 1 (FP64 division is a long instruction sequence here), then
+    // the coefficients of the columns it updates, lane t for column t
     const int lg = jb + l;  // column index within the whole panel
     if (wp == 0) {
       const double alpha = s_tot[PB + l];
@@ -1096,26 +1159,37 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
       const double num = (lane == 0) ? (beta - alpha) : 1.0;
       const double den = (lane == 0) ? beta : (alpha - beta);
       const double qv = num / den;
+      const double q0 = __shfl_sync(0xffffffffu, qv, 0);
       const double q1 = __shfl_sync(0xffffffffu, qv, 1);
+      const double ht = (s2 == 0.0) ? 0.0 : q0;    // htau (a zero tail: H = I)
+      const double rden = (s2 == 0.0) ? 0.0 : q1;  // 1 / (alpha - beta)
+      if (lane > l && lane < w) {
+        // v_i = x_i / (alpha - beta) below the pivot folded into the scale of x_l
+        const double hw = ht * (s_tot[PB + lane] + s_tot[lane] * rden);
+        s_hw[lane] = hw;
+        s_hwr[lane] = hw * rden;
+      }
       if (lane == 0) {
         const bool check = (lg >= 1) && !P.no_break && (P.check_last ? (lg < k) : (lg + 1 < k));
-        s_sc[4] = (check && nrm < eps_s) ? 1.0 : 0.0;
+        s_brk = (check && nrm < eps_s) ? 1 : 0;
+        s_app = (s2 == 0.0) ? 0 : 1;
         s_sc[0] = beta;
-        s_sc[1] = (s2 == 0.0) ? 0.0 : qv;  // htau (a zero tail: H = I)
-        s_sc[2] = (s2 == 0.0) ? 0.0 : q1;  // 1 / (alpha - beta)
+        s_sc[1] = ht;
+        s_sc[2] = rden;
       }
     }
     __syncthreads();
-    flops += 2.0 * (double)(m - p - 1) * (w - lo);
-    if (s_sc[4] != 0.0) {  // break test of Alg. 4 (identical in every CTA)
+    if (tid == 0) flops += 2 * (m - p - 1) * (int64_t)(w - lo);
+    if (s_brk) {  // break test of Alg. 4 (identical in every CTA)
       lacc = l;
       broke = true;
       break;
     }
-    const double beta = s_sc[0], ht = s_sc[1], rden = s_sc[2];
-    minb = fmin(minb, fabs(beta));
+    const double ht = s_sc[1], rden = s_sc[2];
     if (tid == 0) {
-      s_rden[l] = (ht != 0.0) ? rden : 1.0;  // v_l = x_l / (alpha - beta) below the pivot
+      const double beta = s_sc[0];
+      minb = fmin(minb, fabs(beta));
+      s_rden[l] = s_app ? rden : 1.0;  // v_l = x_l / (alpha - beta) below the pivot
       s_beta[l] = beta;
       if (crank == 0) P.htau[p] = ht;
     }
@@ -1132,14 +1206,13 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
       if (tid == 0) s_T[l][l] = ht;
     }
     // apply H_l to the rest of the sub-panel (own rows); x_l stays unscaled
-    if (ht != 0.0) {
+    if (s_app) {
       for (int t = l + 1 + wp; t < w; t += nw) {
-        const double hw = ht * (s_tot[PB + t] + s_tot[t] * rden);
-        const double hwr = hw * rden;  // v_i = x_i / (alpha - beta) folded into the scale
+        const double hw = s_hw[t], hwr = s_hwr[t];
         for (int64_t i = i0 + lane; i < re; i += 32) V.at(i, t) = fma(-hwr, V.at(i, l), V.at(i, t));
         if (own_p && lane == 0) V.at(p, t) -= hw;
       }
-      flops += 2.0 * (double)(m - p) * (w - l - 1);
+      if (tid == 0) flops += 2 * (m - p) * (int64_t)(w - l - 1);
     }
     __syncthreads();
   }
@@ -1172,7 +1245,7 @@ __device__ __forceinline__ void panel_body(Params& P, int j) {
       if (lacc > 0) st->pol_minb = fmin(st->pol_minb, minb);
       if (broke) st->pbreak = 1;
       if (P.trace && st->step < P.trace_cap) P.trace[st->step].l = st->l;
-      add_flops(st, KID_PANEL, flops);
+      add_flops(st, KID_PANEL, (double)flops);
     }
   }
 }
@@ -1936,43 +2009,46 @@ __device__ __forceinline__ bool grid_barrier(DevState* st, unsigned int target, 
 
 __device__ __forceinline__ void qrp_block_argmax(const double* u, int64_t ns, int64_t n, double* s_v, int64_t* s_p,
                                                  double* mu_out, int64_t* j_out) {
+  // integer keys of the non-negative partial norms (the compares stay off the FP64 pipe);
+  // s_v holds the keys' bit patterns
+  long long* s_k = reinterpret_cast<long long*>(s_v);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  double bv = -1.0;
+  long long bk = -1;
   int64_t bp = INT64_MAX;
   for (int64_t j = ns + tid; j < n; j += QRP_THREADS) {
-    const double x = u[j];
-    if (better(x, j, bv, bp)) {
-      bv = x;
+    const long long x = ukey(u[j]);
+    if (kbetter_u(x, j, bk, bp)) {
+      bk = x;
       bp = j;
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
     const int64_t op = __shfl_xor_sync(0xffffffffu, bp, o);
-    if (better(ov, op, bv, bp)) {
-      bv = ov;
+    if (kbetter_u(ok, op, bk, bp)) {
+      bk = ok;
       bp = op;
     }
   }
   if (lane == 0) {
-    s_v[w] = bv;
+    s_k[w] = bk;
     s_p[w] = bp;
   }
   __syncthreads();
   if (tid == 0) {
-    bv = s_v[0];
+    bk = s_k[0];
     bp = s_p[0];
     for (int q = 1; q < QRP_THREADS / 32; ++q)
-      if (better(s_v[q], s_p[q], bv, bp)) {
-        bv = s_v[q];
+      if (kbetter_u(s_k[q], s_p[q], bk, bp)) {
+        bk = s_k[q];
         bp = s_p[q];
       }
-    s_v[QRP_THREADS / 32] = bv;
+    s_k[QRP_THREADS / 32] = bk;
     s_p[QRP_THREADS / 32] = bp;
   }
   __syncthreads();
-  *mu_out = s_v[QRP_THREADS / 32];
+  *mu_out = __longlong_as_double(s_k[QRP_THREADS / 32]);
   *j_out = s_p[QRP_THREADS / 32];
   __syncthreads();
 }
