@@ -820,7 +820,8 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
 
   // Single-column steps (DM off, or k_max = 1) run fused in one cooperative
   // kernel when the pivot column fits in shared memory.
-  const bool qrp_fused = cfg.qrp_grid > 0 && (int64_t)m * (int64_t)sizeof(double) <= QRP_SMEM_MAX;
+  const bool qrp_fused = cfg.qrp_grid > 0 && (int64_t)m * (int64_t)sizeof(double) <= QRP_SMEM_MAX &&
+                         n <= (int64_t)QRP_OWN_MAX * cfg.qrp_grid;
   auto launch_qrp = [&]() -> cudaError_t {
     void* args[] = {(void*)&P};
     const size_t smem = (size_t)m * sizeof(double);

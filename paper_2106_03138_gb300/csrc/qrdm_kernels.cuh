@@ -1979,6 +1979,7 @@ __global__ void __launch_bounds__(256) k_downdate(Params P) {
 // per step: after all CTAs have read the pivot column, and after all updates.
 // ---------------------------------------------------------------------------
 constexpr int QRP_THREADS = 256;
+constexpr int QRP_OWN_MAX = 512;  // trailing columns one CTA of the single-column kernel owns, at most
 
 // Grid-wide barrier for a cooperative launch: arrival counter with release,
 // polling with acquire, bounded by limit_ns of the global timer.  Returns
@@ -2053,13 +2054,15 @@ __device__ __forceinline__ void qrp_block_argmax(const double* u, int64_t ns, in
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(QRP_THREADS) k_qrp_tail(Params P) {
+__global__ void __launch_bounds__(QRP_THREADS, 1) k_qrp_tail(Params P) {
   DevState* st = P.st;
   extern __shared__ double s_x[];  // pivot column rows ns..m-1
   __shared__ double s_v[QRP_THREADS / 32 + 1];
   __shared__ int64_t s_p[QRP_THREADS / 32 + 1];
   __shared__ double s_sc[8];
   __shared__ double s_red[QRP_THREADS / 32];
+  __shared__ double s_rr[QRP_OWN_MAX];  // the updated row-ns entries of this CTA's columns
+  __shared__ int s_rrec[QRP_OWN_MAX];   // 1: the column's norm is recomputed exactly
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const int G = (int)gridDim.x, cta = (int)blockIdx.x;
   const int64_t m = P.m, n = P.n, lda = P.lda, kmin = P.kmin;
@@ -2125,6 +2128,11 @@ __global__ void __launch_bounds__(QRP_THREADS) k_qrp_tail(Params P) {
     }
     __syncthreads();
     const double beta = s_sc[0], ht = s_sc[1], rden = s_sc[2];
+    const bool app = ht != 0.0;
+    // v = x / (alpha - beta) below the pivot, formed once per CTA in shared
+    // memory: the owner writes it back, every CTA's updates use it
+    if (app)
+      for (int64_t i = 1 + tid; i < mr; i += QRP_THREADS) s_x[i] *= rden;
     bar += G;
     if (!grid_barrier(st, bar, step, ns, P.wait_ns)) break;  // all CTAs have read column jstar
     // the owner of position jstar moves the columns: ns <- pivot (R part, beta,
@@ -2141,7 +2149,7 @@ __global__ void __launch_bounds__(QRP_THREADS) k_qrp_tail(Params P) {
         for (int64_t i = ns + tid; i < m; i += QRP_THREADS) cj[i] = cn[i];
       }
       __syncthreads();
-      for (int64_t i = ns + 1 + tid; i < m; i += QRP_THREADS) cn[i] = (ht != 0.0) ? s_x[i - ns] * rden : s_x[i - ns];
+      for (int64_t i = ns + 1 + tid; i < m; i += QRP_THREADS) cn[i] = s_x[i - ns];
       if (tid == 0) {
         cn[ns] = beta;
         if (jstar != ns) {
@@ -2176,49 +2184,64 @@ __global__ void __launch_bounds__(QRP_THREADS) k_qrp_tail(Params P) {
       }
       __syncthreads();
     }
-    // every CTA: apply H to its trailing positions (one warp per column) and
-    // update the partial norm (block downdate with recomputation, l = 1)
+    // every CTA: apply H to its trailing positions (one warp per column),
+    // then the partial norms of all of them at once (block downdate with
+    // recomputation, l = 1: one thread per column for the scalar part, so its
+    // divisions and square root issue once per 32 columns, then one warp per
+    // column that needs the exact norm)
     int nrec = 0;
     {
-      // first position > ns owned by this CTA
-      int64_t c = ns + 1 + ((cta - (int)((ns + 1) % G)) % G + G) % G;
-      c += (int64_t)wp * G;
-      for (; c < n; c += (int64_t)G * (QRP_THREADS / 32)) {
-        double* ac = A + c * lda;
-        double wsum = 0.0;
-        if (ht != 0.0) {
-          for (int64_t i = ns + 1 + lane; i < m; i += 32) wsum = fma(s_x[i - ns] * rden, ac[i], wsum);
+      // first position > ns owned by this CTA, and how many it owns
+      const int64_t c_first = ns + 1 + ((cta - (int)((ns + 1) % G)) % G + G) % G;
+      const int nown = (c_first < n) ? (int)((n - 1 - c_first) / G + 1) : 0;
+      for (int q = wp; q < nown; q += QRP_THREADS / 32) {
+        double* ac = A + (c_first + (int64_t)q * G) * lda;
+        if (app) {
+          double wsum = 0.0;
+          for (int64_t i = ns + 1 + lane; i < m; i += 32) wsum = fma(s_x[i - ns], ac[i], wsum);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
           wsum += ac[ns];
-          const double hw = ht * wsum, hwr = hw * rden;
-          for (int64_t i = ns + 1 + lane; i < m; i += 32) ac[i] = fma(-hwr, s_x[i - ns], ac[i]);
+          const double hw = ht * wsum;
+          for (int64_t i = ns + 1 + lane; i < m; i += 32) ac[i] = fma(-hw, s_x[i - ns], ac[i]);
           __syncwarp();
           if (lane == 0) ac[ns] -= hw;
-          __syncwarp();
         }
+        if (lane == 0) s_rr[q] = ac[ns];
+        __syncwarp();
+      }
+      __syncthreads();
+      for (int q = tid; q < nown; q += QRP_THREADS) {
+        const int64_t c = c_first + (int64_t)q * G;
         const double uc = P.u[c];
+        int rec = 0;
         if (uc != 0.0) {
-          const double x = ac[ns] / uc;
+          const double x = s_rr[q] / uc;
           double t = 1.0 - x * x;
           if (t < 0.0) t = 0.0;
           const double ratio = uc / P.uref[c];
-          if (t * ratio * ratio <= sqeps) {
-            double s = 0.0;
-            for (int64_t i = ns + 1 + lane; i < m; i += 32) s = fma(ac[i], ac[i], s);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) {
-              const double nr = sqrt(s);
-              P.u[c] = nr;
-              P.uref[c] = nr;
-              ++nrec;
-            }
-          } else if (lane == 0) {
+          if (t * ratio * ratio <= sqeps)
+            rec = 1;
+          else
             P.u[c] = uc * sqrt(t);
-          }
         }
-        __syncwarp();
+        s_rrec[q] = rec;
+      }
+      __syncthreads();
+      for (int q = wp; q < nown; q += QRP_THREADS / 32) {
+        if (!s_rrec[q]) continue;
+        const int64_t c = c_first + (int64_t)q * G;
+        const double* ac = A + c * lda;
+        double sq = 0.0;
+        for (int64_t i = ns + 1 + lane; i < m; i += 32) sq = fma(ac[i], ac[i], sq);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) {
+          const double nr = sqrt(sq);
+          P.u[c] = nr;
+          P.uref[c] = nr;
+          ++nrec;
+        }
       }
     }
     if (lane == 0 && nrec && P.trace && step < P.trace_cap)

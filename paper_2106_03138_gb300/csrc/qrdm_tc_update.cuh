@@ -710,13 +710,23 @@ __global__ void __launch_bounds__(TcwTma<FMT>::THREADS, 1)
           break;
         }
         const unsigned char* src = ring + f * G::BOX;
+        // the box into registers first, so the ring gets it back before the conversion
+        constexpr int NPC = G::BOXR / 16;  // 16-byte pieces per lane and column
+        double2 dd_all[TCW_COLS / 32][NPC];
+#pragma unroll
+        for (int u = 0; u < TCW_COLS / 32; ++u)
+#pragma unroll
+          for (int e = 0; e < NPC; ++e)
+            dd_all[u][e] = *reinterpret_cast<const double2*>(src + (size_t)(cq + 32 * u) * (G::BOXR * 8) + (e * 8 + j) * 16);
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&b_free[f]);  // the box's reads are done
 #pragma unroll
         for (int u = 0; u < TCW_COLS / 32; ++u) {
           const int c = cq + 32 * u;
 #pragma unroll
-          for (int e = 0; e < G::BOXR / 16; ++e) {
+          for (int e = 0; e < NPC; ++e) {
             const int h = e * 8 + j;  // 16-byte piece: rows 2h, 2h + 1 of the box, column c
-            const double2 dd = *reinterpret_cast<const double2*>(src + (size_t)c * (G::BOXR * 8) + h * 16);
+            const double2 dd = dd_all[u][e];
             const float x0 = f64_to_f32_rn(dd.x), x1 = f64_to_f32_rn(dd.y);
             const uint32_t off = tc::sw128_off_e<ESZ>(c, b * G::BOXR + 2 * h);
             if (FMT == 1) {
@@ -737,8 +747,6 @@ __global__ void __launch_bounds__(TcwTma<FMT>::THREADS, 1)
             }
           }
         }
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&b_free[f]);  // the box's reads are done
       }
       if (!ok) break;
       tc::fence_proxy_async_smem();  // the split tile is read by the tensor core
