@@ -581,7 +581,7 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   if (perm_grid > (unsigned)(4 * sms)) perm_grid = 4 * sms;
   unsigned dd_grid = (unsigned)((n + 7) / 8);
   if (dd_grid > (unsigned)(8 * sms)) dd_grid = 8 * sms;
-  const unsigned gred_grid = (unsigned)((k_max * (k_max + 1) / 2 + 255) / 256);
+  const unsigned gred_grid = (unsigned)((k_max * (k_max + 1) / 2 + GRED_ENTRIES - 1) / GRED_ENTRIES);
 
   cudaLaunchConfig_t pc = {};
   cudaLaunchAttribute pat[1];
@@ -605,7 +605,7 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
   // events for profiling: two pools (the previous batch is read while the
   // next one runs), each with a start/end pair per launch
   constexpr int MAX_BATCH = 16;
-  const int per_step = 12 + 5 * nsub_full;  // select..permute, 5 per sub-panel, 5 merged, downdate, step end
+  const int per_step = 12 + 6 * nsub_full;  // select..permute, 5-6 per sub-panel, 5 merged, downdate, step end
   const int pool = MAX_BATCH * per_step;
   if (prof && (int)g_events.size() < 2 * 2 * pool) {
     while ((int)g_events.size() < 2 * 2 * pool) {
@@ -718,6 +718,9 @@ int factor_impl(double* dA, int64_t m, int64_t n, int64_t lda, double tau, doubl
              else
                k_trail_w<<<gemm_grid, GEMM_THREADS, TRAIL_W_SMEM, stream>>>(P, j);
            })) != cudaSuccess)
+        return e;
+      if (merged && (e = run(QRDM_K_TRAIL_WREDUCE, [&] { k_trail_wpresum<<<sms, 256, 0, stream>>>(P, j); })) !=
+                        cudaSuccess)
         return e;
       if ((e = run(QRDM_K_TRAIL_WREDUCE, [&] { k_trail_wreduce<<<sms, GEMM_THREADS, 0, stream>>>(P, j); })) !=
           cudaSuccess)

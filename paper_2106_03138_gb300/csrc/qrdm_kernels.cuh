@@ -702,6 +702,11 @@ __global__ void __launch_bounds__(256) k_gram(Params P) { gram_body<double>(P); 
 // mixed-precision form: the candidate Gram matrix in FP32, partials summed in FP64
 __global__ void __launch_bounds__(256) k_gram32(Params P) { gram_body<float>(P); }
 
+// G = sum of the Gram kernel's partials: 8 threads per entry each add a
+// contiguous eighth of the partials (in order), then the eight sums are added
+// in order, so the result is fixed while eight times as many loads are in
+// flight (the partials sit in L2)
+constexpr int GRED_ENTRIES = 32;  // entries per CTA of k_gram_reduce (256 threads)
 __global__ void __launch_bounds__(256) k_gram_reduce(Params P) {
   const DevState* st = P.st;
   if (st->done) return;
@@ -711,8 +716,21 @@ __global__ void __launch_bounds__(256) k_gram_reduce(Params P) {
   const int64_t mr = P.m - st->ns;
   const int64_t nchunks = (mr + P.gram_rows - 1) / P.gram_rows;  // the Gram kernel's row chunks
   const int nparts = (int)min((int64_t)P.gram_chunks, nchunks);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < npairs; e += gridDim.x * blockDim.x) {
-    P.G[e] = sum_strided(P.Gp + e, (int64_t)P.kmax * P.kmax, nparts);
+  __shared__ double s_part[GRED_ENTRIES][9];
+  const int le = threadIdx.x >> 3, h = threadIdx.x & 7;
+  const int per = (nparts + 7) / 8;
+  for (int e0 = blockIdx.x * GRED_ENTRIES; e0 < npairs; e0 += gridDim.x * GRED_ENTRIES) {
+    const int e = e0 + le;
+    const int c0 = h * per, c1 = min(nparts, c0 + per);
+    const int64_t stride = (int64_t)P.kmax * P.kmax;
+    s_part[le][h] = (e < npairs && c1 > c0) ? sum_strided(P.Gp + (int64_t)c0 * stride + e, stride, c1 - c0) : 0.0;
+    __syncthreads();
+    if (h == 0 && e < npairs) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += s_part[le][q];
+      P.G[e] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -1325,6 +1343,7 @@ struct WGeom {
   int cols;
   // partial W of row chunk q, reflector t, column c at Wp[q qstride + t tstride + c - cofs]
   int64_t qstride, tstride, cofs;
+  bool narrow;  // the packed 64-column layout of a merged form's panel columns
 };
 
 // Columns of a sub-panel's W pass (j >= 0, every form but the FP32-class
@@ -1357,6 +1376,7 @@ __device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int6
   g.qstride = (int64_t)P.kmax * P.n;
   g.tstride = P.n;
   g.cofs = 0;
+  g.narrow = false;
   if (P.mixed) {
     g.cols = 0;
     g.nct = 0;
@@ -1373,6 +1393,7 @@ __device__ __forceinline__ WGeom w_geom(const Params& P, int l, int64_t n2, int6
     g.qstride = (int64_t)P.kmax * NARROW_COLS;
     g.tstride = NARROW_COLS;
     g.cofs = narrow_c0;
+    g.narrow = true;
   }
   g.rows_per = wchunk_rows(mr, g.nct, cap, P.w_units);
   g.nrc = (mr + g.rows_per - 1) / g.rows_per;
@@ -1535,6 +1556,48 @@ __device__ __forceinline__ void trail_w_kernel(Params& P, int j) {
 
 __global__ void __launch_bounds__(GEMM_THREADS) k_trail_w(Params P, int j) { trail_w_kernel<double>(P, j); }
 
+// The narrow sub-panel updates of the merged forms split their W pass into
+// up to NARROW_WCHUNKS row chunks (so that every SM works on a 64-column
+// span): their partials are first summed into chunk 0 by many CTAs, 8
+// threads per entry each adding a contiguous eighth of the chunks in order,
+// then the eight sums in order (a fixed result), and k_trail_wreduce reads
+// one chunk.  Entry (t, pc): reflector t, packed column pc of the span.
+constexpr int WPRE_MIN_CHUNKS = 24;  // fewer row chunks are summed by k_trail_wreduce itself
+__device__ __forceinline__ bool wpre_used(const Params& P, const WGeom& g, int j) {
+  return P.merged && j >= 0 && g.narrow && g.nrc >= WPRE_MIN_CHUNKS;
+}
+
+__global__ void __launch_bounds__(256) k_trail_wpresum(Params P, int j) {
+  DevState* st = P.st;
+  if (st->done) return;
+  const SubGeom sg = sub_geom(st, j);
+  const int l = sg.l;
+  const int64_t cend = trail_end(P, st, j);
+  const int64_t n2 = cend - sg.c0, mr = P.m - sg.r0;
+  if (l <= 0 || n2 <= 0 || mr <= 0) return;
+  const WGeom g = w_geom(P, l, l + n2, mr, sg.r0, cend - sg.r0);
+  if (!wpre_used(P, g, j)) return;
+  const int64_t span = cend - sg.r0;
+  const int64_t nent = (int64_t)l * span;
+  __shared__ double s_part[32][9];
+  const int le = threadIdx.x >> 3, h = threadIdx.x & 7;
+  const int64_t per = (g.nrc + 7) / 8;
+  for (int64_t e0 = (int64_t)blockIdx.x * 32; e0 < nent; e0 += (int64_t)gridDim.x * 32) {
+    const int64_t e = e0 + le;
+    const int64_t t = e / span, pc = e % span;
+    const int64_t c0 = h * per, c1 = min(g.nrc, c0 + per);
+    double* base = P.Wp + t * g.tstride + pc;
+    s_part[le][h] = (e < nent && c1 > c0) ? sum_strided(base + c0 * g.qstride, g.qstride, c1 - c0) : 0.0;
+    __syncthreads();
+    if (h == 0 && e < nent) {
+      double v = 0.0;
+      for (int q = 0; q < 8; ++q) v += s_part[le][q];
+      base[0] = v;  // chunk 0
+    }
+    __syncthreads();
+  }
+}
+
 // W = T^T sum(partials), the partials of k_trail_w's row chunks.  For a
 // sub-panel (j >= 0, every form but the FP32-class one) T is not formed:
 // with S = V^T V from the W pass, T^-1 = strict_upper(S) + diag(1/htau)
@@ -1556,7 +1619,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_trail_wreduce(Params P, int j)
   const int64_t nct = (n2 + TW_COLS - 1) / TW_COLS;
   // the row chunks of k_trail_w (k_trail_w32 in the FP32-class form)
   const WGeom g = w_geom(P, l, nsx + n2, mr, (P.merged && j >= 0) ? sg.r0 : -1, cend - sg.r0);
-  const int64_t nrc = g.nrc;
+  const int64_t nrc = wpre_used(P, g, j) ? 1 : g.nrc;  // k_trail_wpresum summed them into chunk 0
   if (blockIdx.x == 0 && threadIdx.x == 0)
     add_flops(st, KID_TRAIL_WREDUCE, (double)n2 * l * ((double)(nrc - 1) + (l + 1.0)));
   __shared__ double s_w[KMAX][TW_COLS + 1];
