@@ -264,14 +264,10 @@ struct ArgMax {
   double v;
   int64_t p;
 };
-__device__ __forceinline__ bool better(double va, int64_t pa, double vb, int64_t pb) {
-  // larger value first, ties to the lower position
-  return va > vb || (va == vb && pa < pb);
-}
-
 // The partial norms are non-negative, and non-negative doubles order like
 // their bit patterns read as int64: the selection compares keys on the
-// integer pipe (a warp-wide FP64 compare takes the FP64 pipe as long as an FMA)
+// integer pipe (a warp-wide FP64 compare takes the FP64 pipe as long as an
+// FMA).  Larger value first, ties to the lower position.
 __device__ __forceinline__ long long ukey(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ bool kbetter_u(long long ka, int64_t pa, long long kb, int64_t pb) {
   return ka > kb || (ka == kb && pa < pb);
