@@ -60,7 +60,7 @@ extern "C" {
 #define QRDM_K_PERMUTE 5       /* a6: column moves */
 #define QRDM_K_PANEL 6         /* a7/a8: Householder panel with break test, T */
 #define QRDM_K_TRAIL_W 7       /* a9: W = V^T A22 (partial) */
-#define QRDM_K_TRAIL_WREDUCE 8 /* a9: W = T^T sum(partials) */
+#define QRDM_K_TRAIL_WREDUCE 8 /* a9: W = T^T sum(partials) (with the pre-sum of many row chunks) */
 #define QRDM_K_TRAIL_UPDATE 9  /* a9: A22 -= V W */
 #define QRDM_K_DOWNDATE 10     /* a10: partial norm update */
 #define QRDM_K_STEP_END 11     /* a11: n_s += l */
