@@ -231,6 +231,37 @@ def test_rank_gap_matrix():
     assert d[:128].min() > 1e-3 and d[128:].max() < 1e-12
 
 
+def criterion_diagonal() -> np.ndarray:
+    """100 x 100 diagonal: 50 unit columns, then 50 of norm eta = 20 eps.
+    Every reflector is the identity (zero tails), every downdate exact, and
+    anorm = 1, eps1 = 100 eps exactly."""
+    d = np.ones(100)
+    d[50:] = 20.0 * EPS
+    return np.asfortranarray(np.diag(d))
+
+
+def test_rank_criterion_and_dm_safeguard_on_an_exact_diagonal():
+    """The paper's stopping test sqrt(n - n_s) mu <= eps n max||a_i|| (Sec.
+    3.4), taken at block starts, and the DM safeguard of Sec. 4 (reading R12:
+    once the test holds, single-column steps finish).  With k_max = 8 the
+    blocks start at 0, 8, ..., 40, 48 (the last unit pair), 50, 58, 66, 74, 82.
+    At n_s = 50 the column maximum eta = 20 eps is already below 100 eps
+    (rank_colmax = 50), but sqrt(50) eta = 141 eps is not; sqrt(26) eta =
+    102 eps at n_s = 74 is not either; sqrt(18) eta = 85 eps at n_s = 82 is,
+    so rank = 82, and the 18 columns left go one per step with DM off."""
+    A = criterion_diagonal()
+    r = O.qrdm(A, 0.9, 0.9, 8)
+    assert r["rank_colmax"] == 50
+    assert r["rank"] == 82
+    tr = r["trace"]
+    ns, k, dm = tr["ns"], tr["k"], tr["dm_on"]
+    assert list(ns[:12]) == [0, 8, 16, 24, 32, 40, 48, 50, 58, 66, 74, 82]
+    assert list(k[:11]) == [8, 8, 8, 8, 8, 8, 2, 8, 8, 8, 8]
+    assert np.all(dm[:11] == 1)
+    assert len(tr) == 11 + 18 and np.all(k[11:] == 1) and np.all(dm[11:] == 0)
+    assert np.array_equal(r["perm"], np.arange(100))
+
+
 def test_rank_exact_integer_matrices():
     for c in golden("exact_rank.json")["cases"]:
         A = np.asfortranarray(np.array(c["columns"]).T)
