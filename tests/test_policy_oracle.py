@@ -100,6 +100,33 @@ def test_step_features_by_hand():
     assert (f[13], f[14], f[15]) == (0.2, 0.7, 0.15)
 
 
+def test_step_feature_counts_at_their_thresholds():
+    """The candidate-count features count u >= t mu with t the FP32 value of
+    each threshold (the kernel compares against FP32 constants): a norm equal
+    to float32(t) mu is counted; the double t itself is no threshold
+    (float32(0.95) < 0.95, float32(0.15) > 0.15 ...), and equality counts."""
+    mu = 1.0
+    ts32 = [float(np.float32(t)) for t in M.THRESH]
+    # one norm sitting exactly on each FP32 threshold, plus the argmax
+    u = np.array([mu] + ts32)
+    f = M.step_features(u, ns=0, jstar=0, anorm=1.0, prev_l=0, prev_k=0, cos_mean=0.0, cos_max=0.0, prev_tau=0.0)
+    # threshold b counts the norms >= ts32[b]: those of thresholds 0..b
+    assert list(np.round(f[:8] * 128).astype(int)) == list(range(1, 9))
+    # a norm just below float32(0.95) mu is not counted at 0.95
+    u2 = np.array([mu, float(np.nextafter(np.float64(ts32[0]), 0.0))])
+    f2 = M.step_features(u2, ns=0, jstar=0, anorm=1.0, prev_l=0, prev_k=0, cos_mean=0.0, cos_max=0.0, prev_tau=0.0)
+    assert f2[0] == 0.0 and f2[1] == 1 / 128
+
+
+def test_outputs_map_to_tau_then_delta():
+    """Output 0 of the MLP is tau and output 1 is delta, each mapped
+    linearly onto its range (0 -> lower end, 1 -> upper end)."""
+    t, d = M.to_tau_delta(np.array([1.0, 0.0]), 0.5, 1.0, 0.3, 0.9)
+    assert (t, d) == (1.0, 0.3)
+    t, d = M.to_tau_delta(np.array([0.25, 0.5]), 0.2, 1.0, 0.4, 1.0)
+    assert t == pytest.approx(0.4) and d == pytest.approx(0.7)
+
+
 def test_constant_schedule_reproduces_the_plain_oracle_bit_for_bit():
     A = inputs.from_spectrum(120, 90, inputs.sigma_geometric(90, 1e-12), 3)
     plain = O.qrdm(A, 0.3, 0.8, 16)
