@@ -53,6 +53,15 @@
  *   v = x / (alpha - beta), v_0 = 1; a zero tail gives htau = 0, beta = alpha.
  *
  * Compiled with -O2 -ffp-contract=off: every operation rounds once.
+ *
+ * PINS (tests/test_oracle_pins.py): closed-form reflectors and T, exact
+ * hand-derived DM decisions and equality edges, brute-force column pivoting
+ * at k_max = 1, A Pi = Q R to roundoff, exact ranks, the stopping test and
+ * the DM safeguard on an exact diagonal, the paper's SDD lemmas and
+ * worst-case theorems, exhaustive subset search.  Parity unpinned: the
+ * permutation on Kahan matrices, whose columns all have unit norm in exact
+ * arithmetic, so that every pivot decision there is a rounding tie; those
+ * runs are checked through invariants only.
  */
 #include <math.h>
 #include <stdint.h>
