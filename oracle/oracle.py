@@ -181,7 +181,9 @@ def qrdm(A: np.ndarray, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *
     ``A`` (R above the diagonal, reflector tails below), ``htau``, ``perm``,
     ``rank``, ``rank_colmax``, ``u``/``uref`` (partial norms at exit),
     ``trace`` (one record per block step, STEP_DTYPE), ``J`` (per step, the
-    original indices of the selected columns, -1 padded), ``status``.
+    original indices of the selected columns, -1 padded), ``status``, and
+    ``stop``: with ``stop_at_rank``, the record of the stopping test that
+    ended the run (its margin ``s_stop``; ``k`` = -1), else None.
     """
     lib = _load()
     if parallel:
@@ -228,6 +230,8 @@ def qrdm(A: np.ndarray, tau: float = 0.9, delta: float = 0.9, k_max: int = 32, *
         "u": u[:n],
         "uref": uref[:n],
         "trace": trace[:min(ns, cap)],
+        # the stopping test's record when the stop at the rank ended the run
+        "stop": trace[ns].copy() if (ns < cap and int(trace[ns]["k"]) == -1) else None,
         "J": J[:min(ns, cap)],
         "nsteps": ns,
     }

@@ -198,7 +198,9 @@ static int cmp_desc(double ua, int64_t pa, double ub, int64_t pb) {
  * Outputs: rank (criterion eq. practical stopping criterion), rank_colmax
  *   (the same test without the sqrt(n - n_s) factor), u_out/uref_out (n, may
  *   be NULL), trace (trace_cap records, may be NULL), Jout (trace_cap*k_max
- *   original column indices of J per step), nsteps.
+ *   original column indices of J per step), nsteps.  With stop_at_rank, a
+ *   stop by the criterion also writes the stopping test's record (k = -1)
+ *   at trace[nsteps] when trace_cap > nsteps.
  * Returns 0, or -i for an invalid i-th argument, or 1 for non-finite input.
  */
 int oq_qrdm_sched(int64_t m, int64_t n, double* A, int64_t lda, double tau, double delta, int64_t kmax,
@@ -300,7 +302,15 @@ int oq_qrdm_sched(int64_t m, int64_t n, double* A, int64_t lda, double tau, doub
       if (*rank_out < 0 && lhs <= rhs) {
         *rank_out = ns;
         dm_on = 0;
-        if (stop_at_rank) break;
+        if (stop_at_rank) {
+          /* the stopping test's own record (its margin s_stop), k = -1, kept
+             past the nsteps executed steps */
+          rec.k = -1;
+          rec.mu = mu;
+          rec.jstar = jstar;
+          if (trace && step < trace_cap) trace[step] = rec;
+          break;
+        }
       }
     }
     rec.dm_on = dm_on;

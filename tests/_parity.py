@@ -54,10 +54,17 @@ def walk(gtrace, gJ, otrace, oJ):
     return None, None
 
 
-def is_tie(otrace, s) -> tuple[bool, float]:
+def is_tie(otrace, s, ostop=None) -> tuple[bool, float]:
+    """Whether the oracle's step s was decided within its rounding margin.
+    Past its last step, the oracle either ran out of columns (no tie: the
+    other side cannot go on) or stopped at the rank, where the margin is that
+    of its stopping test (``ostop``, the oracle's record of it)."""
     if s >= len(otrace):
-        return True, 0.0  # the oracle stopped (criterion) where the GPU went on: stop test
-    rec = otrace[s]
+        if ostop is None:
+            return False, np.inf
+        rec = ostop
+    else:
+        rec = otrace[s]
     score = min(float(rec[f]) for f in SCORES)
     # an earlier near-tie in the recompute test changes u by its uncertainty
     prev = min([float(r["s_recomp"]) for r in otrace[: s + 1]] + [np.inf])
@@ -83,7 +90,7 @@ def compare(A: np.ndarray, g: dict, o: dict) -> dict:
     div, ncols = walk(g["trace"], g["J"], o["trace"], o["J"])
     report = {"diverged_at": div, "tie_score": None}
     if div is not None:
-        tie, score = is_tie(o["trace"], div)
+        tie, score = is_tie(o["trace"], div, o.get("stop"))
         report["tie_score"] = score
         assert tie, f"GPU and oracle take different decisions at step {div} with no tie (score {score:.3g})"
         ncmp = ncols
@@ -96,17 +103,21 @@ def compare(A: np.ndarray, g: dict, o: dict) -> dict:
     report.update(compare_rows(A, g, o, ncmp))
     # rank_colmax (mu <= eps1 anorm, no sqrt factor) changes no decision, so it
     # is not in the trace walk; it may differ only where the oracle's mu at
-    # that step lay within the roundoff band sqrt(mn) eps anorm of the threshold
+    # that step lay within the roundoff band sqrt(mn) eps anorm of the
+    # threshold.  Inside the compared columns both sides started the same
+    # steps, so a value there must be one of those step starts.
     rc_g, rc_o = g["rank_colmax"], o["rank_colmax"]
     if rc_g != rc_o and min(rc_g, rc_o) < ncmp:
         eps1 = EPS * n
         band = np.sqrt(float(m) * n) * EPS * anorm
         tr = o["trace"]
         for rc in (rc_g, rc_o):
+            if rc >= ncmp:
+                continue
             hit = np.nonzero(tr["ns"] == rc)[0]
-            if hit.size:
-                mu = float(tr["mu"][hit[0]])
-                assert abs(mu - eps1 * anorm) <= band, f"rank_colmax {rc_g} vs {rc_o} without a tie"
+            assert hit.size, f"rank_colmax {rc} is not the start of a block step"
+            mu = float(tr["mu"][hit[0]])
+            assert abs(mu - eps1 * anorm) <= band, f"rank_colmax {rc_g} vs {rc_o} without a tie"
     return report
 
 

@@ -260,6 +260,15 @@ def test_rank_criterion_and_dm_safeguard_on_an_exact_diagonal():
     assert np.all(dm[:11] == 1)
     assert len(tr) == 11 + 18 and np.all(k[11:] == 1) and np.all(dm[11:] == 0)
     assert np.array_equal(r["perm"], np.arange(100))
+    assert r["stop"] is None
+    # stopping at the rank: 11 steps, then the stopping test's own record at
+    # n_s = 82 with mu = eta exactly
+    s = O.qrdm(A, 0.9, 0.9, 8, stop_at_rank=True)
+    assert s["rank"] == 82 and len(s["trace"]) == 11
+    assert np.array_equal(s["trace"], tr[:11])
+    st = s["stop"]
+    assert int(st["k"]) == -1 and int(st["ns"]) == 82 and float(st["mu"]) == 20.0 * EPS
+    assert np.all(s["A"][82:, 82:] == A[82:, 82:]) and np.all(s["htau"][82:] == 0.0)
 
 
 def test_rank_exact_integer_matrices():

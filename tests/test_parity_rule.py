@@ -1,0 +1,182 @@
+"""The GPU-vs-oracle comparison rule (tests/_parity.py), checked on the CPU.
+
+The GPU parity tests are only as strong as ``compare``.  Here the oracle's
+own output plays the GPU's part: ``compare`` must accept it unchanged, accept
+it moved by half of every rounding bound, and accept a divergence at an exact
+tie; and it must reject each planted mistake that a wrong kernel could make
+(an R entry, a diagonal, a reflector or an htau beyond its bound, a swapped
+permutation, a different pick, block size or step count with no tie, a wrong
+rank, a missed stop at the rank)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_03138_gb300 import inputs
+from tests._parity import compare, rdiag_tol, row_err
+
+M, N = 300, 200
+
+
+def _matrix():
+    """300 x 200 with a rank-100 gap: live rows 0..99, rounding noise after."""
+    return inputs.from_spectrum(M, N, inputs.sigma_gap(N, N // 2), 11)
+
+
+def _copy(o):
+    return {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in o.items()}
+
+
+@pytest.fixture(scope="module")
+def case():
+    A = _matrix()
+    return A, O.qrdm(A, 0.5, 0.9, 16)
+
+
+def _perturbed(A, o, frac, seed=0):
+    """The oracle's output moved by frac of each bound of the rule, random signs."""
+    rng = np.random.default_rng(seed)
+    g = _copy(o)
+    p = min(M, N)
+    anorm = float(np.max(np.linalg.norm(A, axis=0)))
+    e = row_err(M, p, anorm)
+    d = np.abs(np.diag(o["A"])[:p])
+    i0 = int(np.nonzero(d < 4.0 * e)[0][0])
+    R = np.triu(o["A"][:p, :])
+    sgn = rng.choice([-1.0, 1.0], size=R.shape)
+    g["A"][:p, :] += np.triu(frac * sgn * (1e-11 * np.abs(R) + e[:, None]), 1)
+    dt = np.minimum(rdiag_tol(d, anorm, M), 1e-11 * d + e)
+    g["A"][np.arange(p), np.arange(p)] += frac * np.sign(np.diag(R)) * sgn[0, :p] * dt
+    for i in range(i0):
+        tail = rng.choice([-1.0, 1.0], size=M - i - 1)
+        g["A"][i + 1:, i] += frac * tail * (3.0 * e[i] / d[i])
+        g["htau"][i] += frac * rng.choice([-1.0, 1.0]) * (2.0 * e[i] / d[i])
+    return g, e, d, i0
+
+
+def test_accepts_the_oracle_unchanged(case):
+    A, o = case
+    rep = compare(A, _copy(o), o)
+    assert rep["diverged_at"] is None and rep["ncmp"] == N
+    assert rep["r_max_err_over_bound"] == 0.0
+    assert rep["noise_onset_row"] == N // 2  # both regimes of the rule are exercised
+
+
+def test_accepts_changes_within_half_of_every_bound(case):
+    A, o = case
+    for seed in range(3):
+        g, _, _, _ = _perturbed(A, o, 0.5, seed)
+        rep = compare(A, g, o)
+        # (adding a step of 1e-11 |R| rounds it by up to 2e-5 of itself)
+        assert 0.2 < rep["r_max_err_over_bound"] <= 0.5 * (1 + 1e-4)
+        assert 0.2 < rep["v_max_err_over_bound"] <= 0.5 * (1 + 1e-4)
+        assert 0.2 < rep["htau_max_err_over_bound"] <= 0.5 * (1 + 1e-4)
+
+
+def test_accepts_a_divergence_at_an_exact_tie():
+    """Two identical columns have equal norms at every step: a program that
+    takes the other one where the oracle takes the first is as right, and
+    only the rows finished before that step are compared."""
+    A = _matrix()
+    j1, j2 = 37, 150
+    A[:, j2] = A[:, j1]
+    o = O.qrdm(A, 0.5, 0.9, 16)
+    sw = np.arange(N)
+    sw[j1], sw[j2] = j2, j1
+    g = _copy(o)
+    g["perm"] = sw[o["perm"]]
+    g["J"] = np.where(o["J"] >= 0, sw[np.maximum(o["J"], 0)], -1)
+    rep = compare(A, g, o)
+    assert rep["diverged_at"] is not None and rep["tie_score"] == 0.0
+    assert 0 < rep["ncmp"] < N
+
+
+def _plant(name, A, o, e, d, i0):
+    g = _copy(o)
+    if name == "r_entry":  # one entry of a live row, 3 bounds off
+        i, j = 10, 150
+        g["A"][i, j] += 3.0 * (1e-11 * abs(o["A"][i, j]) + e[i])
+    elif name == "r_diag_relative":  # a large |R_ii| off by 1e-10 relative
+        g["A"][5, 5] *= 1.0 + 1e-10
+    elif name == "r_diag_noise_row":  # a noise row's |R_ii| off by 3 bounds
+        i = i0 + 20
+        g["A"][i, i] += np.sign(o["A"][i, i]) * 3.0 * rdiag_tol(d, float(np.max(np.linalg.norm(A, axis=0))), M)[i]
+    elif name == "r_noise_block":  # a noise-row entry off by the size of the live block
+        g["A"][i0 + 5, i0 + 40] += abs(o["A"][0, 0])
+    elif name == "reflector_sign":
+        g["A"][11:, 10] *= -1.0
+    elif name == "reflector_entry":
+        g["A"][60, 40] += 4.0 * 3.0 * e[40] / d[40]
+    elif name == "htau":
+        g["htau"][7] += 3.0 * 2.0 * e[7] / d[7]
+    elif name == "perm_swap":
+        g["perm"][[3, 4]] = g["perm"][[4, 3]]
+    elif name == "perm_swap_tail":
+        g["perm"][[N - 2, N - 1]] = g["perm"][[N - 1, N - 2]]
+    elif name == "pick":  # a different column at a step with a clear margin
+        s = 2
+        used = set(int(x) for x in g["J"][s][: int(o["trace"]["k"][s])])
+        g["J"][s][3] = next(j for j in range(N) if j not in used)
+    elif name == "block_size":
+        g["trace"]["k"][4] -= 1
+    elif name == "panel_break":
+        g["trace"]["l"][1] -= 1
+    elif name == "dm_flag":
+        g["trace"]["dm_on"][3] = 1 - g["trace"]["dm_on"][3]
+    elif name == "one_step_short":
+        g["trace"], g["J"] = g["trace"][:-1], g["J"][:-1]
+    elif name == "rank":
+        g["rank"] += 1
+    elif name == "rank_colmax":
+        g["rank_colmax"] -= 1
+    else:
+        raise ValueError(name)
+    return g
+
+
+PLANTS = ["r_entry", "r_diag_relative", "r_diag_noise_row", "r_noise_block", "reflector_sign", "reflector_entry",
+          "htau", "perm_swap", "perm_swap_tail", "pick", "block_size", "panel_break", "dm_flag", "one_step_short",
+          "rank", "rank_colmax"]
+
+
+@pytest.mark.parametrize("name", PLANTS)
+def test_rejects_a_planted_mistake(case, name):
+    A, o = case
+    _, e, d, i0 = _perturbed(A, o, 0.0)
+    g = _plant(name, A, o, e, d, i0)
+    with pytest.raises(AssertionError):
+        compare(A, g, o)
+
+
+def test_a_missed_stop_at_the_rank_needs_a_tie_in_the_stopping_test(case):
+    """With the stop at the rank (Sec. 3.4 criterion), a program that goes on
+    where the oracle stopped is accepted only if the oracle's stopping test
+    was within its rounding margin.  At the 1e-15 gap the residual norms are
+    rounding noise and the test is a tie; after exactly zero residuals
+    (mu = 0) it is not."""
+    A, _ = case
+    o = O.qrdm(A, 0.5, 0.9, 16, stop_at_rank=True)
+    full = O.qrdm(A, 0.5, 0.9, 16)
+    assert o["stop"] is not None and int(o["stop"]["ns"]) == o["rank"]
+    assert float(o["stop"]["s_stop"]) < 1.0
+    rep = compare(A, full, o)
+    assert rep["diverged_at"] == len(o["trace"]) and rep["ncmp"] == o["rank"]
+
+    rng = np.random.default_rng(4)
+    Z = np.zeros((100, 60))
+    live = np.sort(rng.choice(60, size=40, replace=False))
+    Z[:, live] = rng.standard_normal((100, 40))
+    o = O.qrdm(Z, 0.5, 0.9, 16, stop_at_rank=True)
+    full = O.qrdm(Z, 0.5, 0.9, 16)
+    assert o["rank"] == 40 and o["stop"] is not None and np.isinf(float(o["stop"]["s_stop"]))
+    assert len(full["trace"]) > len(o["trace"])
+    with pytest.raises(AssertionError):
+        compare(Z, full, o)
+    # and the run without the stop has no stopping record: past its last
+    # step nothing may go on
+    assert full["stop"] is None
+    short = _copy(full)
+    short["trace"], short["J"] = full["trace"][:-1], full["J"][:-1]
+    with pytest.raises(AssertionError):
+        compare(Z, full, short)
