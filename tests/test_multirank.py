@@ -73,6 +73,19 @@ def test_two_gloo_ranks_replicas():
             line = json.loads(text.strip())
             assert line["impl"] == "reference" and line["cpu_baseline"]["kind"] == "oracle"
             assert np.isfinite(line["value"]) and line["value"] > 0
+            # the base contract's keys, with this arm's own config and an
+            # e2e that moves no bytes between host and device
+            for key, typ in (("metric", str), ("unit", str), ("n_gpus", int), ("steps", int), ("warmup", int),
+                             ("ms_per_step", float), ("higher_is_better", bool), ("scaling", str),
+                             ("dtype", str), ("data", str), ("config", dict), ("e2e", dict)):
+                assert isinstance(line[key], typ), key
+            assert line["n_gpus"] == world and line["higher_is_better"] is True and line["vs_baseline"] is None
+            assert line["dtype"] == "f64" and line["config"]["workload"].startswith("CPU sample")
+            assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                                   "d2h_bytes_per_step": 0}
+            cb = line["cpu_baseline"]
+            assert cb["value"] == line["value"] and isinstance(cb["cores"], int) and cb["cores"] >= 1
+            assert isinstance(cb["sample"], str) and cb["nproc"] >= cb["cores"]
         else:
             assert text == ""
 
@@ -84,3 +97,14 @@ def test_single_process_helpers():
     assert bench.max_over_ranks(3.0) == 3.0
     assert bench.aggregate_gflops(1, 2e9, 2, 1000.0) == pytest.approx(4.0)
     assert bench.metric_flops(4096, 4096) == pytest.approx(4 * 4096 ** 3 - 4 * 4096 ** 3 / 3)
+    # the metric is twice LAPACK's xGEQRF count 2 m n^2 - 2 n^3 / 3
+    assert bench.metric_flops(8192, 2048) == pytest.approx(2 * (2 * 8192 * 2048 ** 2 - 2 * 2048 ** 3 / 3))
+    # the count up to a stop after r columns: all of it at r = n, and within
+    # O(1/r) of twice the Householder sum 4 (m - i)(n - i) over i < r
+    for m, n in ((4096, 4096), (8192, 2048), (16384, 16384)):
+        assert bench.executed_flops(m, n, n) == pytest.approx(bench.metric_flops(m, n), rel=1e-12)
+        for r in (64, n // 2, n):
+            i = np.arange(r, dtype=np.float64)
+            exact = 2.0 * float(np.sum(4.0 * (m - i) * (n - i)))
+            assert bench.executed_flops(m, n, r) == pytest.approx(exact, rel=2.0 / r)
+    assert bench.executed_flops(100, 50, 0) == 0.0
