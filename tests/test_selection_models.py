@@ -8,7 +8,14 @@ the reformulated kernels keep the plain forms' decisions:
 * the pairwise swaps of Sec. 4 simulated with an inverse map equal the
   simulation that searches the current position of each selected column;
 * a transposed lane tree (each level keeps half of a lane's values) adds the
-  same pairs as one xor lane tree per value, so every sum has the same bits.
+  same pairs as one xor lane tree per value, so every sum has the same bits;
+* the argmax, the candidate test u >= tau mu and the candidate order taken on
+  the raw bits of the partial norms read as signed 64-bit integers (integer
+  compares instead of FP64 ones) equal the same decisions on the values.
+  This holds for non-negative doubles.  The partial norms are never negative
+  and never -0.0: they are square roots of sums of squares, 0.0 for factored
+  columns, or u sqrt(t) with u > 0 and t clamped to +0.0 or more (1 - q is
+  +0.0 when q = 1 in round-to-nearest).
 """
 from __future__ import annotations
 
@@ -159,3 +166,40 @@ def test_transposed_lane_tree_adds_the_same_pairs_as_the_xor_tree():
                         idx += h
                 ref = _xor_tree(list(x[:, idx]), offs)[L]
                 assert got[L][0] == ref  # bit for bit
+
+
+def _keys(u):
+    return np.asarray(u, dtype=np.float64).view(np.int64)
+
+
+def test_integer_keys_of_non_negative_doubles_order_like_the_values():
+    rng = np.random.default_rng(12)
+    tiny = np.nextafter(0.0, 1.0)
+    edges = np.array([0.0, tiny, 2 * tiny, np.finfo(np.float64).tiny, 1.0, np.nextafter(1.0, 2.0),
+                      np.nextafter(1.0, 0.0), 20 * 2.0 ** -52, np.finfo(np.float64).max])
+    for trial in range(400):
+        n = int(rng.integers(1, 300))
+        u = np.abs(rng.standard_normal(n)) * np.exp(rng.uniform(-700, 700, size=n))  # finite values
+        if trial % 3 == 0:
+            u[rng.integers(0, n, size=n // 4 + 1)] = rng.choice(edges)
+        if trial % 4 == 0:  # exact ties, and zero columns
+            u[rng.integers(0, n, size=n // 3 + 1)] = u[0]
+            u[rng.integers(0, n)] = 0.0
+        assert np.all(u >= 0.0) and not np.any(np.signbit(u))
+        k = _keys(u)
+        # argmax, ties to the lowest position
+        assert int(np.argmax(k)) == int(np.argmax(u))
+        # the candidate test u >= thr, thr = tau mu, with the key of thr
+        for tau in (0.0, 0.15, 0.5, 0.9, 1.0, float(rng.uniform())):
+            thr = tau * float(u.max())
+            assert np.array_equal(k >= _keys([thr])[0], u >= thr)
+        # the order by (u descending, position ascending)
+        pos = np.arange(n)
+        assert np.array_equal(np.lexsort((pos, -k)), np.lexsort((pos, -u)))
+
+
+def test_negative_zero_would_break_the_keys():
+    """Why the partial norms must never be -0.0: its key is the smallest
+    integer, so it would sort below +0.0, where the values tie."""
+    assert _keys([-0.0])[0] < _keys([0.0])[0]
+    assert -0.0 == 0.0
