@@ -271,6 +271,22 @@ def test_rank_criterion_and_dm_safeguard_on_an_exact_diagonal():
     assert np.all(s["A"][82:, 82:] == A[82:, 82:]) and np.all(s["htau"][82:] == 0.0)
 
 
+def test_rank_criterion_counts_all_n_minus_ns_columns_on_a_wide_matrix():
+    """The criterion's factor is sqrt(n - n_s), the number of columns of R22
+    (Sec. 3.4), not sqrt(min(m, n) - n_s).  The diagonal above with 40 zero
+    columns appended (100 x 140): eps1 = 140 eps.  At n_s = 90, sqrt(50) eta
+    = 141.4 eps does not pass; at n_s = 98, sqrt(42) eta = 129.6 eps does, so
+    rank = 98 (with sqrt(100 - n_s) it would already pass at n_s = 58)."""
+    A = np.asfortranarray(np.hstack([criterion_diagonal(), np.zeros((100, 40))]))
+    r = O.qrdm(A, 0.9, 0.9, 8)
+    assert r["rank"] == 98 and r["rank_colmax"] == 50
+    tr = r["trace"]
+    assert list(tr["ns"]) == [0, 8, 16, 24, 32, 40, 48, 50, 58, 66, 74, 82, 90, 98, 99]
+    assert list(tr["k"]) == [8, 8, 8, 8, 8, 8, 2, 8, 8, 8, 8, 8, 8, 1, 1]
+    assert list(tr["dm_on"]) == [1] * 13 + [0, 0]
+    assert np.array_equal(r["perm"], np.arange(140))
+
+
 def test_rank_exact_integer_matrices():
     for c in golden("exact_rank.json")["cases"]:
         A = np.asfortranarray(np.array(c["columns"]).T)
@@ -354,11 +370,63 @@ def test_cancellation_triggers_recompute():
     np.testing.assert_allclose(r["u"][1:], exact, rtol=1e-13)
 
 
+DOWNDATE_CASES = [
+    ("geo 300x300 1e-15", lambda sd: inputs.from_spectrum(300, 300, inputs.sigma_geometric(300, 1e-15), sd), 0.15,
+     0.9, 16, range(4)),
+    ("geo 400x250 1e-12", lambda sd: inputs.from_spectrum(400, 250, inputs.sigma_geometric(250, 1e-12), sd), 0.5,
+     0.9, 32, range(2)),
+    ("kahan 300", lambda sd: inputs.kahan(300), 0.15, 0.9, 16, range(1)),
+]
+
+
+@pytest.mark.parametrize("case", DOWNDATE_CASES, ids=lambda c: c[0])
+def test_partial_norms_stay_within_the_downdate_bound(case):
+    """A bound that does not use the oracle's own uref.  A partial norm
+    carries an absolute error of about sqrt(m) eps uref (inner products of
+    length m); the downdate amplifies it by (uref/u)^2 relative to u, and the
+    recompute test (Sec. 3.1, t (u/uref)^2 > sqrt(eps) to keep a downdate)
+    holds that factor below 1/sqrt(eps).  So at every block-step start each
+    partial norm is within sqrt(m eps) relative of the true norm of its
+    column of R22, computed here from the trailing block itself."""
+    _, build, tau, delta, kmax, seeds = case
+    for sd in seeds:
+        A = build(sd)
+        m = A.shape[0]
+        for steps in (3, 6, 10, 15, 20, 30):
+            r = O.qrdm(A, tau, delta, kmax, max_steps=steps)
+            ns = int(r["trace"]["l"].sum())
+            if ns >= min(A.shape):
+                break
+            true = np.linalg.norm(r["A"][ns:, ns:], axis=0)
+            rel = np.abs(r["u"][ns:] - true) / true
+            assert rel.max() <= np.sqrt(m * EPS), (sd, steps, ns, rel.max())
+
+
 # ---------------------------------------------------------------- theorems (SDD mode)
 def _sdd_run(A, tau, kmax):
     r = O.qrdm(A, tau, 1.0, kmax, sdd=True, no_break=True)
     assert r["status"] == 0
     return r
+
+
+@pytest.mark.parametrize("cos,accepted", [(0.35, True), (0.6, False)])
+def test_sdd_delta_divides_tau_squared_by_the_candidate_count(cos, accepted):
+    """eq. delta_max with reading R18: delta_s = min(delta, tau^2 / |I|), |I|
+    the candidates other than the pivot (eq. def_candidate_set), so that the
+    k - 1 <= |I| off-diagonal cosines of a row add up to less than tau^2.
+    Pivot e1, candidates of norms 0.95 (cosine `cos` with the pivot) and 0.92
+    (orthogonal to both), tau = 0.9: |I| = 2 and delta_s = 0.405.  A cosine of
+    0.35 passes (it would not under tau^2 / (|I| + 1) = 0.27); 0.6 does not
+    (it would under tau^2 / (|I| - 1) = 0.81)."""
+    A = np.zeros((4, 4))
+    A[0, 0] = 1.0
+    A[:2, 1] = 0.95 * np.array([cos, np.sqrt(1.0 - cos * cos)])
+    A[2, 2] = 0.92
+    A[3, 3] = 0.1
+    r = O.qrdm(np.asfortranarray(A), 0.9, 0.9, 4, sdd=True, no_break=True, max_steps=1)
+    tr = r["trace"][0]
+    assert int(tr["ncand"]) == 2
+    assert list(r["J"][0][: int(tr["k"])]) == ([0, 1, 2] if accepted else [0, 2])
 
 
 @pytest.mark.parametrize("seed", range(4))

@@ -2,11 +2,13 @@
 
 The GPU parity tests are only as strong as ``compare``.  Here the oracle's
 own output plays the GPU's part: ``compare`` must accept it unchanged, accept
-it moved by half of every rounding bound, and accept a divergence at an exact
-tie; and it must reject each planted mistake that a wrong kernel could make
-(an R entry, a diagonal, a reflector or an htau beyond its bound, a swapped
-permutation, a different pick, block size or step count with no tie, a wrong
-rank, a missed stop at the rank)."""
+it moved by half of every rounding bound, accept a divergence at an exact
+tie, and accept the oracle's run on a rounding-sized perturbation of the
+input (which checks the margins the oracle logs: a decision it calls clear
+must not flip); and it must reject each planted mistake that a wrong kernel
+could make (an R entry, a diagonal, a reflector or an htau beyond its bound,
+a swapped permutation, a different pick, block size or step count with no
+tie, a wrong rank, a missed stop at the rank)."""
 from __future__ import annotations
 
 import numpy as np
@@ -14,7 +16,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2106_03138_gb300 import inputs
-from tests._parity import compare, rdiag_tol, row_err
+from tests._parity import EPS, compare, rdiag_tol, row_err
 
 M, N = 300, 200
 
@@ -90,6 +92,46 @@ def test_accepts_a_divergence_at_an_exact_tie():
     rep = compare(A, g, o)
     assert rep["diverged_at"] is not None and rep["tie_score"] == 0.0
     assert 0 < rep["ncmp"] < N
+
+
+PERTURBED = [
+    # (name, matrix, tau, delta, k_max, decisions flip somewhere)
+    ("gap256 (0.9, 0.9, 32)", lambda: inputs.from_spectrum(256, 256, inputs.sigma_gap(256, 128), 5), 0.9, 0.9, 32,
+     True),
+    ("gap256 (0.15, 0.9, 64)", lambda: inputs.from_spectrum(256, 256, inputs.sigma_gap(256, 128), 5), 0.15, 0.9, 64,
+     True),
+    ("geo 300x200 1e-15 (0.5, 0.9, 16)",
+     lambda: inputs.from_spectrum(300, 200, inputs.sigma_geometric(200, 1e-15), 7), 0.5, 0.9, 16, True),
+    ("geo 300x200 1e-12 (0.2, 0.95, 16)",
+     lambda: inputs.from_spectrum(300, 200, inputs.sigma_geometric(200, 1e-12), 8), 0.2, 0.95, 16, False),
+    ("dense 200x150 (0.9, 0.9, 32)", lambda: inputs.random_dense(200, 150, 3), 0.9, 0.9, 32, False),
+    ("kahan 200 (0.15, 0.9, 64)", lambda: inputs.kahan(200), 0.15, 0.9, 64, True),
+]
+
+
+@pytest.mark.parametrize("case", PERTURBED, ids=lambda c: c[0])
+def test_the_oracle_on_a_perturbed_input_passes_the_rule(case):
+    """Soundness of the margins the oracle logs: its own run on A + E, with
+    entries of E up to about eps anorm (rounding-sized), is another correct
+    program's answer for A.  The rule must accept it: every step where the
+    two runs decide differently must be one the oracle logged as a tie, and
+    the rows before it must agree within the bounds.  Where the inputs have a
+    roundoff tail or equal norms (gap, 1e-15 geometric, Kahan) the decisions
+    do flip, so the tie test itself is exercised."""
+    _, build, tau, delta, kmax, flips = case
+    A = build()
+    o = O.qrdm(A, tau, delta, kmax)
+    anorm = float(np.max(np.linalg.norm(A, axis=0)))
+    diverged = []
+    for seed in range(2):
+        rng = np.random.default_rng(seed)
+        for scale in (0.25, 1.0):
+            E = scale * EPS * anorm * rng.standard_normal(A.shape)
+            rep = compare(A, O.qrdm(A + E, tau, delta, kmax), o)
+            diverged.append(rep["diverged_at"] is not None)
+            if rep["ncmp"]:
+                assert rep["r_max_err_over_bound"] <= 0.5
+    assert any(diverged) == flips
 
 
 def _plant(name, A, o, e, d, i0):
