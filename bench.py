@@ -968,6 +968,8 @@ def main() -> int:
                for nm, (m, n), f in zip(WORKLOAD, shapes, infos)]
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            # the same rate by LAPACK's xGEQRF count 2mn^2 - 2n^3/3, half the metric's
+            "value_lapack_count": value / 2.0,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(world), "roofline": roofline, "cpu_baseline": cpu,
