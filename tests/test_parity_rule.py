@@ -16,7 +16,20 @@ import pytest
 
 from oracle import oracle as O
 from paper_2106_03138_gb300 import inputs
-from tests._parity import EPS, compare, rdiag_tol, row_err
+from tests._parity import EPS, SCORES, compare
+
+# The rule's bounds, restated from its statement (tests/_parity.py docstring)
+# rather than imported, so that a changed constant there fails here.
+
+
+def row_err(m, ncmp, anorm):
+    """e_i = sqrt(m (i + 1)) eps anorm."""
+    return np.sqrt(m * (np.arange(ncmp) + 1.0)) * EPS * anorm
+
+
+def rdiag_tol(d, anorm, m):
+    """|R_ii| within 1e-11 relative where |R_ii| >= 1e-3 anorm, else 1e-11 |R_ii| + e_i."""
+    return np.where(d >= 1e-3 * anorm, 1e-11 * d, 1e-11 * d + row_err(m, d.size, anorm))
 
 M, N = 300, 200
 
@@ -134,24 +147,43 @@ def test_the_oracle_on_a_perturbed_input_passes_the_rule(case):
     assert any(diverged) == flips
 
 
+# Errors are planted at 1.5 times their bound: a rule loosened by a factor of
+# two or more would accept them.
+OVER = 1.5
+
+
 def _plant(name, A, o, e, d, i0):
     g = _copy(o)
-    if name == "r_entry":  # one entry of a live row, 3 bounds off
+    anorm = float(np.max(np.linalg.norm(A, axis=0)))
+    if name == "r_entry":  # one entry of a live row
         i, j = 10, 150
-        g["A"][i, j] += 3.0 * (1e-11 * abs(o["A"][i, j]) + e[i])
-    elif name == "r_diag_relative":  # a large |R_ii| off by 1e-10 relative
-        g["A"][5, 5] *= 1.0 + 1e-10
-    elif name == "r_diag_noise_row":  # a noise row's |R_ii| off by 3 bounds
+        g["A"][i, j] += OVER * (1e-11 * abs(o["A"][i, j]) + e[i])
+    elif name == "r_entry_absolute":  # the smallest live entry, where the e_i term governs
+        R = np.abs(np.triu(o["A"][:i0, :], 1))
+        R[R == 0.0] = np.inf
+        i, j = np.unravel_index(np.argmin(R), R.shape)
+        assert 1e-11 * R[i, j] < 0.01 * e[i]
+        g["A"][i, j] += OVER * (1e-11 * R[i, j] + e[i])
+    elif name == "r_diag_relative":  # a large |R_ii|, relative bound 1e-11
+        g["A"][5, 5] *= 1.0 + OVER * 1e-11
+    elif name == "r_diag_relative_only":
+        # |R_ii| >= 1e-3 anorm has no absolute slack: 1e-11 |R_ii| + e_i / 2
+        # passes every entry bound but not the diagonal's
+        assert abs(o["A"][5, 5]) >= 1e-3 * anorm
+        g["A"][5, 5] += np.sign(o["A"][5, 5]) * (1e-11 * abs(o["A"][5, 5]) + 0.5 * e[5])
+    elif name == "r_diag_noise_row":  # a noise row's |R_ii|
         i = i0 + 20
-        g["A"][i, i] += np.sign(o["A"][i, i]) * 3.0 * rdiag_tol(d, float(np.max(np.linalg.norm(A, axis=0))), M)[i]
-    elif name == "r_noise_block":  # a noise-row entry off by the size of the live block
-        g["A"][i0 + 5, i0 + 40] += abs(o["A"][0, 0])
+        g["A"][i, i] += np.sign(o["A"][i, i]) * OVER * rdiag_tol(d, anorm, M)[i]
+    elif name == "r_noise_block":  # a noise-row entry beyond the size of the noise block
+        i, j = i0 + 5, i0 + 40
+        noise = 2.0 * float(np.max(np.linalg.norm(np.triu(o["A"][: min(M, N), :])[i0:], axis=0)))
+        g["A"][i, j] += OVER * (1e-11 * abs(o["A"][i, j]) + e[i] + noise)
     elif name == "reflector_sign":
         g["A"][11:, 10] *= -1.0
     elif name == "reflector_entry":
-        g["A"][60, 40] += 4.0 * 3.0 * e[40] / d[40]
+        g["A"][60, 40] += OVER * 3.0 * e[40] / d[40]
     elif name == "htau":
-        g["htau"][7] += 3.0 * 2.0 * e[7] / d[7]
+        g["htau"][7] += OVER * 2.0 * e[7] / d[7]
     elif name == "perm_swap":
         g["perm"][[3, 4]] = g["perm"][[4, 3]]
     elif name == "perm_swap_tail":
@@ -177,7 +209,7 @@ def _plant(name, A, o, e, d, i0):
     return g
 
 
-PLANTS = ["r_entry", "r_diag_relative", "r_diag_noise_row", "r_noise_block", "reflector_sign", "reflector_entry",
+PLANTS = ["r_entry", "r_entry_absolute", "r_diag_relative", "r_diag_relative_only", "r_diag_noise_row", "r_noise_block", "reflector_sign", "reflector_entry",
           "htau", "perm_swap", "perm_swap_tail", "pick", "block_size", "panel_break", "dm_flag", "one_step_short",
           "rank", "rank_colmax"]
 
@@ -222,3 +254,84 @@ def test_a_missed_stop_at_the_rank_needs_a_tie_in_the_stopping_test(case):
     short["trace"], short["J"] = full["trace"][:-1], full["J"][:-1]
     with pytest.raises(AssertionError):
         compare(Z, full, short)
+
+
+def _pick_at(g, o, s):
+    """g with a different column picked at step s."""
+    g = _copy(g)
+    used = set(int(x) for x in o["J"][s][: int(o["trace"]["k"][s])])
+    g["J"][s][3] = next(j for j in range(N) if j not in used)
+    return g
+
+
+@pytest.mark.parametrize("score,tie", [(0.9, True), (1.1, False)])
+def test_a_logged_score_below_one_is_a_tie_and_above_is_not(case, score, tie):
+    """The threshold of the tie test itself: a step whose smallest logged
+    score (decision margin over its rounding uncertainty) is below 1 may
+    diverge, one at or above 1 may not."""
+    A, o = case
+    o2 = _copy(o)
+    # step 2's smallest score becomes `score` (the others there are far above it)
+    assert min(float(o["trace"][f][2]) for f in SCORES) > 1e3
+    o2["trace"]["s_order"][2] = score
+    g = _pick_at(o, o, 2)
+    if tie:
+        assert compare(A, g, o2)["diverged_at"] == 2
+    else:
+        with pytest.raises(AssertionError):
+            compare(A, g, o2)
+
+
+@pytest.mark.parametrize("score,tie", [(0.5, True), (2.0, False)])
+def test_an_earlier_recompute_near_tie_explains_a_later_divergence(case, score, tie):
+    """A norm recomputed or downdated on a near-tie of the recompute test
+    changes that norm within its uncertainty, so every later decision may
+    differ: a divergence at step 3 is accepted when step 1 logged a recompute
+    score below 1."""
+    A, o = case
+    o2 = _copy(o)
+    o2["trace"]["s_recomp"][1] = score
+    g = _pick_at(o, o, 3)
+    if tie:
+        assert compare(A, g, o2)["diverged_at"] == 3
+    else:
+        with pytest.raises(AssertionError):
+            compare(A, g, o2)
+
+
+def test_the_permutation_of_unfactored_columns_is_compared():
+    """A wide matrix (m < n): the columns past min(m, n) are never factored,
+    but their order is part of the result and must match when no decision
+    differs.  Two identical tiny columns stay there; exchanging their labels
+    leaves R by original column unchanged, so only the permutation check can
+    see it."""
+    rng = np.random.default_rng(4)
+    c = 1e-8 * rng.standard_normal((80, 1))
+    A = np.asfortranarray(np.hstack([inputs.from_spectrum(80, 118, inputs.sigma_geometric(80, 1e-6), 4), c, c]))
+    o = O.qrdm(A, 0.5, 0.9, 16)
+    g = _copy(o)
+    assert compare(A, g, o)["diverged_at"] is None
+    p1, p2 = (int(np.nonzero(o["perm"] == j)[0][0]) for j in (118, 119))
+    assert min(p1, p2) >= 80  # both left unfactored
+    g["perm"][[p1, p2]] = g["perm"][[p2, p1]]
+    with pytest.raises(AssertionError):
+        compare(A, g, o)
+
+
+def test_the_permutation_before_a_tie_is_compared():
+    """After a divergence at a tie, the permutation of the columns factored
+    before it must still match."""
+    A = _matrix()
+    j1, j2 = 37, 150
+    A[:, j2] = A[:, j1]
+    o = O.qrdm(A, 0.5, 0.9, 16)
+    sw = np.arange(N)
+    sw[j1], sw[j2] = j2, j1
+    g = _copy(o)
+    g["perm"] = sw[o["perm"]]
+    g["J"] = np.where(o["J"] >= 0, sw[np.maximum(o["J"], 0)], -1)
+    ncmp = compare(A, g, o)["ncmp"]
+    g["perm"][[0, 1]] = g["perm"][[1, 0]]
+    assert ncmp > 2
+    with pytest.raises(AssertionError):
+        compare(A, g, o)
