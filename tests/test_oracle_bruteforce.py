@@ -38,7 +38,8 @@ def _house(x):
     return v, (beta - alpha) / beta, beta
 
 
-def qrdm_bruteforce(A, tau, delta, kmax):
+def qrdm_bruteforce(A, tau, delta, kmax, schedule=None):
+    """schedule: per-step (tau, delta) rows; steps past its end use (tau, delta)."""
     R = np.array(A, dtype=np.float64)
     m, n = R.shape
     kmin = min(m, n)
@@ -48,6 +49,9 @@ def qrdm_bruteforce(A, tau, delta, kmax):
     ns, dm_on, rank = 0, True, None
     steps = []
     while ns < kmin:
+        step_tau, step_delta = (tau, delta)
+        if schedule is not None and len(steps) < len(schedule):
+            step_tau, step_delta = float(schedule[len(steps)][0]), float(schedule[len(steps)][1])
         u = np.linalg.norm(R[ns:, ns:], axis=0)  # exact partial norms of positions ns..n-1
         jstar = int(np.argmax(u))  # first maximum: lowest position
         mu = float(u[jstar])
@@ -55,13 +59,13 @@ def qrdm_bruteforce(A, tau, delta, kmax):
         margins = [np.inf]
         if u.size > 1 and mu > 0:
             margins.append((mu - np.partition(u, -2)[-2]) / mu)
-            margins.append(np.min(np.abs(np.delete(u, jstar) - tau * mu)) / (tau * mu))
+            margins.append(np.min(np.abs(np.delete(u, jstar) - step_tau * mu)) / (step_tau * mu))
         if dm_on and anorm > 0:
             margins.append(abs(np.sqrt(n - ns) * mu - eps1 * anorm) / (eps1 * anorm))
         if dm_on and np.sqrt(n - ns) * mu <= eps1 * anorm:
             dm_on, rank = False, ns
         kcap = min(kmax if dm_on else 1, kmin - ns)
-        cand = [j for j in range(n - ns) if j != jstar and u[j] >= tau * mu]
+        cand = [j for j in range(n - ns) if j != jstar and u[j] >= step_tau * mu]
         cand.sort(key=lambda j: (-u[j], j))
         if kcap > 1:  # the order of the kept candidates and at the cap
             kept = cand[: kcap]
@@ -75,8 +79,8 @@ def qrdm_bruteforce(A, tau, delta, kmax):
             ok = True
             for b in J:
                 th = abs(G[a, b]) / (dn[a] * dn[b]) if dn[a] > 0 and dn[b] > 0 else 1.0
-                margins.append(abs(th - delta))
-                if not th < delta:
+                margins.append(abs(th - step_delta))
+                if not th < step_delta:
                     ok = False
             if ok:
                 J.append(a)
@@ -88,7 +92,7 @@ def qrdm_bruteforce(A, tau, delta, kmax):
                 R[:, [p, q]] = R[:, [q, p]]
                 label[[p, q]] = label[[q, p]]
         k = len(picked)
-        eps_s = tau * mu
+        eps_s = step_tau * mu
         lacc = k
         for l in range(k):
             col = ns + l
@@ -170,3 +174,24 @@ def test_oracle_takes_the_brute_force_decisions(case):
         compared += ncols
     print(f"\n[brute force] {name}: {compared} of {12 * min(build(0).shape)} columns compared")
     assert compared >= round(share * 12 * min(build(0).shape)), compared
+
+
+def test_per_step_schedule_matches_the_brute_force():
+    """A per-step (tau, delta) schedule (the learned policy's form): step s
+    uses row s of the schedule for its candidate threshold, its cosine test
+    and its break threshold eps_s = tau_s mu."""
+    rng = np.random.default_rng(7)
+    compared = 0
+    for sd in range(12):
+        A = inputs.random_dense(30, 24, 50 + sd)
+        sched = np.column_stack([rng.uniform(0.3, 1.0, 10), rng.uniform(0.3, 1.0, 10)])
+        o = O.qrdm(A, 0.9, 0.9, 6, schedule=sched)
+        b = qrdm_bruteforce(A, 0.9, 0.9, 6, schedule=sched)
+        for s, (rec, bs) in enumerate(zip(o["trace"], b["steps"])):
+            if not _clear(rec, 1e-6) or bs["margin"] <= 1e-6:
+                break
+            k = int(rec["k"])
+            assert (k, int(rec["l"])) == (bs["k"], bs["l"]) and list(o["J"][s][:k]) == bs["J"], (sd, s)
+            assert float(rec["eps_s"]) == pytest.approx((sched[s][0] if s < 10 else 0.9) * float(rec["mu"]), rel=1e-15)
+            compared += 1
+    assert compared >= 60, compared
