@@ -555,3 +555,22 @@ def test_ls_basic_rank_deficient_compatible_system_is_solved():
     x = O.ls_basic(A, b, rank=25, tau=0.9, delta=0.9, k_max=32)
     assert np.count_nonzero(x) <= 25
     assert np.linalg.norm(A @ x - b) <= 1e-12 * np.linalg.norm(b)
+
+
+# ---------------------------------------------------------------- OpenMP build
+@pytest.mark.parametrize("kind", ["gap", "geo", "kahan"])
+def test_openmp_build_gives_the_same_bits(kind):
+    """The OpenMP build (timed as the all-cores CPU baseline) spreads only the
+    trailing update's independent column loops over threads, each column
+    summed in the same order, so every output is bit-identical to the
+    single-threaded build's."""
+    if O.build_omp() is None:
+        pytest.skip("the C compiler has no OpenMP")
+    A = {"gap": lambda: inputs.from_spectrum(400, 300, inputs.sigma_gap(300, 150), 2),
+         "geo": lambda: inputs.from_spectrum(350, 350, inputs.sigma_geometric(350, 1e-15), 3),
+         "kahan": lambda: inputs.kahan(300)}[kind]()
+    a = O.qrdm(A, 0.15, 0.9, 32)
+    b = O.qrdm(A, 0.15, 0.9, 32, parallel=True)
+    for key in ("A", "htau", "perm", "u", "uref", "trace", "J"):
+        assert np.array_equal(a[key], b[key]), key
+    assert (a["rank"], a["rank_colmax"], a["nsteps"]) == (b["rank"], b["rank_colmax"], b["nsteps"])
