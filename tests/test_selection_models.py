@@ -9,6 +9,9 @@ the reformulated kernels keep the plain forms' decisions:
   simulation that searches the current position of each selected column;
 * a transposed lane tree (each level keeps half of a lane's values) adds the
   same pairs as one xor lane tree per value, so every sum has the same bits;
+* the trailing update's W = T^T V^T A, formed without T by forward
+  substitution with S = V^T V (W_t = htau_t (P_t - sum_{q<t} S_qt W_q)),
+  makes A - V W equal the reflectors applied one after another;
 * the argmax, the candidate test u >= tau mu and the candidate order taken on
   the raw bits of the partial norms read as signed 64-bit integers (integer
   compares instead of FP64 ones) equal the same decisions on the values.
@@ -203,3 +206,32 @@ def test_negative_zero_would_break_the_keys():
     integer, so it would sort below +0.0, where the values tie."""
     assert _keys([-0.0])[0] < _keys([0.0])[0]
     assert -0.0 == 0.0
+
+
+def test_w_by_forward_substitution_applies_the_block_reflector():
+    """Sec. 3.2: H_1 ... H_l = I - V T V^T, so the trailing update is
+    A - V (T^T V^T A).  The kernels never form T: with S = V^T V,
+    T^-1 = strict_upper(S) + diag(1/htau), and W solves (T^-1)^T W = V^T A
+    column by column.  Checked against the reflectors applied one by one,
+    including a reflector with a zero tail (htau = 0, H = I)."""
+    rng = np.random.default_rng(11)
+    for m, l, n2 in ((50, 6, 20), (33, 16, 7), (9, 1, 4), (64, 32, 5)):
+        h, tau = np.linalg.qr(rng.standard_normal((m, l)), mode="raw")
+        V = np.tril(h.T, -1)[:, :l] + np.eye(m, l)
+        htau = tau.copy()
+        if l > 2:  # a zero tail: H_2 = I
+            V[3:, 2] = 0.0
+            htau[2] = 0.0
+        A = rng.standard_normal((m, n2))
+        P = V.T @ A
+        S = V.T @ V
+        W = np.zeros((l, n2))
+        for t in range(l):
+            W[t] = htau[t] * (P[t] - S[:t, t] @ W[:t])
+        ref = A.copy()
+        for i in range(l):  # H_1 first, then H_2, ...
+            v = V[:, i]
+            ref -= htau[i] * np.outer(v, v @ ref)
+        np.testing.assert_allclose(A - V @ W, ref, atol=1e-13 * np.abs(A).max())
+        if l > 2:
+            assert np.all(W[2] == 0.0)
