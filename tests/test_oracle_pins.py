@@ -574,3 +574,84 @@ def test_openmp_build_gives_the_same_bits(kind):
     for key in ("A", "htau", "perm", "u", "uref", "trace", "J"):
         assert np.array_equal(a[key], b[key]), key
     assert (a["rank"], a["rank_colmax"], a["nsteps"]) == (b["rank"], b["rank_colmax"], b["nsteps"])
+
+
+# ---------------------------------------------------------------- metamorphic invariances
+def _clear_everywhere(o, gap=1e-6):
+    tr = o["trace"]
+    gaps = np.min(np.stack([tr[f] for f in ("g_argmax", "g_cand", "g_cos", "g_break", "g_stop")]), axis=0)
+    return bool(np.all(gaps > gap))
+
+
+@pytest.mark.parametrize("kind", ["dense", "gap", "kahan"])
+def test_scaling_by_a_power_of_two_scales_r_exactly(kind):
+    """Every threshold of QRDM is relative: the candidate test tau mu, the
+    cosines, the break test eps_s = tau mu, the downdate's ratios and the
+    stopping test against eps1 max||a_i|| (Sec. 2, 3.4, Alg. 4).  Scaling A by
+    2^k is exact in binary floating point, so every decision, every reflector
+    and htau are the same bits, and R is scaled exactly."""
+    A = {"dense": lambda: inputs.random_dense(90, 70, 1),
+         "gap": lambda: inputs.from_spectrum(120, 100, inputs.sigma_gap(100, 40), 2),
+         "kahan": lambda: inputs.kahan(80)}[kind]()
+    o = O.qrdm(A, 0.3, 0.8, 16)
+    for c in (2.0 ** 40, 2.0 ** -30):
+        s = O.qrdm(c * A, 0.3, 0.8, 16)
+        assert np.array_equal(s["perm"], o["perm"]) and np.array_equal(s["J"], o["J"])
+        assert (s["rank"], s["rank_colmax"]) == (o["rank"], o["rank_colmax"])
+        for f in ("k", "l", "ns", "dm_on", "nrecomp"):
+            assert np.array_equal(s["trace"][f], o["trace"][f]), f
+        assert np.array_equal(s["htau"], o["htau"])
+        R_o, R_s = np.triu(o["A"]), np.triu(s["A"])
+        assert np.array_equal(R_s, c * R_o)
+        assert np.array_equal(s["A"] - R_s, o["A"] - R_o)  # reflector tails
+
+
+def test_a_column_permutation_of_the_input_selects_the_same_columns():
+    """The decisions depend on the columns, not on where they sit (positions
+    only break exact ties, absent here): factoring A[:, pi] picks the same
+    original columns in the same order, and each column's R entries are the
+    same bits, since every column is updated on its own."""
+    A = inputs.random_dense(80, 60, 3)
+    o = O.qrdm(A, 0.5, 0.9, 8)
+    assert _clear_everywhere(o)
+    pi = np.random.default_rng(4).permutation(60)
+    b = O.qrdm(A[:, pi], 0.5, 0.9, 8)
+    assert np.array_equal(pi[b["perm"]], o["perm"])
+    R_o = np.empty((60, 60))
+    R_b = np.empty((60, 60))
+    R_o[:, o["perm"]] = np.triu(o["A"][:60])
+    R_b[:, pi[b["perm"]]] = np.triu(b["A"][:60])
+    assert np.array_equal(R_b, R_o)
+
+
+def test_a_left_orthogonal_factor_changes_no_decision():
+    """Column norms and the Gram matrix of the trailing block are invariant
+    under A -> U A with U orthogonal (the appendix's invariance of singular
+    values under orthogonal factors), so QRDM on U A takes the same decisions
+    and gives the same |R| up to rounding (R is unique up to row signs)."""
+    rng = np.random.default_rng(5)
+    for A in (inputs.random_dense(70, 50, 6), inputs.from_spectrum(70, 50, inputs.sigma_geometric(50, 1e-6), 7)):
+        U = inputs.haar(70, 70, rng)
+        o = O.qrdm(A, 0.3, 0.8, 8)
+        b = O.qrdm(U @ A, 0.3, 0.8, 8)
+        assert _clear_everywhere(o)
+        assert np.array_equal(b["perm"], o["perm"]) and np.array_equal(b["J"], o["J"])
+        np.testing.assert_allclose(np.abs(np.triu(b["A"][:50])), np.abs(np.triu(o["A"][:50])),
+                                   rtol=1e-10, atol=1e-13 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("kmax", [1, 8, 32])
+def test_inputs_that_need_no_pivoting_give_plain_householder_qr(kmax):
+    """Orthogonal columns of strictly decreasing norm: every column is a
+    candidate in position order, every cosine is 0, no residual falls below
+    eps_s, so the permutation is the identity and R is the plain Householder
+    R of A (the library's, up to row signs): here diag(d)."""
+    Q = inputs.haar(60, 40, np.random.default_rng(8))
+    d = 2.0 ** (-np.arange(40) / 8.0)
+    A = np.asfortranarray(Q * d)
+    o = O.qrdm(A, 0.01, 0.9, kmax)
+    assert np.array_equal(o["perm"], np.arange(40))
+    R = np.triu(o["A"][:40])
+    Rlib = np.linalg.qr(A, mode="r")
+    np.testing.assert_allclose(np.abs(R), np.abs(Rlib), atol=1e-14)
+    np.testing.assert_allclose(np.abs(np.diag(R)), d, rtol=1e-13)
