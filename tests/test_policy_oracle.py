@@ -100,6 +100,24 @@ def test_step_features_by_hand():
     assert (f[13], f[14], f[15]) == (0.2, 0.7, 0.15)
 
 
+def test_step_features_do_not_depend_on_the_matrix_scale():
+    """Every feature is relative (norms against mu, mu against max||a_i||),
+    so scaling the norms by 2^k (exact in floating point) leaves all 16
+    features the same bits: the policy cannot react to the scale of A."""
+    rng = np.random.default_rng(9)
+    for _ in range(50):
+        n = int(rng.integers(5, 300))
+        u = np.abs(rng.standard_normal(n)) * np.exp(rng.uniform(-20, 20, size=n))
+        ns = int(rng.integers(0, n - 1))
+        jstar = ns + int(np.argmax(u[ns:]))
+        anorm = float(u.max()) * float(rng.uniform(1.0, 3.0))
+        args = dict(prev_l=5, prev_k=9, cos_mean=0.1, cos_max=0.4, prev_tau=0.6)
+        f = M.step_features(u, ns, jstar, anorm, **args)
+        for c in (2.0 ** 30, 2.0 ** -40):
+            g = M.step_features(c * u, ns, jstar, c * anorm, **args)
+            assert np.array_equal(f, g)
+
+
 def test_step_feature_counts_at_their_thresholds():
     """The candidate-count features count u >= t mu with t the FP32 value of
     each threshold (the kernel compares against FP32 constants): a norm equal
