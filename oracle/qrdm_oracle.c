@@ -57,8 +57,13 @@
  * PINS (tests/test_oracle_pins.py): closed-form reflectors and T, exact
  * hand-derived DM decisions and equality edges, brute-force column pivoting
  * at k_max = 1, A Pi = Q R to roundoff, exact ranks, the stopping test and
- * the DM safeguard on an exact diagonal, the paper's SDD lemmas and
- * worst-case theorems, exhaustive subset search.  Parity unpinned: the
+ * the DM safeguard on exact diagonals, the partial norms within the
+ * downdate bound of the true norms, the SDD threshold, the paper's SDD
+ * lemmas and worst-case theorems, exhaustive subset search, and invariances
+ * (exact power-of-two scaling, column permutations, a left orthogonal
+ * factor).  tests/test_oracle_bruteforce.py compares every decision with a
+ * brute-force QRDM2 (exact norms, unblocked reflectors) on small matrices.
+ * Parity unpinned: the
  * permutation on Kahan matrices, whose columns all have unit norm in exact
  * arithmetic, so that every pivot decision there is a rounding tie; those
  * runs are checked through invariants only.
