@@ -97,6 +97,11 @@ def test_kahan_matrix_and_its_perturbation():
     want = 1e-10 * EPS * np.arange(n, 0, -1) * s ** np.arange(n)
     # K_ii + d rounds d to the spacing of K_ii: compare within half of it
     assert np.all(np.abs(np.diag(D) - want) <= 0.5 * np.spacing(np.diag(K0)))
+    # at most 1e-10 (n - i + 1) ulps of K_ii for these sizes: the term rounds
+    # away entirely, and the workload is the unperturbed Kahan matrix in FP64
+    assert np.all(want < 0.5 * np.spacing(np.diag(K0)))
+    for size in (n, 2048):
+        assert np.array_equal(inputs.kahan(size, c), inputs.kahan(size, c, pert=0.0))
 
 
 def test_named_workloads():
