@@ -127,6 +127,9 @@ def kahan(n: int, c: float = 0.285, pert: float = 1e-10) -> np.ndarray:
 
     Every column has unit norm in exact arithmetic.  A diagonal perturbation
     pert * eps * (n - i + 1) * s^(i-1) (eps = 2^-52) is added to K_ii, i = 1..n.
+    At the default pert = 1e-10 that is far below half an ulp of K_ii (for
+    n <= 2048), so in FP64 it rounds away and the result is the unperturbed
+    Kahan matrix.
     """
     s = math.sqrt(1.0 - c * c)
     d = s ** np.arange(n, dtype=np.float64)
