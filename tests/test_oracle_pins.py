@@ -400,6 +400,32 @@ def test_partial_norms_stay_within_the_downdate_bound(case):
             true = np.linalg.norm(r["A"][ns:, ns:], axis=0)
             rel = np.abs(r["u"][ns:] - true) / true
             assert rel.max() <= np.sqrt(m * EPS), (sd, steps, ns, rel.max())
+            assert np.all(r["u"][:ns] == 0.0)  # factored columns carry no partial norm
+
+
+def test_recompute_test_at_its_threshold_recomputes():
+    """Reading R9 (the robust downdate of Sec. 3.1): the norm is recomputed
+    when t (u/uref)^2 <= sqrt(eps), equality included.  An exact case: four
+    unit pivots of norms 4, 3.5, 3, 2.5 (zero tails, so every reflector is the
+    identity) and a column of norm exactly 1 whose entries in the pivot rows
+    are (8191, 125, 26, 9) 2^-13, with 2^-13 below them.  Their squares add up
+    to 1 - 2^-26 exactly (8191^2 + 125^2 + 26^2 + 9^2 = 2^26 - 1), so
+    t = 2^-26 = sqrt(eps) exactly and uref = u: the test sits on its
+    threshold.  The norm is recomputed (uref reset to the new 2^-13), and the
+    column beside it, untouched by the pivots, is not.  Factored columns'
+    partial norms are zero afterwards."""
+    A = np.zeros((6, 6))
+    A[0, 0], A[1, 1], A[2, 2], A[3, 3] = 4.0, 3.5, 3.0, 2.5
+    A[:5, 4] = np.array([8191.0, 125.0, 26.0, 9.0, 1.0]) * 2.0 ** -13
+    A[5, 5] = 0.5
+    assert np.linalg.norm(A[:, 4]) == 1.0
+    r = O.qrdm(np.asfortranarray(A), 0.5, 0.9, 4, max_steps=1)
+    tr = r["trace"][0]
+    assert (int(tr["k"]), int(tr["l"]), int(tr["nrecomp"])) == (4, 4, 1)
+    assert np.array_equal(r["perm"], np.arange(6))
+    assert r["u"][4] == 2.0 ** -13 and r["uref"][4] == 2.0 ** -13
+    assert r["u"][5] == 0.5 and r["uref"][5] == 0.5
+    assert np.all(r["u"][:4] == 0.0)
 
 
 # ---------------------------------------------------------------- theorems (SDD mode)
