@@ -31,6 +31,7 @@ def rdiag_tol(d, anorm, m):
     """|R_ii| within 1e-11 relative where |R_ii| >= 1e-3 anorm, else 1e-11 |R_ii| + e_i."""
     return np.where(d >= 1e-3 * anorm, 1e-11 * d, 1e-11 * d + row_err(m, d.size, anorm))
 
+
 M, N = 300, 200
 
 
