@@ -218,3 +218,29 @@ def test_policy_and_mlp_argument_checks(lib):
     assert lib.qrdm_mlp_adam_step(fake, fake, fake, fake, fake, 1, 1e-3, 1.0, 0.999, 1e-8, 0.0, None) == -8
     assert lib.qrdm_mlp_train(fake, fake, fake, fake, fake, 0, 4, 1, 1e-3, 0.0, 1, None, fake, 1 << 30, None) == -6
     assert lib.qrdm_mlp_train(fake, fake, fake, fake, fake, 10, 4, 1, -1.0, 0.0, 1, None, fake, 1 << 30, None) == -9
+
+
+def test_the_library_path_has_no_fallback(monkeypatch):
+    """The product path fails loudly when libqrdm.so is missing, and no
+    module of the package imports the CPU oracle (which is test
+    infrastructure only): there is no CPU fallback to land on."""
+    import ast
+    import glob
+
+    from paper_2106_03138_gb300 import _binding, build as _build
+
+    monkeypatch.setattr(_binding, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", os.path.join(os.path.dirname(_build.LIB), "no_such_libqrdm.so"))
+    with pytest.raises(RuntimeError):
+        _binding.load(build_if_missing=False)
+    pkg = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2106_03138_gb300")
+    for f in glob.glob(os.path.join(pkg, "*.py")):
+        tree = ast.parse(open(f).read())
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                mods = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom):
+                mods = [node.module or ""]
+            else:
+                continue
+            assert not any(m == "oracle" or m.startswith("oracle.") for m in mods), (f, mods)
