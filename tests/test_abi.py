@@ -244,3 +244,27 @@ def test_the_library_path_has_no_fallback(monkeypatch):
             else:
                 continue
             assert not any(m == "oracle" or m.startswith("oracle.") for m in mods), (f, mods)
+
+
+def test_the_oracle_shares_no_code_with_the_gpu_path():
+    """The oracle imports nothing from the package and includes none of its
+    headers; the CUDA sources include nothing from the oracle."""
+    import ast
+    import glob
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for f in glob.glob(os.path.join(root, "oracle", "*.py")):
+        for node in ast.walk(ast.parse(open(f).read())):
+            if isinstance(node, ast.Import):
+                mods = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom):
+                mods = [node.module or ""]
+            else:
+                continue
+            assert not any(m.startswith("paper_2106_03138_gb300") for m in mods), (f, mods)
+    for f in glob.glob(os.path.join(root, "oracle", "*.c")):
+        incs = re.findall(r'#include\s*[<"]([^>"]+)[>"]', open(f).read())
+        assert all("/" not in i and not i.startswith("qrdm") for i in incs), (f, incs)
+    for f in glob.glob(os.path.join(root, "paper_2106_03138_gb300", "csrc", "*")):
+        incs = re.findall(r'#include\s*[<"]([^>"]+)[>"]', open(f).read())
+        assert not any("oracle" in i or i.startswith("oq_") for i in incs), (f, incs)
