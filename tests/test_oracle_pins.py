@@ -583,6 +583,24 @@ def test_ls_basic_rank_deficient_compatible_system_is_solved():
     assert np.linalg.norm(A @ x - b) <= 1e-12 * np.linalg.norm(b)
 
 
+def test_ls_basic_incompatible_rank_deficient_is_the_lstsq_on_the_pivot_columns():
+    """The basic solution x = Pi [R11^-1 (Q^T b)_{1:r}; 0] is, by definition,
+    the least-squares solution restricted to the r pivot columns: for an
+    incompatible right-hand side it equals the library least-squares
+    solution of A[:, perm[:r]] scattered back, and its residual is
+    orthogonal to those columns."""
+    A = inputs.from_spectrum(90, 70, inputs.sigma_gap(70, 25, lo=1e-15), 9)
+    b = np.random.default_rng(10).standard_normal(90)
+    f = O.qrdm(A, 0.9, 0.9, 32)
+    x = O.ls_basic(A, b, rank=25, fact=f)
+    sel = f["perm"][:25]
+    ref = np.zeros(70)
+    ref[sel] = np.linalg.lstsq(A[:, sel], b, rcond=None)[0]
+    cond = np.linalg.cond(A[:, sel])
+    np.testing.assert_allclose(x, ref, rtol=0, atol=100 * cond * 2.0 ** -52 * np.abs(ref).max())
+    assert np.linalg.norm(A[:, sel].T @ (b - A @ x)) <= 1e-12 * np.linalg.norm(b) * np.linalg.norm(A[:, sel])
+
+
 # ---------------------------------------------------------------- OpenMP build
 @pytest.mark.parametrize("kind", ["gap", "geo", "kahan"])
 def test_openmp_build_gives_the_same_bits(kind):
